@@ -1,0 +1,353 @@
+"""Benchmark of the GB300 RandomizedNNLS hot path (sketch + Lawson-Hanson solve).
+
+One step = one pass of the whole path over one problem: sample the rows
+(Philox), sketch [A | b] (sign flip + Walsh-Hadamard + sampled-row combine),
+Gram of the sketch, Lawson-Hanson NNLS.  Default workload: A 2^20 x 64
+term-document-like FP32, r = 4096 (workload 2), inputs resident in HBM
+(273 MB, larger than the 129 MB L2, so no flush between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config C] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own
+instance (weak scaling, no collective on the data path); the reported value
+is all ranks' solves divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "RandNNLS solves/s & SRHT GB/s vs ~8 TB/s HBM at residual ratio <=1.01"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_desc(cfg: int, p) -> dict:
+    names = {1: "c1: A 4096x20 uniform FP64, r=512", 2: "c2: A 2^20x64 term-doc FP32, r=4096",
+             3: "c3: A 2^22x128 term-doc FP32, r=8192"}
+    return {"workload": names[cfg], "n": int(p.n), "d": int(p.d), "r": int(p.r), "sampling": "iid",
+            "l2": "inputs larger than L2 (no flush)" if p.A.nbytes > 129e6 else "inputs in L2 (small case)",
+            "parallelism": "independent instance per GPU"}
+
+
+def algorithmic_bytes(p, s: int) -> int:
+    # one read of [A | b], one write of the sketch, the sampled-row indices
+    return int(p.n * (p.d + 1) * s + p.r * (p.d + 1) * s + 4 * p.r)
+
+
+def measured_hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_0812_4547_gb300/csrc/sketch.cu", "paper_0812_4547_gb300/csrc/common.cuh",
+                "paper_0812_4547_gb300/csrc/kernels.h"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged since."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)[kernel]
+        if rec.get("source_sha256") == source_hash() and rec.get("workload") == workload:
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs (read-only query)."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, t0: float, t1: float) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts + frac, float(parts[1]), float(parts[2]), parts[4:8]))
+            except Exception:
+                continue
+        os.unlink(self.path)
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        use = inside if inside else sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:2]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median([r[1] for r in use]) if use else None,
+                "sm_max_mhz": max([r[2] for r in use]) if use else None,
+                "reasons": reasons, "samples_in_region": len(inside)}
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------------------
+def run_reference(args, cfg: int):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    p = workloads.problem(cfg)
+    threads = os.cpu_count() or 1
+    for i in range(args.warmup):
+        oracle.randomized_nnls(p.A, p.b, p.r, seed=i, nthreads=threads)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.randomized_nnls(p.A, p.b, p.r, seed=args.warmup + i, nthreads=threads)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded term-document-like stand-in for TechTC300)",
+           "config": workload_desc(cfg, p),
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                            "sample": f"{args.steps} full solves of the workload (FP64 C oracle, OpenMP over columns)"},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(p, seconds: float) -> dict:
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        oracle.randomized_nnls(p.A, p.b, p.r, seed=done, nthreads=threads)
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": f"{done} full solves of the workload in {dt:.1f} s (FP64 C oracle, OpenMP over columns)"}
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    cfg = args.config
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl")
+    import paper_0812_4547_gb300 as P
+    from paper_0812_4547_gb300 import _binding as B
+
+    dev = torch.device("cuda", local)
+    base = workloads.CONFIGS[cfg]["seed"]
+    p = workloads.problem(cfg, seed=base + 1000 * rank) if ws > 1 else workloads.problem(cfg)
+    f64 = cfg == 1
+    dt_np = np.float64 if f64 else np.float32
+    tdt = torch.float64 if f64 else torch.float32
+    elt = 8 if f64 else 4
+    A_host = torch.from_numpy(np.ascontiguousarray(p.A.astype(dt_np).T)).pin_memory()
+    b_host = torch.from_numpy(np.asarray(p.b, dtype=dt_np)).pin_memory()
+    A = A_host.to(dev).t()
+    b = b_host.to(dev)
+    ctx = P.Context(local)
+    r = p.r
+    SA = torch.empty((p.d, r), dtype=tdt, device=dev).t()
+    Sb = torch.empty(r, dtype=tdt, device=dev)
+    idx = torch.empty(r, dtype=torch.int32, device=dev)
+    x = torch.empty(p.d, dtype=torch.float64, device=dev)
+    info = torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device=dev)
+    x_host = torch.empty(p.d, dtype=torch.float64).pin_memory()
+
+    def step(i: int):
+        ctx.sketch(A, b, r, seed=i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
+        ctx.solve(SA, Sb, r=r, x=x, info=info)
+
+    stream = ctx.stream
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.15)
+    B.rnnls_profile_begin(ctx.handle, 16 * args.steps + 64)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    w0 = time.time()
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    prof = B.rnnls_profile_end(ctx.handle)
+    clk = clocks.stop(w0, w1)
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = ms / args.steps
+    value = ws * args.steps / (ms / 1e3)
+
+    # e2e: pinned host inputs copied in and the solution read back every step
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, min(args.steps, 200))
+    for i in range(2):
+        A.copy_(A_host.t(), non_blocking=True)
+        b.copy_(b_host, non_blocking=True)
+        step(i)
+        x_host.copy_(x, non_blocking=True)
+        stream.synchronize()
+    e0 = time.perf_counter()
+    for i in range(e2e_steps):
+        A.copy_(A_host.t(), non_blocking=True)
+        b.copy_(b_host, non_blocking=True)
+        step(i)
+        x_host.copy_(x, non_blocking=True)
+        stream.synchronize()
+    e_dt = time.perf_counter() - e0
+    if ws > 1:
+        t = torch.tensor([e_dt], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e_dt = float(t.item())
+    e2e = {"value": ws * e2e_steps / e_dt, "unit": "solves/s",
+           "h2d_bytes_per_step": int(A_host.numel() * elt + b_host.numel() * elt),
+           "d2h_bytes_per_step": int(x_host.numel() * 8)}
+
+    # residual ratio of Theorem 1 (evaluation, off the timed path): x~ for
+    # seed 0 vs the exact NNLS on the full A, both solved by the library
+    step(0)
+    x_t = x.clone()
+    x_opt, info_opt = ctx.solve(A, b, r=p.n)
+    res_t = ctx.residual(A, b, x_t) if not f64 else None
+    res_o = ctx.residual(A, b, x_opt) if not f64 else None
+    torch.cuda.synchronize()
+    ratio = None
+    if res_t is not None:
+        ratio = float(res_t.item()) / float(res_o.item())
+    sketch_info = P.info_dict(info)
+
+    # roofline of the dominant kernel (the chunked sketch), timed live with
+    # CUDA events on the launching stream during the timed region
+    kname = "sketch_chunked_f32" if "sketch_chunked_f32" in prof else max(prof, key=lambda k: prof[k][1])
+    launches, kms = prof[kname]
+    abytes = algorithmic_bytes(p, elt)
+    achieved = abytes / (kms / launches / 1e3) / 1e9
+    peak, peak_src = measured_hbm_peak()
+    sketch_ms = sum(prof.get(k, (0, 0.0))[1] for k in ("sample_rows", "build_plan", "sketch_chunked_f32",
+                                                        "reduce_partials", "sketch_small", "sketch_f64"))
+    wl = workload_desc(cfg, p)
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if f64 else "f32",
+        "data": "synthetic (seeded term-document-like stand-in for TechTC300)", "config": wl,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": recorded_traffic(kname, wl["workload"]), "kernel": kname,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "algorithmic_bytes_per_launch": abytes, "avg_launch_us": 1e3 * kms / launches},
+        "sketch_gbs": abytes * args.steps / (sketch_ms / 1e3) / 1e9 if sketch_ms > 0 else None,
+        "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "e2e": e2e, "clocks": clk,
+        "residual_ratio": ratio, "residual_ratio_le_1.01": (ratio is not None and ratio <= 1.01),
+        "solve_info": {"status": sketch_info["status"], "passive_count": sketch_info["passive_count"],
+                       "outer_iters": sketch_info["outer_iters"]},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    elif rank == 0:
+        out["cpu_baseline"] = None
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

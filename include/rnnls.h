@@ -1,0 +1,182 @@
+/*
+ * rnnls.h -- C ABI of the GB300 RandomizedNNLS library (librnnls.so).
+ *
+ * Implements the method of Boutsidis & Drineas, "Random Projections for the
+ * Nonnegative Least-Squares Problem": given a tall A (n x d, n >> d), a
+ * target b and a sample size r, build the small problem
+ *     SA = H~ D A,  Sb = H~ D b                         (Alg. 1 steps 1-4)
+ * with D a random +-1 diagonal and H~ the randomly sampled, rescaled rows of
+ * the normalised Walsh-Hadamard matrix H_n (Sec. 2), and return
+ *     x~ = argmin_{x >= 0} ||SA x - Sb||^2              (Alg. 1 step 5)
+ * computed by the Lawson-Hanson active-set method (Sec. 2.2) on the
+ * quadratic-programming form Q = SA'SA, q = SA'Sb (Sec. 3.4).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major with an explicit leading dimension.
+ *   - Pointers named A, b, SA, Sb, idx, x, info, SB, X are DEVICE pointers
+ *     (cudaMalloc'd or torch-allocated memory of the context's device)
+ *     unless the entry point's comment says HOST.  The caller owns every
+ *     buffer; the library never frees or retains caller pointers.
+ *   - The library owns only the context and its workspace (device memory
+ *     grown on demand by cudaMalloc and freed by rnnls_destroy).
+ *   - All work is enqueued on the context's stream and is asynchronous
+ *     unless stated; results are valid once that stream is synchronised.
+ *   - Rows n_raw..n-1, where n is the next power of two >= n_raw, are the
+ *     zero padding of Sec. 2; they are never read or stored.
+ *   - Return value: RNNLS_OK or an error code below.  Argument errors are
+ *     detected on the host before anything is enqueued.  Per-solve
+ *     outcomes (singular, iteration cap) are reported in rnnls_info.
+ *
+ * Randomness (the paper leaves the generator unspecified, Alg. 1 steps 2
+ * and 4): Philox4x64-10 (Salmon et al., SC'11) keyed by (seed, instance),
+ * counter (j, stream, 0, 0).
+ *   D_ii  : bit (i mod 64) of word (i / 64) of stream 0; set bit -> -1.
+ *   iid   : draw k (k < r) is row (word k of stream 2) >> (64 - log2 n).
+ *   Bernoulli (Alg. 1 step 2): row i kept iff word i of stream 1 is below
+ *           r * 2^(64 - log2 n), i.e. with probability exactly r/n; every
+ *           row when r >= n.  Kept rows are listed in increasing order.
+ *   Word w of a stream is word (w mod 4) of block j = w / 4.
+ * Scale of every kept row: 1/sqrt(r), the normalisation 1/sqrt(n) of H_n
+ * times sqrt(n/r) of S (Alg. 1 step 2); 1/sqrt(n) in Bernoulli mode with
+ * r >= n (Alg. 2 with p_i = 1/n).
+ */
+#ifndef RNNLS_H
+#define RNNLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RNNLS_OK 0
+#define RNNLS_EINVAL 1       /* bad argument (null pointer, size, stride, flag) */
+#define RNNLS_ECAPACITY 2    /* sampled rows exceed the caller's capacity */
+#define RNNLS_ENONFINITE 3   /* NaN or Inf in the Gram matrix of the sketch */
+#define RNNLS_ESINGULAR 4    /* passive-set system numerically singular */
+#define RNNLS_EMAXITER 5     /* Lawson-Hanson iteration cap reached */
+#define RNNLS_ETIMEOUT 6     /* a bounded device-side wait gave up */
+#define RNNLS_ECUDA 7        /* a CUDA runtime call failed */
+#define RNNLS_ENOMEM 8       /* workspace allocation failed */
+#define RNNLS_EUNSUPPORTED 9 /* size outside what this build handles */
+
+/* ---- flags --------------------------------------------------------------- */
+#define RNNLS_SAMPLE_IID 0u       /* r uniform draws with replacement (default) */
+#define RNNLS_SAMPLE_BERNOULLI 1u /* each row kept with probability r/n (Alg. 1 step 2) */
+#define RNNLS_SAMPLE_MASK 1u
+
+typedef struct rnnls_ctx rnnls_ctx;
+
+/* Outcome of one Lawson-Hanson solve (written by the device). */
+typedef struct rnnls_info {
+  int32_t status;        /* RNNLS_OK, RNNLS_ESINGULAR, RNNLS_EMAXITER or RNNLS_ENONFINITE */
+  int32_t outer_iters;   /* accepted additions to the passive set */
+  int32_t inner_iters;   /* passive-set solves inside the interpolation loop */
+  int32_t passive_count; /* |P| at exit = number of positive entries of x */
+  double tol;            /* dual tolerance used: 10 eps ||SA||_1 max(r, d) ||Sb||_2 */
+  double dual_max;       /* max over j not in P of w_j = (SA'(Sb - SA x))_j at exit */
+  double objective;      /* ||SA x - Sb||^2 at exit */
+} rnnls_info;
+
+/* One problem of a batched solve.  All pointers are device pointers. */
+typedef struct rnnls_problem {
+  const float *SA; /* r x d, column-major, leading dimension ldsa >= r */
+  int64_t ldsa;
+  const float *Sb; /* r */
+  int64_t r;
+  int64_t d;
+  double *x;         /* out: d */
+  rnnls_info *info;  /* out: nullable */
+} rnnls_problem;
+
+/* Create a context on CUDA device `device` that enqueues on `stream`
+ * (a cudaStream_t, borrowed, may be NULL for the legacy default stream).
+ * Errors: EINVAL (ctx null), ECUDA (device unusable). */
+int rnnls_create(rnnls_ctx **ctx, int device, void *stream);
+
+/* Free the context and its workspace (synchronises its stream first). */
+int rnnls_destroy(rnnls_ctx *ctx);
+
+/* Replace the stream the context enqueues on (borrowed). */
+int rnnls_set_stream(rnnls_ctx *ctx, void *stream);
+
+/* Sketch of Alg. 1 steps 1-4 for FP32 data:
+ *   SA[k, j] = s * sum_i H_n[idx[k], i] D_ii A[i, j]   (k < r_out, j < d)
+ *   Sb[k]    = s * sum_i H_n[idx[k], i] D_ii b[i]
+ * with s the row scale above and H_n unnormalised (entries +-1).
+ * A: n_raw x d, leading dimension lda >= n_raw.  b: n_raw.
+ * SA: cap x d, leading dimension ldsa >= cap.  Sb: cap.  idx: cap int32
+ * (nullable): the sampled rows, draw order (iid) or increasing (Bernoulli).
+ * cap must be >= r in iid mode; in Bernoulli mode a count above cap
+ * returns ECAPACITY (size cap as r + 6 sqrt(r) + 16, or n when r >= n).
+ * r_out (HOST, nullable) receives the number of rows; in Bernoulli mode
+ * this synchronises the stream.  Requires n_raw >= 1, d >= 1, r >= 1,
+ * n_raw <= 2^28.  A and b need not be 16-byte aligned (aligned is faster).
+ * Accuracy: FP32 accumulation; relative Frobenius error vs FP64 about
+ * 1e-7 * sqrt(log2 n). */
+int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d,
+                 int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, float *SA, int64_t ldsa, float *Sb,
+                 int32_t *idx, int64_t cap, int64_t *r_out);
+
+/* The same sketch in FP64 throughout (for FP64 inputs). */
+int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double *b, int64_t n_raw, int64_t d,
+                     int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, double *SA, int64_t ldsa,
+                     double *Sb, int32_t *idx, int64_t cap, int64_t *r_out);
+
+/* Small NNLS of Alg. 1 step 5:  x = argmin_{x >= 0} ||SA x - Sb||^2,
+ * SA r x d (ldsa >= r), Sb r, FP32 device data; x (device, FP64, d) and
+ * info (device, nullable).  Lawson-Hanson rules: start at x = 0 (Sec. 4.1);
+ * add argmax_j w_j (ties to the smallest j) while it exceeds info->tol;
+ * a candidate whose passive solve gives z_t <= 0 or a dependent column
+ * (pivot^2 <= 1e-13 Q_tt) is rejected for that selection; interpolate with
+ * alpha = min x_j/(x_j - z_j) (ties to the smallest j) and drop x_j <= 0;
+ * caps 3d additions and 30d interpolation solves (EMAXITER).
+ * Q = SA'SA and q = SA'Sb are formed with products exact and sums
+ * compensated (about 2^-44 relative), the Lawson-Hanson decisions use
+ * passive solves refined to that accuracy.  Requires 1 <= d <= 256,
+ * r >= 1.  A return of RNNLS_OK means the work was enqueued; the solve's
+ * own outcome is info->status. */
+int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
+                rnnls_info *info);
+
+/* The same solve for FP64 sketches. */
+int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,
+                    double *x, rnnls_info *info);
+
+/* Many independent small NNLS problems in one launch sequence (one
+ * Lawson-Hanson block per problem, uneven d and r allowed).  `probs` is a
+ * HOST array of `count` descriptors whose pointers are device pointers. */
+int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count, uint32_t flags);
+
+/* Objective of Definition 1 on the full data: out[0] = ||A x - b||^2 with
+ * A n x d (lda >= n) and b FP32, x FP64 (device), accumulated in FP64.
+ * out: device double. */
+int rnnls_residual(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
+                   const double *x, double *out);
+
+/* Launch profiling (tracing aid, not part of the method).  Between
+ * rnnls_profile_begin and rnnls_profile_end the context records a CUDA
+ * event pair on its stream around each of its kernel launches (at most
+ * max_launches).  rnnls_profile_end synchronises the stream and writes one
+ * entry per kernel kind (HOST array `out` of capacity max_out): the kernel
+ * name, its launch count and the summed event time in milliseconds.
+ * *n_out receives the number of entries written.  Errors: EINVAL (null
+ * context or out, max_launches < 1), ENOMEM, ECUDA. */
+typedef struct rnnls_kernel_time {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} rnnls_kernel_time;
+
+int rnnls_profile_begin(rnnls_ctx *ctx, int max_launches);
+int rnnls_profile_end(rnnls_ctx *ctx, rnnls_kernel_time *out, int max_out, int *n_out);
+
+/* Human-readable text of a status code (static storage). */
+const char *rnnls_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RNNLS_H */

@@ -1,0 +1,154 @@
+"""GB300-native RandomizedNNLS (Boutsidis & Drineas): the subsampled randomized
+Hadamard sketch of a tall [A | b] and the Lawson-Hanson solve on the sketch,
+behind the C ABI of include/rnnls.h.
+
+:class:`Context` marshals torch tensors (device memory and streams only) into
+the C calls; the same-name raw wrappers live in :mod:`._binding`.
+Matrices are column-major: an (n, d) tensor with ``stride(0) == 1``
+(e.g. ``torch.empty(d, n, device="cuda").t()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+from . import _binding as B
+from ._binding import (RNNLS_SAMPLE_BERNOULLI, RNNLS_SAMPLE_IID, RNNLSError, rnnls_info,  # noqa: F401
+                       rnnls_problem)
+
+INFO_BYTES = ctypes.sizeof(rnnls_info)
+
+
+def bernoulli_capacity(r: int, n: int) -> int:
+    """Row capacity that a Bernoulli-mode sketch output needs (6 sigma above r)."""
+    if r >= n:
+        return n
+    return int(r + math.ceil(6.0 * math.sqrt(r)) + 16)
+
+
+def padded_n(n_raw: int) -> int:
+    n = 1
+    while n < n_raw:
+        n <<= 1
+    return n
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def colmajor(t):
+    """Column-major copy (or view) of a 2-D tensor."""
+    if t.dim() != 2:
+        raise ValueError("expected a matrix")
+    if t.stride(0) == 1 and t.stride(1) >= max(t.shape[0], 1):
+        return t
+    return t.t().contiguous().t()
+
+
+def _ld(t) -> int:
+    return max(int(t.stride(1)), int(t.shape[0]), 1)
+
+
+def info_dict(raw) -> dict:
+    """Decode an rnnls_info held in a uint8 tensor (host or device)."""
+    b = bytes(raw.cpu().numpy().tobytes())
+    inf = rnnls_info.from_buffer_copy(b[:INFO_BYTES])
+    return {k: getattr(inf, k) for k, _ in rnnls_info._fields_}
+
+
+class Context:
+    """One library context bound to a CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.handle = B.rnnls_create(device, self.stream.cuda_stream)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            B.rnnls_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream) -> None:
+        self.stream = stream
+        B.rnnls_set_stream(self.handle, stream.cuda_stream)
+
+    # -- sketch -------------------------------------------------------------------------
+    def sketch(self, A, b, r: int, seed: int, instance: int = 0, mode: int = RNNLS_SAMPLE_IID, SA=None, Sb=None,
+               idx=None, cap: int | None = None, want_count: bool = True):
+        """SA, Sb, idx and the row count of Alg. 1's sketch (FP32 or FP64 by A's dtype)."""
+        torch = _torch()
+        A = colmajor(A)
+        n_raw, d = A.shape
+        n = padded_n(n_raw)
+        if cap is None:
+            cap = r if mode == RNNLS_SAMPLE_IID else bernoulli_capacity(r, n)
+        dt = A.dtype
+        if SA is None:
+            SA = torch.empty((d, cap), dtype=dt, device=A.device).t()
+        if Sb is None:
+            Sb = torch.empty(cap, dtype=dt, device=A.device)
+        if idx is None:
+            idx = torch.empty(cap, dtype=torch.int32, device=A.device)
+        fn = B.rnnls_sketch if dt == torch.float32 else B.rnnls_sketch_f64
+        if dt not in (torch.float32, torch.float64) or b.dtype != dt or SA.dtype != dt or Sb.dtype != dt:
+            raise TypeError("A, b, SA, Sb must share dtype float32 or float64")
+        if not b.is_contiguous() or not Sb.is_contiguous() or not idx.is_contiguous():
+            raise ValueError("b, Sb and idx must be contiguous")
+        rows = fn(self.handle, A.data_ptr(), _ld(A), b.data_ptr(), n_raw, d, r, seed, instance, mode,
+                  SA.data_ptr(), _ld(SA), Sb.data_ptr(), idx.data_ptr(), cap, want_count)
+        return SA, Sb, idx, rows
+
+    # -- solve ----------------------------------------------------------------------------
+    def solve(self, SA, Sb, r: int | None = None, x=None, info=None):
+        """x = argmin_{x>=0} ||SA x - Sb||^2 (Lawson-Hanson); returns (x, info bytes)."""
+        torch = _torch()
+        SA = colmajor(SA)
+        rr = SA.shape[0] if r is None else r
+        d = SA.shape[1]
+        if x is None:
+            x = torch.empty(d, dtype=torch.float64, device=SA.device)
+        if info is None:
+            info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=SA.device)
+        fn = B.rnnls_solve if SA.dtype == torch.float32 else B.rnnls_solve_f64
+        fn(self.handle, SA.data_ptr(), _ld(SA), Sb.data_ptr(), rr, d, x.data_ptr(), info.data_ptr())
+        return x, info
+
+    def solve_batched(self, problems):
+        """problems: list of (SA, Sb, x, info) tensors; FP32 sketches."""
+        descs = []
+        for SA, Sb, x, info in problems:
+            SA = colmajor(SA)
+            descs.append(rnnls_problem(SA.data_ptr(), _ld(SA), Sb.data_ptr(), SA.shape[0], SA.shape[1], x.data_ptr(),
+                                       info.data_ptr() if info is not None else None))
+        B.rnnls_solve_batched(self.handle, descs, 0)
+
+    def residual(self, A, b, x, out=None):
+        """||A x - b||^2 on the full data (FP64 accumulation), a 1-element device tensor."""
+        torch = _torch()
+        A = colmajor(A)
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=A.device)
+        B.rnnls_residual(self.handle, A.data_ptr(), _ld(A), b.data_ptr(), A.shape[0], A.shape[1], x.data_ptr(),
+                         out.data_ptr())
+        return out
+
+    def randomized_nnls(self, A, b, r: int, seed: int, instance: int = 0, mode: int = RNNLS_SAMPLE_IID):
+        """Alg. 1 end to end on device tensors: sketch, then Lawson-Hanson."""
+        SA, Sb, idx, rows = self.sketch(A, b, r, seed, instance, mode)
+        x, info = self.solve(SA[:rows], Sb[:rows], r=rows)
+        return x, info, (SA, Sb, idx, rows)
+
+
+def lib_path() -> str:
+    return B.lib_path()

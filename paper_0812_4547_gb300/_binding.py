@@ -1,0 +1,190 @@
+"""ctypes declarations of the C ABI in include/rnnls.h (librnnls.so).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Importing this module never builds anything; :func:`lib` raises
+if ``librnnls.so`` is missing, so no caller can fall back to another path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+RNNLS_OK = 0
+RNNLS_EINVAL = 1
+RNNLS_ECAPACITY = 2
+RNNLS_ENONFINITE = 3
+RNNLS_ESINGULAR = 4
+RNNLS_EMAXITER = 5
+RNNLS_ETIMEOUT = 6
+RNNLS_ECUDA = 7
+RNNLS_ENOMEM = 8
+RNNLS_EUNSUPPORTED = 9
+
+RNNLS_SAMPLE_IID = 0
+RNNLS_SAMPLE_BERNOULLI = 1
+
+#: every entry point declared in include/rnnls.h
+EXPORTS = (
+    "rnnls_create", "rnnls_destroy", "rnnls_set_stream", "rnnls_sketch", "rnnls_sketch_f64", "rnnls_solve",
+    "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
+    "rnnls_profile_end",
+)
+
+
+class rnnls_info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("outer_iters", ctypes.c_int32),
+        ("inner_iters", ctypes.c_int32),
+        ("passive_count", ctypes.c_int32),
+        ("tol", ctypes.c_double),
+        ("dual_max", ctypes.c_double),
+        ("objective", ctypes.c_double),
+    ]
+
+
+class rnnls_kernel_time(ctypes.Structure):
+    _fields_ = [
+        ("name", ctypes.c_char * 32),
+        ("launches", ctypes.c_int64),
+        ("total_ms", ctypes.c_double),
+    ]
+
+
+class rnnls_problem(ctypes.Structure):
+    _fields_ = [
+        ("SA", ctypes.c_void_p),
+        ("ldsa", ctypes.c_int64),
+        ("Sb", ctypes.c_void_p),
+        ("r", ctypes.c_int64),
+        ("d", ctypes.c_int64),
+        ("x", ctypes.c_void_p),
+        ("info", ctypes.c_void_p),
+    ]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        P, I64, U64, U32, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        L.rnnls_create.argtypes = [ctypes.POINTER(P), I32, P]
+        L.rnnls_destroy.argtypes = [P]
+        L.rnnls_set_stream.argtypes = [P, P]
+        sk = [P, P, I64, P, I64, I64, I64, U64, U64, U32, P, I64, P, P, I64, ctypes.POINTER(I64)]
+        L.rnnls_sketch.argtypes = sk
+        L.rnnls_sketch_f64.argtypes = sk
+        L.rnnls_solve.argtypes = [P, P, I64, P, I64, I64, P, P]
+        L.rnnls_solve_f64.argtypes = [P, P, I64, P, I64, I64, P, P]
+        L.rnnls_solve_batched.argtypes = [P, ctypes.POINTER(rnnls_problem), I64, U32]
+        L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
+        L.rnnls_profile_begin.argtypes = [P, I32]
+        L.rnnls_profile_end.argtypes = [P, ctypes.POINTER(rnnls_kernel_time), I32, ctypes.POINTER(I32)]
+        L.rnnls_strerror.argtypes = [I32]
+        L.rnnls_strerror.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name != "rnnls_strerror":
+                getattr(L, name).restype = I32
+        _LIB = L
+        return L
+
+
+class RNNLSError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().rnnls_strerror(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def check(status: int, where: str) -> None:
+    if status != RNNLS_OK:
+        raise RNNLSError(status, where)
+
+
+# thin same-name wrappers over raw pointers -------------------------------------------------
+
+def rnnls_create(device: int = 0, stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    check(lib().rnnls_create(ctypes.byref(h), device, ctypes.c_void_p(stream)), "rnnls_create")
+    return h.value
+
+
+def rnnls_destroy(ctx: int) -> None:
+    check(lib().rnnls_destroy(ctypes.c_void_p(ctx)), "rnnls_destroy")
+
+
+def rnnls_set_stream(ctx: int, stream: int) -> None:
+    check(lib().rnnls_set_stream(ctypes.c_void_p(ctx), ctypes.c_void_p(stream)), "rnnls_set_stream")
+
+
+def _sketch(fn, name, ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA, ldsa, Sb, idx, cap, want_count):
+    rout = ctypes.c_int64(-1)
+    st = fn(ctypes.c_void_p(ctx), ctypes.c_void_p(A), lda, ctypes.c_void_p(b), n_raw, d, r, seed, instance, flags,
+            ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), ctypes.c_void_p(idx), cap,
+            ctypes.byref(rout) if want_count else None)
+    check(st, name)
+    return rout.value
+
+
+def rnnls_sketch(ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA, ldsa, Sb, idx, cap, want_count=True):
+    return _sketch(lib().rnnls_sketch, "rnnls_sketch", ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA, ldsa,
+                   Sb, idx, cap, want_count)
+
+
+def rnnls_sketch_f64(ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA, ldsa, Sb, idx, cap, want_count=True):
+    return _sketch(lib().rnnls_sketch_f64, "rnnls_sketch_f64", ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA,
+                   ldsa, Sb, idx, cap, want_count)
+
+
+def rnnls_solve(ctx, SA, ldsa, Sb, r, d, x, info) -> None:
+    check(lib().rnnls_solve(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
+                            ctypes.c_void_p(x), ctypes.c_void_p(info)), "rnnls_solve")
+
+
+def rnnls_solve_f64(ctx, SA, ldsa, Sb, r, d, x, info) -> None:
+    check(lib().rnnls_solve_f64(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
+                                ctypes.c_void_p(x), ctypes.c_void_p(info)), "rnnls_solve_f64")
+
+
+def rnnls_solve_batched(ctx, problems, flags: int = 0) -> None:
+    arr = (rnnls_problem * len(problems))(*problems)
+    check(lib().rnnls_solve_batched(ctypes.c_void_p(ctx), arr, len(problems), flags), "rnnls_solve_batched")
+
+
+def rnnls_residual(ctx, A, lda, b, n, d, x, out) -> None:
+    check(lib().rnnls_residual(ctypes.c_void_p(ctx), ctypes.c_void_p(A), lda, ctypes.c_void_p(b), n, d,
+                               ctypes.c_void_p(x), ctypes.c_void_p(out)), "rnnls_residual")
+
+
+def rnnls_profile_begin(ctx, max_launches: int = 4096) -> None:
+    check(lib().rnnls_profile_begin(ctypes.c_void_p(ctx), max_launches), "rnnls_profile_begin")
+
+
+def rnnls_profile_end(ctx) -> dict:
+    """{kernel name: (launches, total_ms)} of the launches since rnnls_profile_begin."""
+    out = (rnnls_kernel_time * 32)()
+    n = ctypes.c_int(0)
+    check(lib().rnnls_profile_end(ctypes.c_void_p(ctx), out, 32, ctypes.byref(n)), "rnnls_profile_end")
+    return {out[i].name.decode(): (int(out[i].launches), float(out[i].total_ms)) for i in range(n.value)}
+
+
+def rnnls_strerror(status: int) -> str:
+    return lib().rnnls_strerror(status).decode()

@@ -1,0 +1,375 @@
+// api.cu -- the C ABI declared in include/rnnls.h: context, workspace,
+// argument checks and dispatch to the sampling, sketch and solve kernels.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "kernels.h"
+
+namespace rnnls {
+
+int ensure_workspace(rnnls_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return RNNLS_OK;
+  // in-flight work on the context stream may still use the old buffer
+  RNNLS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  const size_t want = align_up(bytes + bytes / 4, 1 << 20);
+  if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    return RNNLS_ENOMEM;
+  }
+  ctx->ws_bytes = want;
+  return RNNLS_OK;
+}
+
+int ensure_aux(rnnls_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->aux_bytes) return RNNLS_OK;
+  RNNLS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (ctx->aux) cudaFree(ctx->aux);
+  ctx->aux = nullptr;
+  ctx->aux_bytes = 0;
+  const size_t want = align_up(bytes + bytes / 4, 1 << 16);
+  if (cudaMalloc(&ctx->aux, want) != cudaSuccess) {
+    cudaGetLastError();
+    return RNNLS_ENOMEM;
+  }
+  ctx->aux_bytes = want;
+  return RNNLS_OK;
+}
+
+int ensure_pinned(rnnls_ctx *ctx, size_t bytes) {
+  // the previous copy out of the staging buffer must be complete
+  RNNLS_CUDA_TRY(cudaEventSynchronize(ctx->pinned_ready));
+  if (bytes <= ctx->pinned_bytes) return RNNLS_OK;
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  ctx->pinned = nullptr;
+  ctx->pinned_bytes = 0;
+  const size_t want = align_up(bytes + bytes / 4, 4096);
+  if (cudaMallocHost(&ctx->pinned, want) != cudaSuccess) {
+    cudaGetLastError();
+    return RNNLS_ENOMEM;
+  }
+  ctx->pinned_bytes = want;
+  return RNNLS_OK;
+}
+
+const char *kernel_name(int kid) {
+  static const char *names[K_COUNT] = {"sample_rows", "build_plan", "sketch_chunked_f32", "sketch_small",
+                                       "reduce_partials", "sketch_f64", "gram", "gram_reduce", "colabs",
+                                       "lawson_hanson", "residual"};
+  return (kid >= 0 && kid < K_COUNT) ? names[kid] : "?";
+}
+
+}  // namespace rnnls
+
+using namespace rnnls;
+
+namespace {
+
+constexpr int64_t kMaxRows = (int64_t)1 << 28;
+
+// Device layout of the auxiliary buffer: [count (int64) | sampled rows (int32)].
+struct aux_view {
+  int64_t *d_count;
+  int32_t *idx;
+  void *bern_ws;
+};
+
+int get_aux(rnnls_ctx *ctx, int64_t cap, int64_t n, bool need_idx, aux_view &v) {
+  const size_t b_count = 256;
+  const size_t b_idx = need_idx ? align_up((size_t)cap * sizeof(int32_t), 256) : 0;
+  const size_t b_bern = bernoulli_ws_bytes(n);
+  int st = ensure_aux(ctx, b_count + b_idx + b_bern);
+  if (st) return st;
+  char *base = (char *)ctx->aux;
+  v.d_count = (int64_t *)base;
+  v.idx = need_idx ? (int32_t *)(base + b_count) : nullptr;
+  v.bern_ws = base + b_count + b_idx;
+  return RNNLS_OK;
+}
+
+template <typename T>
+int check_sketch_args(rnnls_ctx *ctx, const T *A, int64_t lda, const T *b, int64_t n_raw, int64_t d, int64_t r,
+                      uint32_t flags, T *SA, int64_t ldsa, T *Sb, int64_t cap) {
+  if (!ctx || !A || !b || !SA || !Sb) return RNNLS_EINVAL;
+  if (n_raw < 1 || d < 1 || r < 1 || cap < 1) return RNNLS_EINVAL;
+  if (lda < n_raw || ldsa < cap) return RNNLS_EINVAL;
+  if (flags & ~RNNLS_SAMPLE_MASK) return RNNLS_EINVAL;
+  if ((flags & RNNLS_SAMPLE_MASK) == RNNLS_SAMPLE_IID && cap < r) return RNNLS_EINVAL;
+  if (n_raw > kMaxRows || d > (1 << 20) || r > ((int64_t)1 << 30)) return RNNLS_EUNSUPPORTED;
+  return RNNLS_OK;
+}
+
+// Sampling shared by both precisions; fills a.idx / count and the scale.
+int sample_rows(rnnls_ctx *ctx, int L, int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, int32_t *idx,
+                int64_t cap, aux_view &av, double &scale) {
+  const int64_t n = (int64_t)1 << L;
+  const bool bern = (flags & RNNLS_SAMPLE_MASK) == RNNLS_SAMPLE_BERNOULLI;
+  int st;
+  prof_scope ps(ctx, K_SAMPLE);
+  if (bern) {
+    st = launch_sample_bernoulli(ctx->stream, seed, instance, L, r, idx, cap, av.d_count, av.bern_ws);
+    scale = (r >= n) ? 1.0 / sqrt((double)n) : 1.0 / sqrt((double)r);
+  } else {
+    st = launch_sample_iid(ctx->stream, seed, instance, L, r, idx);
+    scale = 1.0 / sqrt((double)r);
+  }
+  return st;
+}
+
+int read_count(rnnls_ctx *ctx, const aux_view &av, int64_t cap, int64_t *r_out) {
+  int st = ensure_pinned(ctx, sizeof(int64_t));
+  if (st) return st;
+  RNNLS_CUDA_TRY(cudaMemcpyAsync(ctx->pinned, av.d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  RNNLS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  const int64_t cnt = *(int64_t *)ctx->pinned;
+  *r_out = cnt < cap ? cnt : cap;
+  return cnt > cap ? RNNLS_ECAPACITY : RNNLS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rnnls_create(rnnls_ctx **out, int device, void *stream) {
+  if (!out) return RNNLS_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return RNNLS_ECUDA;
+  }
+  RNNLS_CUDA_TRY(cudaSetDevice(device));
+  rnnls_ctx *ctx = new (std::nothrow) rnnls_ctx();
+  if (!ctx) return RNNLS_ENOMEM;
+  memset(ctx, 0, sizeof(*ctx));
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->pinned_ready, cudaEventDisableTiming) != cudaSuccess) {
+    delete ctx;
+    return RNNLS_ECUDA;
+  }
+  *out = ctx;
+  return RNNLS_OK;
+}
+
+static void profile_free(rnnls_ctx *ctx) {
+  if (ctx->prof_ev) {
+    for (int i = 0; i < 2 * ctx->prof_cap; ++i) cudaEventDestroy(ctx->prof_ev[i]);
+    delete[] ctx->prof_ev;
+    delete[] ctx->prof_kid;
+  }
+  ctx->prof_ev = nullptr;
+  ctx->prof_kid = nullptr;
+  ctx->prof_cap = 0;
+  ctx->prof_n = 0;
+  ctx->prof_on = 0;
+}
+
+int rnnls_profile_begin(rnnls_ctx *ctx, int max_launches) {
+  if (!ctx || max_launches < 1) return RNNLS_EINVAL;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  if (ctx->prof_cap < max_launches) {
+    RNNLS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    profile_free(ctx);
+    ctx->prof_ev = new (std::nothrow) cudaEvent_t[2 * (size_t)max_launches];
+    ctx->prof_kid = new (std::nothrow) int[(size_t)max_launches];
+    if (!ctx->prof_ev || !ctx->prof_kid) return RNNLS_ENOMEM;
+    for (int i = 0; i < 2 * max_launches; ++i) RNNLS_CUDA_TRY(cudaEventCreate(&ctx->prof_ev[i]));
+    ctx->prof_cap = max_launches;
+  }
+  ctx->prof_n = 0;
+  ctx->prof_on = 1;
+  return RNNLS_OK;
+}
+
+int rnnls_profile_end(rnnls_ctx *ctx, rnnls_kernel_time *out, int max_out, int *n_out) {
+  if (!ctx || !out || max_out < 1) return RNNLS_EINVAL;
+  ctx->prof_on = 0;
+  RNNLS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  double tot[K_COUNT] = {0};
+  int64_t cnt[K_COUNT] = {0};
+  for (int i = 0; i < ctx->prof_n; ++i) {
+    float ms = 0.0f;
+    RNNLS_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+    tot[ctx->prof_kid[i]] += ms;
+    cnt[ctx->prof_kid[i]] += 1;
+  }
+  int n = 0;
+  for (int k = 0; k < K_COUNT && n < max_out; ++k) {
+    if (!cnt[k]) continue;
+    memset(out[n].name, 0, sizeof(out[n].name));
+    strncpy(out[n].name, kernel_name(k), sizeof(out[n].name) - 1);
+    out[n].launches = cnt[k];
+    out[n].total_ms = tot[k];
+    ++n;
+  }
+  if (n_out) *n_out = n;
+  ctx->prof_n = 0;
+  return RNNLS_OK;
+}
+
+int rnnls_destroy(rnnls_ctx *ctx) {
+  if (!ctx) return RNNLS_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  profile_free(ctx);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->aux) cudaFree(ctx->aux);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  cudaEventDestroy(ctx->pinned_ready);
+  delete ctx;
+  return RNNLS_OK;
+}
+
+int rnnls_set_stream(rnnls_ctx *ctx, void *stream) {
+  if (!ctx) return RNNLS_EINVAL;
+  ctx->stream = (cudaStream_t)stream;
+  return RNNLS_OK;
+}
+
+int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d, int64_t r,
+                 uint64_t seed, uint64_t instance, uint32_t flags, float *SA, int64_t ldsa, float *Sb, int32_t *idx,
+                 int64_t cap, int64_t *r_out) {
+  int st = check_sketch_args(ctx, A, lda, b, n_raw, d, r, flags, SA, ldsa, Sb, cap);
+  if (st) return st;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int L = log2_ceil64(n_raw);
+  const bool bern = (flags & RNNLS_SAMPLE_MASK) == RNNLS_SAMPLE_BERNOULLI;
+  const int64_t rows = bern ? cap : r;
+  aux_view av;
+  st = get_aux(ctx, rows, (int64_t)1 << L, idx == nullptr, av);
+  if (st) return st;
+  int32_t *rows_idx = idx ? idx : av.idx;
+  double scale = 0.0;
+  st = sample_rows(ctx, L, r, seed, instance, flags, rows_idx, rows, av, scale);
+  if (st) return st;
+  sketch_args_f32 a;
+  a.A = A;
+  a.lda = lda;
+  a.b = b;
+  a.n_raw = n_raw;
+  a.d = (int)d;
+  a.L = L;
+  a.r = rows;
+  a.d_count = bern ? av.d_count : nullptr;
+  a.seed = seed;
+  a.inst = instance;
+  a.scale = (float)scale;
+  a.SA = SA;
+  a.ldsa = ldsa;
+  a.Sb = Sb;
+  a.idx = rows_idx;
+  st = sketch_f32(ctx, a, ctx->num_sms);
+  if (st) return st;
+  if (r_out) {
+    if (!bern) {
+      *r_out = r;
+    } else {
+      st = read_count(ctx, av, cap, r_out);
+      if (st) return st;
+    }
+  }
+  return RNNLS_OK;
+}
+
+int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double *b, int64_t n_raw, int64_t d,
+                     int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, double *SA, int64_t ldsa, double *Sb,
+                     int32_t *idx, int64_t cap, int64_t *r_out) {
+  int st = check_sketch_args(ctx, A, lda, b, n_raw, d, r, flags, SA, ldsa, Sb, cap);
+  if (st) return st;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int L = log2_ceil64(n_raw);
+  const bool bern = (flags & RNNLS_SAMPLE_MASK) == RNNLS_SAMPLE_BERNOULLI;
+  const int64_t rows = bern ? cap : r;
+  aux_view av;
+  st = get_aux(ctx, rows, (int64_t)1 << L, idx == nullptr, av);
+  if (st) return st;
+  int32_t *rows_idx = idx ? idx : av.idx;
+  double scale = 0.0;
+  st = sample_rows(ctx, L, r, seed, instance, flags, rows_idx, rows, av, scale);
+  if (st) return st;
+  sketch_args_f64 a;
+  a.A = A;
+  a.lda = lda;
+  a.b = b;
+  a.n_raw = n_raw;
+  a.d = (int)d;
+  a.L = L;
+  a.r = rows;
+  a.d_count = bern ? av.d_count : nullptr;
+  a.seed = seed;
+  a.inst = instance;
+  a.scale = scale;
+  a.SA = SA;
+  a.ldsa = ldsa;
+  a.Sb = Sb;
+  a.idx = rows_idx;
+  st = sketch_f64(ctx, a);
+  if (st) return st;
+  if (r_out) {
+    if (!bern) {
+      *r_out = r;
+    } else {
+      st = read_count(ctx, av, cap, r_out);
+      if (st) return st;
+    }
+  }
+  return RNNLS_OK;
+}
+
+int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
+                rnnls_info *info) {
+  if (!ctx || !SA || !Sb || !x || r < 1 || d < 1 || ldsa < r) return RNNLS_EINVAL;
+  if (d > 256) return RNNLS_EUNSUPPORTED;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  return solve_f32(ctx, SA, ldsa, Sb, r, d, x, info);
+}
+
+int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,
+                    double *x, rnnls_info *info) {
+  if (!ctx || !SA || !Sb || !x || r < 1 || d < 1 || ldsa < r) return RNNLS_EINVAL;
+  if (d > 256) return RNNLS_EUNSUPPORTED;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  return solve_f64(ctx, SA, ldsa, Sb, r, d, x, info);
+}
+
+int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count, uint32_t flags) {
+  if (!ctx || !probs || count < 1 || flags != 0) return RNNLS_EINVAL;
+  for (int64_t i = 0; i < count; ++i) {
+    const rnnls_problem &p = probs[i];
+    if (!p.SA || !p.Sb || !p.x || p.r < 1 || p.d < 1 || p.ldsa < p.r) return RNNLS_EINVAL;
+    if (p.d > 256) return RNNLS_EUNSUPPORTED;
+  }
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  return solve_batched(ctx, probs, count);
+}
+
+int rnnls_residual(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
+                   const double *x, double *out) {
+  if (!ctx || !A || !b || !x || !out || n < 1 || d < 1 || lda < n) return RNNLS_EINVAL;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  return residual_f32(ctx, A, lda, b, n, d, x, out);
+}
+
+const char *rnnls_strerror(int status) {
+  switch (status) {
+    case RNNLS_OK: return "ok";
+    case RNNLS_EINVAL: return "invalid argument";
+    case RNNLS_ECAPACITY: return "sampled rows exceed the output capacity";
+    case RNNLS_ENONFINITE: return "non-finite value in the sketch's Gram matrix";
+    case RNNLS_ESINGULAR: return "passive-set system numerically singular";
+    case RNNLS_EMAXITER: return "Lawson-Hanson iteration cap reached";
+    case RNNLS_ETIMEOUT: return "bounded device wait gave up";
+    case RNNLS_ECUDA: return "CUDA runtime error";
+    case RNNLS_ENOMEM: return "workspace allocation failed";
+    case RNNLS_EUNSUPPORTED: return "size outside what this build supports";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// kernels.h -- host-side launchers shared between the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rnnls {
+
+// ---- sampling (sample.cu) -------------------------------------------------
+// idx[k] = top L bits of word k of stream 2, k < r.
+int launch_sample_iid(cudaStream_t s, uint64_t seed, uint64_t inst, int L, int64_t r, int32_t *idx);
+// Bernoulli rows in increasing order; count written to *d_count (device);
+// rows beyond cap are dropped (the count still reports the true total).
+size_t bernoulli_ws_bytes(int64_t n);
+int launch_sample_bernoulli(cudaStream_t s, uint64_t seed, uint64_t inst, int L, int64_t r, int32_t *idx,
+                            int64_t cap, int64_t *d_count, void *ws);
+
+// ---- combine plan (sample.cu) ----------------------------------------------
+// Chunk size of the large-n sketch: 2^kLogM rows.
+constexpr int kLogM = 12;
+constexpr int kM = 1 << kLogM;
+constexpr int kThreads = 256;                 // threads of a sketch block
+constexpr int kWorkers = 4;                   // chunks transformed together
+constexpr int kPlanCapacityDen = kThreads - kWorkers;  // rows per slot bound
+
+struct plan_t {
+  uint32_t *pk;   // [kgroups][slots][kThreads]
+  int32_t *k;     // [kgroups][slots][kThreads]
+  uint32_t *cls;  // [kgroups][kThreads]: class (h & 3) of each thread's rows
+  int slots;
+  int kgroups;
+  int64_t rows_per_group;
+};
+size_t plan_ws_bytes(int slots, int kgroups);
+int launch_build_plan(cudaStream_t s, const int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
+                      void *ws_sort);
+
+// ---- sketch (sketch.cu) ------------------------------------------------------
+struct sketch_args_f32 {
+  const float *A;
+  int64_t lda;
+  const float *b;
+  int64_t n_raw;
+  int d;
+  int L;
+  int64_t r;          // rows (iid) or capacity bound (Bernoulli)
+  const int64_t *d_count;  // device row count (Bernoulli) or null
+  uint64_t seed, inst;
+  float scale;
+  float *SA;
+  int64_t ldsa;
+  float *Sb;
+  const int32_t *idx;
+};
+int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms);
+
+struct sketch_args_f64 {
+  const double *A;
+  int64_t lda;
+  const double *b;
+  int64_t n_raw;
+  int d;
+  int L;
+  int64_t r;
+  const int64_t *d_count;
+  uint64_t seed, inst;
+  double scale;
+  double *SA;
+  int64_t ldsa;
+  double *Sb;
+  const int32_t *idx;
+};
+int sketch_f64(rnnls_ctx *ctx, const sketch_args_f64 &a);
+
+// ---- solve (solve.cu) ----------------------------------------------------------
+int solve_f32(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
+              rnnls_info *info);
+int solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d, double *x,
+              rnnls_info *info);
+int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count);
+int residual_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
+                 const double *x, double *out);
+
+}  // namespace rnnls

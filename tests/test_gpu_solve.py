@@ -1,0 +1,150 @@
+"""GPU parity of the Lawson-Hanson solve (Alg. 1 step 5) against the oracle.
+
+The GPU solve and the oracle solve run on the same sketch bytes (the GPU's
+FP32 SA promoted exactly to FP64 for the oracle).  Bar: identical passive
+(active) sets, x within 1e-6 relative, same status.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from tests.gpu_util import dev_colmajor, dev_vec, host
+
+pytestmark = pytest.mark.gpu
+
+TOL_X = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_0812_4547_gb300 as P
+
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+def solve_both(ctx, orc, S, s, dtype=np.float32):
+    import paper_0812_4547_gb300 as P
+
+    S = np.asarray(S, dtype=dtype)
+    s = np.asarray(s, dtype=dtype)
+    x, info = ctx.solve(dev_colmajor(S), dev_vec(s))
+    xg = host(x)
+    inf = P.info_dict(info)
+    xo, io = orc.nnls(S, s)
+    return xg, inf, xo, io
+
+
+def check_match(xg, inf, xo, io):
+    assert inf["status"] == io["status"] == 0, (inf, io)
+    assert np.array_equal(xg > 0, xo > 0), (np.nonzero(xg > 0), np.nonzero(xo > 0))
+    den = max(np.linalg.norm(xo), 1e-300)
+    assert np.linalg.norm(xg - xo) / den <= TOL_X
+    assert inf["passive_count"] == io["passive_count"]
+
+
+@pytest.mark.parametrize("m,d,seed", [(50, 1, 0), (200, 5, 1), (300, 15, 2), (1000, 40, 3), (4096, 64, 4),
+                                      (2000, 100, 5), (8192, 128, 6), (4096, 200, 7)])
+def test_random_problems(ctx, orc, m, d, seed):
+    rng = np.random.default_rng(seed)
+    S = rng.standard_normal((m, d))
+    s = rng.standard_normal(m) + S @ np.maximum(rng.standard_normal(d), 0)
+    check_match(*solve_both(ctx, orc, S, s))
+
+
+@pytest.mark.parametrize("d,r", [(16, 512), (64, 4096), (128, 8192)])
+def test_sketch_of_termdoc_workload(ctx, orc, d, r):
+    # the oracle's own sketch of a term-document problem, solved on both sides
+    p = workloads.problem(2, n=1 << 15, d=d, r=r)
+    SA, Sb, _ = orc.sketch(p.A, p.b, r, seed=1)
+    check_match(*solve_both(ctx, orc, SA.astype(np.float32), Sb.astype(np.float32)))
+
+
+def test_interpolation_steps(ctx, orc):
+    # nearly low-rank columns force many interpolation (alpha) steps
+    for seed in range(6):
+        rng = np.random.default_rng(300 + seed)
+        S = rng.standard_normal((40, 3)) @ rng.standard_normal((3, 15)) + 0.1 * rng.standard_normal((40, 15))
+        s = rng.standard_normal(40)
+        xg, inf, xo, io = solve_both(ctx, orc, S, s)
+        check_match(xg, inf, xo, io)
+        assert inf["outer_iters"] == io["outer_iters"]
+        assert inf["inner_iters"] == io["inner_iters"]
+
+
+def test_degenerate(ctx, orc):
+    rng = np.random.default_rng(1)
+    S = rng.random((100, 6))
+    xg, inf, xo, io = solve_both(ctx, orc, S, np.zeros(100))
+    assert np.all(xg == 0) and inf["passive_count"] == 0 and inf["status"] == 0
+    xg, inf, xo, io = solve_both(ctx, orc, S, -S.sum(axis=1))
+    assert np.all(xg == 0)
+    xg, inf, xo, io = solve_both(ctx, orc, S[:, :1], 3 * S[:, 0])
+    assert abs(xg[0] - 3.0) < 1e-6
+
+
+def test_info_fields(ctx, orc):
+    rng = np.random.default_rng(2)
+    S = rng.random((500, 12))
+    s = rng.random(500)
+    xg, inf, xo, io = solve_both(ctx, orc, S, s)
+    S64 = S.astype(np.float32).astype(np.float64)
+    s64 = s.astype(np.float32).astype(np.float64)
+    assert inf["tol"] == pytest.approx(orc.lh_tol(S64, s64), rel=1e-6)
+    obj = np.linalg.norm(S64 @ xo - s64) ** 2
+    assert inf["objective"] == pytest.approx(obj, rel=1e-8)
+    assert inf["dual_max"] <= inf["tol"]
+
+
+def test_fp64_solve(ctx, orc):
+    p = workloads.problem(1)
+    SA, Sb, _ = orc.sketch(p.A, p.b, p.r, seed=0)
+    xg, inf, xo, io = solve_both(ctx, orc, SA, Sb, dtype=np.float64)
+    check_match(xg, inf, xo, io)
+
+
+def test_batched_uneven(ctx, orc):
+    import torch
+
+    import paper_0812_4547_gb300 as P
+
+    rng = np.random.default_rng(3)
+    probs, want = [], []
+    for i, (m, d) in enumerate([(300, 10), (1000, 50), (77, 3), (4096, 120), (512, 64)]):
+        S = rng.standard_normal((m, d)).astype(np.float32)
+        s = (rng.standard_normal(m) + S @ np.maximum(rng.standard_normal(d), 0)).astype(np.float32)
+        x = torch.empty(d, dtype=torch.float64, device="cuda")
+        info = torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device="cuda")
+        probs.append((dev_colmajor(S), dev_vec(s), x, info))
+        want.append(orc.nnls(S, s))
+    ctx.solve_batched(probs)
+    torch.cuda.synchronize()
+    for (SA, Sb, x, info), (xo, io) in zip(probs, want):
+        check_match(host(x), P.info_dict(info), xo, io)
+
+
+def test_residual(ctx, orc):
+    rng = np.random.default_rng(4)
+    A = rng.random((100000, 7)).astype(np.float32)
+    b = rng.random(100000).astype(np.float32)
+    x = rng.random(7)
+    out = ctx.residual(dev_colmajor(A), dev_vec(b), dev_vec(x))
+    assert host(out)[0] == pytest.approx(orc.residual_sq(A, b, x), rel=1e-12)
+
+
+def test_end_to_end_randomized_nnls(ctx, orc):
+    # sketch + solve on device vs the all-FP64 oracle pipeline: the sketch
+    # differs at FP32 rounding, so x~ agrees to the conditioning of the
+    # small problem; the residual ratio of Theorem 1 is compared directly.
+    p = workloads.problem(2, n=1 << 16, d=32, r=2048)
+    x, info, _ = ctx.randomized_nnls(dev_colmajor(p.A), dev_vec(p.b), p.r, seed=5)
+    xg = host(x)
+    xo, io, _ = orc.randomized_nnls(p.A, p.b, p.r, 5)
+    xopt, _ = orc.exact_nnls(p.A, p.b)
+    opt = orc.residual_sq(p.A, p.b, xopt)
+    rg = orc.residual_sq(p.A, p.b, xg) / opt
+    ro = orc.residual_sq(p.A, p.b, xo) / opt
+    assert rg >= 1 - 1e-9
+    assert abs(rg - ro) <= 1e-6 * ro
+    assert np.linalg.norm(xg - xo) <= 1e-3 * np.linalg.norm(xo)
