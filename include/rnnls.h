@@ -172,6 +172,31 @@ typedef struct rnnls_kernel_time {
 int rnnls_profile_begin(rnnls_ctx *ctx, int max_launches);
 int rnnls_profile_end(rnnls_ctx *ctx, rnnls_kernel_time *out, int max_out, int *n_out);
 
+/* rnnls_sketch without any memory allocation (the paper has no counterpart:
+ * this is a deployment convenience).  For callers that cannot call
+ * cudaMalloc when they need a sketch -- a frozen or fully reserved memory
+ * pool, a real-time loop that must not enter the allocator (it may
+ * synchronise the device), a host that only hands out registered buffers.
+ * Computes exactly what rnnls_sketch computes in iid mode (r uniform row
+ * draws, same Philox streams and scale), enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) of the current device.
+ * Inputs and outputs are the caller's, as in rnnls_sketch (idx nullable);
+ * all scratch lives in one 8 MiB array compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ * The first call on a device looks up that device's address of the array
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  Every call shares the array and overwrites
+ * all of the scratch it reads (nothing needs clearing), so calls whose work
+ * overlaps on the GPU (other streams, other threads) race: serialise them.
+ * Limits: 1 <= r <= 16384 (RNNLS_EUNSUPPORTED above), n_raw <= 2^28;
+ * large column counts get fewer chunk groups (less parallelism) so that the
+ * partial sums fit.  Calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Errors: EINVAL (null pointer, bad size or stride),
+ * EUNSUPPORTED (r above the limit), ECUDA. */
+int rnnls_sketch_noalloc(void *stream, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d,
+                         int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa, float *Sb,
+                         int32_t *idx);
+
 /* Human-readable text of a status code (static storage). */
 const char *rnnls_strerror(int status);
 

@@ -30,7 +30,7 @@ RNNLS_SAMPLE_BERNOULLI = 1
 EXPORTS = (
     "rnnls_create", "rnnls_destroy", "rnnls_set_stream", "rnnls_sketch", "rnnls_sketch_f64", "rnnls_solve",
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
-    "rnnls_profile_end",
+    "rnnls_profile_end", "rnnls_sketch_noalloc",
 )
 
 
@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_profile_begin.argtypes = [P, I32]
         L.rnnls_profile_end.argtypes = [P, ctypes.POINTER(rnnls_kernel_time), I32, ctypes.POINTER(I32)]
+        L.rnnls_sketch_noalloc.argtypes = [P, P, I64, P, I64, I64, I64, U64, U64, P, I64, P, P]
         L.rnnls_strerror.argtypes = [I32]
         L.rnnls_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:

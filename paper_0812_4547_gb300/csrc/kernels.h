@@ -55,6 +55,8 @@ struct sketch_args_f32 {
   const int32_t *idx;
 };
 int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms);
+// sketch_f32 with caller-provided scratch (no allocation; see noalloc.cu)
+int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, void *scratch, size_t bytes);
 
 struct sketch_args_f64 {
   const double *A;

@@ -1,0 +1,106 @@
+// noalloc.cu -- a sketch entry point that never allocates memory.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// sketch: code running while a memory pool is frozen or fully reserved by a
+// framework, real-time loops that must not call into the allocator (it can
+// synchronise the device or fail under fragmentation), and hosts that hand
+// out only pre-registered buffers.  rnnls_sketch_noalloc serves them: the
+// caller passes the inputs and outputs, and all scratch space (sampled rows
+// when no idx buffer is given, the combine plan, the per-chunk-range partial
+// sums) comes from one fixed array compiled into this library.
+//
+// The array is a file-scope __device__ variable, so every GPU that loads the
+// library holds kNoAllocScratchBytes of it until the process exits.  Host
+// code cannot use the array's name as a device address; the first call on a
+// device asks the runtime for that device's address (cudaGetSymbolAddress)
+// and remembers it.
+#include <math.h>
+
+#include <mutex>
+
+#include "kernels.h"
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // 8 MiB per device
+constexpr int64_t kNoAllocMaxRows = 16384;                  // largest r accepted
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_setup_mutex;
+void *g_scratch_addr[kMaxDevices];
+int g_num_sms[kMaxDevices];
+
+// Once per device, with that device current: the device address of the
+// scratch array and the SM count.
+int setup_device(int dev, void **addr, int *num_sms) {
+  if (dev < 0 || dev >= kMaxDevices) return RNNLS_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return RNNLS_ECUDA;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return RNNLS_ECUDA;
+    }
+    g_num_sms[dev] = sms;
+    g_scratch_addr[dev] = p;
+  }
+  *addr = g_scratch_addr[dev];
+  *num_sms = g_num_sms[dev];
+  return RNNLS_OK;
+}
+
+}  // namespace
+
+extern "C" int rnnls_sketch_noalloc(void *stream, const float *A, int64_t lda, const float *b, int64_t n_raw,
+                                    int64_t d, int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa,
+                                    float *Sb, int32_t *idx) {
+  using namespace rnnls;
+  if (!A || !b || !SA || !Sb) return RNNLS_EINVAL;
+  if (n_raw < 1 || d < 1 || r < 1 || lda < n_raw || ldsa < r) return RNNLS_EINVAL;
+  if (n_raw > ((int64_t)1 << 28) || d > (1 << 20) || r > kNoAllocMaxRows) return RNNLS_EUNSUPPORTED;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return RNNLS_ECUDA;
+  }
+  void *scratch = nullptr;
+  int num_sms = 0;
+  int st = setup_device(dev, &scratch, &num_sms);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // scratch layout: [sampled rows when idx is null][plan + partial sums]
+  char *base = (char *)scratch;
+  size_t used = 0;
+  int32_t *rows = idx;
+  if (!rows) {
+    rows = (int32_t *)base;
+    used = align_up((size_t)r * sizeof(int32_t), 256);
+  }
+  const int L = log2_ceil64(n_raw);
+  st = launch_sample_iid(s, seed, instance, L, r, rows);
+  if (st) return st;
+  sketch_args_f32 a;
+  a.A = A;
+  a.lda = lda;
+  a.b = b;
+  a.n_raw = n_raw;
+  a.d = (int)d;
+  a.L = L;
+  a.r = r;
+  a.d_count = nullptr;
+  a.seed = seed;
+  a.inst = instance;
+  a.scale = (float)(1.0 / sqrt((double)r));
+  a.SA = SA;
+  a.ldsa = ldsa;
+  a.Sb = Sb;
+  a.idx = rows;
+  return sketch_f32_scratch(s, a, num_sms, base + used, kNoAllocScratchBytes - used);
+}

@@ -446,6 +446,93 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
   return RNNLS_OK;
 }
 
+// Same launches as sketch_f32, but every scratch buffer comes from the
+// caller-provided region `scratch` (bytes long) and nothing is allocated.
+// Chunk groups are capped so that the partial sums fit in that region.
+template <int SLOTS, bool VEC>
+int launch_chunked_stream(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, int groups, int iters,
+                          float *part, int64_t r_part, int direct) {
+  auto kern = sketch_chunked_f32<SLOTS, VEC>;
+  const size_t smem = (size_t)kWorkers * kM * sizeof(float);
+  RNNLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)(a.d + 1), (unsigned)groups, (unsigned)plan.kgroups);
+  kern<<<grid, kThreads, smem, s>>>(a.A, a.lda, a.b, a.n_raw, a.d, iters, a.seed, a.inst, plan.pk, plan.k, plan.cls,
+                                     part, r_part, a.scale, a.SA, a.ldsa, a.Sb, direct);
+  return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
+}
+
+template <int SLOTS>
+int launch_chunked_stream_v(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, int groups, int iters,
+                            float *part, int64_t r_part, int direct, bool vec) {
+  return vec ? launch_chunked_stream<SLOTS, true>(s, a, plan, groups, iters, part, r_part, direct)
+             : launch_chunked_stream<SLOTS, false>(s, a, plan, groups, iters, part, r_part, direct);
+}
+
+int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, void *scratch, size_t bytes) {
+  const int64_t n = (int64_t)1 << a.L;
+  if (n <= 8192) {
+    const size_t smem = (size_t)n * sizeof(float) + (size_t)std::max<int64_t>(n / 64, 4) * sizeof(uint64_t);
+    sketch_small<float><<<(unsigned)(a.d + 1), 256, smem, s>>>(a.A, a.lda, a.b, a.n_raw, a.d, a.L, a.seed, a.inst,
+                                                               a.idx, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
+    return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
+  }
+  const int64_t C = n / kM;
+  const int slots = pick_slots(a.r);
+  const int64_t rows_per_group = (int64_t)kPlanCapacityDen * slots;
+  const int kgroups = (int)((a.r + rows_per_group - 1) / rows_per_group);
+  const bool vec = ((uintptr_t)a.A % 16 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.b % 16 == 0);
+  const size_t plan_bytes = plan_ws_bytes(slots, kgroups);
+  if (plan_bytes + 256 > bytes) return RNNLS_EUNSUPPORTED;
+  const size_t part_one = align_up((size_t)(a.d + 1) * a.r * sizeof(float), 256);
+  const int64_t fit = (int64_t)((bytes - plan_bytes - 256) / part_one);
+  const int per_sm = occupancy_for(slots, vec);
+  const int64_t slots_total = (int64_t)num_sms * per_sm;
+  int groups = 1;
+  double best = -1.0;
+  for (int64_t g = 1; g <= C / 4; g <<= 1) {
+    if (g > 1 && g > fit) break;
+    const int64_t units = (int64_t)(a.d + 1) * g * kgroups;
+    const int64_t waves = (units + slots_total - 1) / slots_total;
+    const double eff = (double)units / (double)(waves * slots_total);
+    const double score = eff - 0.02 * std::log2((double)g);
+    if (score > best + 1e-9) {
+      best = score;
+      groups = (int)g;
+    }
+    if (units >= 8 * slots_total) break;
+  }
+  const int iters = (int)(C / 4 / groups);
+  const int direct = (groups == 1) ? 1 : 0;
+  ws_carver wc(scratch);
+  plan_t plan;
+  plan.pk = wc.take<uint32_t>((size_t)kgroups * slots * kThreads);
+  plan.k = wc.take<int32_t>((size_t)kgroups * slots * kThreads);
+  plan.cls = wc.take<uint32_t>((size_t)kgroups * kThreads);
+  plan.slots = slots;
+  plan.kgroups = kgroups;
+  plan.rows_per_group = rows_per_group;
+  float *part = direct ? nullptr : wc.take<float>((size_t)groups * (a.d + 1) * a.r);
+  int st = launch_build_plan(s, a.idx, a.r, a.d_count, plan, nullptr);
+  if (st) return st;
+  switch (slots) {
+    case 1: st = launch_chunked_stream_v<1>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
+    case 2: st = launch_chunked_stream_v<2>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
+    case 4: st = launch_chunked_stream_v<4>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
+    case 8: st = launch_chunked_stream_v<8>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
+    case 16: st = launch_chunked_stream_v<16>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
+    case 24: st = launch_chunked_stream_v<24>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
+    case 32: st = launch_chunked_stream_v<32>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
+    default: st = launch_chunked_stream_v<40>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
+  }
+  if (st) return st;
+  if (!direct) {
+    dim3 grid((unsigned)std::min<int64_t>((a.r + 255) / 256, 64), (unsigned)(a.d + 1));
+    reduce_partials<float><<<grid, 256, 0, s>>>(part, groups, a.d, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
+    if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
+  }
+  return RNNLS_OK;
+}
+
 int sketch_f64(rnnls_ctx *ctx, const sketch_args_f64 &a) {
   const int64_t n = (int64_t)1 << a.L;
   cudaStream_t s = ctx->stream;
