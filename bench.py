@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="run each step's sketch and solve back to back on one stream")
+    ap.add_argument("--solve-streams", type=int, default=2,
+                    help="solve streams when pipelined (each solve runs in one block)")
     return ap.parse_args()
 
 
@@ -230,22 +234,55 @@ def main():
     b_host = torch.from_numpy(np.asarray(p.b, dtype=dt_np)).pin_memory()
     A = A_host.to(dev).t()
     b = b_host.to(dev)
-    ctx = P.Context(local)
     r = p.r
-    SA = torch.empty((p.d, r), dtype=tdt, device=dev).t()
-    Sb = torch.empty(r, dtype=tdt, device=dev)
-    idx = torch.empty(r, dtype=torch.int32, device=dev)
-    x = torch.empty(p.d, dtype=torch.float64, device=dev)
-    info = torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device=dev)
+    pipeline = not args.no_pipeline
+    # the sketch of step i+1 overlaps the solves of earlier steps: one sketch
+    # stream, `nsolve` solve streams (each solve is one block on one SM),
+    # sketch outputs in nsolve + 1 rotating buffers, ordered by events
+    s_sketch = torch.cuda.current_stream(dev)
+    nsolve = max(1, args.solve_streams) if pipeline else 1
+    s_solves = [torch.cuda.Stream(dev) for _ in range(nsolve)] if pipeline else [s_sketch]
+    ctx = P.Context(local, s_sketch)
+    ctx_vs = [P.Context(local, st) for st in s_solves] if pipeline else [ctx]
+    if pipeline:
+        # one SM per concurrent Lawson-Hanson solve stays free of sketch blocks
+        ctx.set_sketch_sms(torch.cuda.get_device_properties(local).multi_processor_count - nsolve)
+    nbuf = nsolve + 1 if pipeline else 1
+    SAs = [torch.empty((p.d, r), dtype=tdt, device=dev).t() for _ in range(nbuf)]
+    Sbs = [torch.empty(r, dtype=tdt, device=dev) for _ in range(nbuf)]
+    idxs = [torch.empty(r, dtype=torch.int32, device=dev) for _ in range(nbuf)]
+    xs = [torch.empty(p.d, dtype=torch.float64, device=dev) for _ in range(nbuf)]
+    infos = [torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device=dev) for _ in range(nbuf)]
+    sketched = [torch.cuda.Event() for _ in range(nbuf)]
+    solved = [torch.cuda.Event() for _ in range(nbuf)]
+    used = [False] * nbuf
+    SA, Sb, idx, x, info = SAs[0], Sbs[0], idxs[0], xs[0], infos[0]
     x_host = torch.empty(p.d, dtype=torch.float64).pin_memory()
 
     def step(i: int):
-        ctx.sketch(A, b, r, seed=i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
-        ctx.solve(SA, Sb, r=r, x=x, info=info)
+        k = i % nbuf
+        if pipeline and used[k]:
+            s_sketch.wait_event(solved[k])  # the buffer's previous solve has read it
+        ctx.sketch(A, b, r, seed=i, instance=rank, SA=SAs[k], Sb=Sbs[k], idx=idxs[k], want_count=False)
+        cv = ctx_vs[i % nsolve]
+        if pipeline:
+            sketched[k].record(s_sketch)
+            s_solves[i % nsolve].wait_event(sketched[k])
+        cv.solve(SAs[k], Sbs[k], r=r, x=xs[k], info=infos[k])
+        if pipeline:
+            solved[k].record(s_solves[i % nsolve])
+            used[k] = True
 
-    stream = ctx.stream
+    def drain():
+        if pipeline:
+            for k in range(nbuf):
+                if used[k]:
+                    s_sketch.wait_event(solved[k])
+
+    stream = s_sketch
     for i in range(args.warmup):
         step(i)
+    drain()
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -253,6 +290,9 @@ def main():
     clocks.start()
     time.sleep(0.15)
     B.rnnls_profile_begin(ctx.handle, 16 * args.steps + 64)
+    if pipeline:
+        for cv in ctx_vs:
+            B.rnnls_profile_begin(cv.handle, 16 * args.steps + 64)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -260,10 +300,16 @@ def main():
     ev0.record(stream)
     for i in range(args.steps):
         step(args.warmup + i)
+    drain()
     ev1.record(stream)
     torch.cuda.synchronize()
     w1 = time.time()
     prof = B.rnnls_profile_end(ctx.handle)
+    if pipeline:
+        for cv in ctx_vs:
+            for k, v in B.rnnls_profile_end(cv.handle).items():
+                a = prof.get(k, (0, 0.0))
+                prof[k] = (a[0] + v[0], a[1] + v[1])
     clk = clocks.stop(w0, w1)
     ms = ev0.elapsed_time(ev1)
     if ws > 1:
@@ -275,18 +321,23 @@ def main():
     value = ws * args.steps / (ms / 1e3)
 
     # e2e: pinned host inputs copied in and the solution read back every step
+    # (through the same public calls, one stream, no overlap between steps)
+    def seq_step(i: int):
+        ctx.sketch(A, b, r, seed=i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
+        ctx.solve(SA, Sb, r=r, x=x, info=info)
+
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, min(args.steps, 200))
     for i in range(2):
         A.copy_(A_host.t(), non_blocking=True)
         b.copy_(b_host, non_blocking=True)
-        step(i)
+        seq_step(i)
         x_host.copy_(x, non_blocking=True)
         stream.synchronize()
     e0 = time.perf_counter()
     for i in range(e2e_steps):
         A.copy_(A_host.t(), non_blocking=True)
         b.copy_(b_host, non_blocking=True)
-        step(i)
+        seq_step(i)
         x_host.copy_(x, non_blocking=True)
         stream.synchronize()
     e_dt = time.perf_counter() - e0
@@ -300,7 +351,7 @@ def main():
 
     # residual ratio of Theorem 1 (evaluation, off the timed path): x~ for
     # seed 0 vs the exact NNLS on the full A, both solved by the library
-    step(0)
+    seq_step(0)
     x_t = x.clone()
     x_opt, info_opt = ctx.solve(A, b, r=p.n)
     res_t = ctx.residual(A, b, x_t) if not f64 else None
@@ -313,14 +364,16 @@ def main():
 
     # roofline of the dominant kernel (the chunked sketch), timed live with
     # CUDA events on the launching stream during the timed region
-    kname = "sketch_chunked_f32" if "sketch_chunked_f32" in prof else max(prof, key=lambda k: prof[k][1])
+    kname = "sketch_srht_f32" if "sketch_srht_f32" in prof else max(prof, key=lambda k: prof[k][1])
     launches, kms = prof[kname]
     abytes = algorithmic_bytes(p, elt)
     achieved = abytes / (kms / launches / 1e3) / 1e9
     peak, peak_src = measured_hbm_peak()
-    sketch_ms = sum(prof.get(k, (0, 0.0))[1] for k in ("sample_rows", "build_plan", "sketch_chunked_f32",
+    sketch_ms = sum(prof.get(k, (0, 0.0))[1] for k in ("sample_rows", "build_plan", "sketch_srht_f32",
                                                         "reduce_partials", "sketch_small", "sketch_f64"))
     wl = workload_desc(cfg, p)
+    wl["pipeline"] = (f"sketches on one stream overlap solves on {nsolve} streams ({nbuf} sketch buffers)"
+                      if pipeline else "sketch and solve back to back on one stream")
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -342,6 +395,9 @@ def main():
         out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
     elif rank == 0:
         out["cpu_baseline"] = None
+    if pipeline:
+        for cv in ctx_vs:
+            cv.close()
     ctx.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

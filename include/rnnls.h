@@ -101,6 +101,13 @@ int rnnls_destroy(rnnls_ctx *ctx);
 /* Replace the stream the context enqueues on (borrowed). */
 int rnnls_set_stream(rnnls_ctx *ctx, void *stream);
 
+/* Cap the number of SMs the large-n sketch kernel of this context occupies
+ * (one resident block per SM); 0 (the default) means every SM.  Leaving a
+ * few SMs free lets solves enqueued on other streams run beside a sketch
+ * instead of waiting for it.  Results do not depend on the cap.
+ * Errors: EINVAL (ctx null or sms < 0). */
+int rnnls_set_sketch_sms(rnnls_ctx *ctx, int sms);
+
 /* Sketch of Alg. 1 steps 1-4 for FP32 data:
  *   SA[k, j] = s * sum_i H_n[idx[k], i] D_ii A[i, j]   (k < r_out, j < d)
  *   Sb[k]    = s * sum_i H_n[idx[k], i] D_ii b[i]

@@ -83,6 +83,10 @@ class Context:
         self.stream = stream
         B.rnnls_set_stream(self.handle, stream.cuda_stream)
 
+    def set_sketch_sms(self, sms: int) -> None:
+        """Cap the SMs the large-n sketch occupies (0: all), leaving the rest to other streams."""
+        B.rnnls_set_sketch_sms(self.handle, sms)
+
     # -- sketch -------------------------------------------------------------------------
     def sketch(self, A, b, r: int, seed: int, instance: int = 0, mode: int = RNNLS_SAMPLE_IID, SA=None, Sb=None,
                idx=None, cap: int | None = None, want_count: bool = True):

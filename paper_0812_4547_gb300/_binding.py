@@ -30,7 +30,7 @@ RNNLS_SAMPLE_BERNOULLI = 1
 EXPORTS = (
     "rnnls_create", "rnnls_destroy", "rnnls_set_stream", "rnnls_sketch", "rnnls_sketch_f64", "rnnls_solve",
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
-    "rnnls_profile_end", "rnnls_sketch_noalloc",
+    "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms",
 )
 
 
@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_create.argtypes = [ctypes.POINTER(P), I32, P]
         L.rnnls_destroy.argtypes = [P]
         L.rnnls_set_stream.argtypes = [P, P]
+        L.rnnls_set_sketch_sms.argtypes = [P, I32]
         sk = [P, P, I64, P, I64, I64, I64, U64, U64, U32, P, I64, P, P, I64, ctypes.POINTER(I64)]
         L.rnnls_sketch.argtypes = sk
         L.rnnls_sketch_f64.argtypes = sk
@@ -134,6 +135,10 @@ def rnnls_destroy(ctx: int) -> None:
 
 def rnnls_set_stream(ctx: int, stream: int) -> None:
     check(lib().rnnls_set_stream(ctypes.c_void_p(ctx), ctypes.c_void_p(stream)), "rnnls_set_stream")
+
+
+def rnnls_set_sketch_sms(ctx: int, sms: int) -> None:
+    check(lib().rnnls_set_sketch_sms(ctypes.c_void_p(ctx), sms), "rnnls_set_sketch_sms")
 
 
 def _sketch(fn, name, ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA, ldsa, Sb, idx, cap, want_count):

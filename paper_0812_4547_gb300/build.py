@@ -19,6 +19,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build", platform.machine())
 LIB = os.path.join(PKG, "librnnls.so")
+# experiments: extra nvcc flags and an alternative output (never the product library)
+EXTRA = os.environ.get("RNNLS_NVCC_EXTRA", "").split()
+if os.environ.get("RNNLS_BUILD_VARIANT"):
+    BUILD = os.path.join(PKG, "_build", platform.machine() + "-" + os.environ["RNNLS_BUILD_VARIANT"])
+    LIB = os.path.join(BUILD, "librnnls.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -60,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src: str) -> tuple[str, str]:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, "-c", src, "-o", obj] + ARCH + NVCC_FLAGS + extra
+        cmd = [cc, "-c", src, "-o", obj] + ARCH + NVCC_FLAGS + EXTRA + extra
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{res.stderr[-6000:]}")

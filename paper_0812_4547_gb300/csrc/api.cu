@@ -40,6 +40,24 @@ int ensure_aux(rnnls_ctx *ctx, size_t bytes) {
   return RNNLS_OK;
 }
 
+int ensure_counters(rnnls_ctx *ctx, size_t n, unsigned int **out) {
+  if (n > ctx->counters_len) {
+    RNNLS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (ctx->counters) cudaFree(ctx->counters);
+    ctx->counters = nullptr;
+    ctx->counters_len = 0;
+    const size_t want = align_up(n, 1024);
+    if (cudaMalloc(&ctx->counters, want * sizeof(unsigned int)) != cudaSuccess) {
+      cudaGetLastError();
+      return RNNLS_ENOMEM;
+    }
+    RNNLS_CUDA_TRY(cudaMemset(ctx->counters, 0, want * sizeof(unsigned int)));
+    ctx->counters_len = want;
+  }
+  *out = ctx->counters;
+  return RNNLS_OK;
+}
+
 int ensure_pinned(rnnls_ctx *ctx, size_t bytes) {
   // the previous copy out of the staging buffer must be complete
   RNNLS_CUDA_TRY(cudaEventSynchronize(ctx->pinned_ready));
@@ -57,7 +75,7 @@ int ensure_pinned(rnnls_ctx *ctx, size_t bytes) {
 }
 
 const char *kernel_name(int kid) {
-  static const char *names[K_COUNT] = {"sample_rows", "build_plan", "sketch_chunked_f32", "sketch_small",
+  static const char *names[K_COUNT] = {"sample_rows", "build_plan", "sketch_srht_f32", "sketch_small",
                                        "reduce_partials", "sketch_f64", "gram", "gram_reduce", "colabs",
                                        "lawson_hanson", "residual"};
   return (kid >= 0 && kid < K_COUNT) ? names[kid] : "?";
@@ -220,6 +238,7 @@ int rnnls_destroy(rnnls_ctx *ctx) {
   profile_free(ctx);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->aux) cudaFree(ctx->aux);
+  if (ctx->counters) cudaFree(ctx->counters);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   cudaEventDestroy(ctx->pinned_ready);
   delete ctx;
@@ -229,6 +248,12 @@ int rnnls_destroy(rnnls_ctx *ctx) {
 int rnnls_set_stream(rnnls_ctx *ctx, void *stream) {
   if (!ctx) return RNNLS_EINVAL;
   ctx->stream = (cudaStream_t)stream;
+  return RNNLS_OK;
+}
+
+int rnnls_set_sketch_sms(rnnls_ctx *ctx, int sms) {
+  if (!ctx || sms < 0) return RNNLS_EINVAL;
+  ctx->sketch_sms = sms;
   return RNNLS_OK;
 }
 
@@ -246,9 +271,16 @@ int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, in
   if (st) return st;
   int32_t *rows_idx = idx ? idx : av.idx;
   double scale = 0.0;
-  st = sample_rows(ctx, L, r, seed, instance, flags, rows_idx, rows, av, scale);
-  if (st) return st;
+  // iid rows for the large-n path are drawn inside the sketch's plan kernel
+  const bool fused_iid = !bern && ((int64_t)1 << L) > 8192;
+  if (fused_iid) {
+    scale = 1.0 / sqrt((double)r);
+  } else {
+    st = sample_rows(ctx, L, r, seed, instance, flags, rows_idx, rows, av, scale);
+    if (st) return st;
+  }
   sketch_args_f32 a;
+  a.gen_iid = fused_iid ? 1 : 0;
   a.A = A;
   a.lda = lda;
   a.b = b;

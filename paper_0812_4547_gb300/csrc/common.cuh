@@ -166,6 +166,11 @@ __device__ __forceinline__ float flip_if(float v, uint32_t bit) {
   return __int_as_float(__float_as_int(v) ^ (bit << 31));
 }
 
+// Shared-memory word of position p (12 bits) of a 4096-float chunk loaded
+// by a tensor copy with 128-byte swizzling into a 1024-byte aligned buffer:
+// the 16-byte unit (bits 2-4) is XORed with the 128-byte row (bits 5-7).
+__host__ __device__ __forceinline__ uint32_t swz128(uint32_t p) { return p ^ (((p >> 5) & 7u) << 2); }
+
 }  // namespace rnnls
 
 // ---------------------------------------------------------------------------
@@ -175,6 +180,7 @@ struct rnnls_ctx {
   int device;
   cudaStream_t stream;
   int num_sms;
+  int sketch_sms;     // SMs the large-n sketch may occupy (0: all)
   int max_smem_optin;
   void *ws;          // device workspace
   size_t ws_bytes;
@@ -183,6 +189,8 @@ struct rnnls_ctx {
   cudaEvent_t pinned_ready;  // recorded after the last copy out of `pinned`
   void *aux;         // device: sampled rows when the caller passes none, counts
   size_t aux_bytes;
+  unsigned int *counters;  // device: zero-initialised completion counters (reset by their users)
+  size_t counters_len;
   // launch profiling (rnnls_profile_begin / rnnls_profile_end)
   int prof_on;
   int prof_cap;
@@ -198,6 +206,8 @@ int ensure_workspace(rnnls_ctx *ctx, size_t bytes);
 int ensure_pinned(rnnls_ctx *ctx, size_t bytes);
 // Make sure the auxiliary device buffer holds `bytes`.
 int ensure_aux(rnnls_ctx *ctx, size_t bytes);
+// At least `n` zeroed completion counters (kernels leave them at zero).
+int ensure_counters(rnnls_ctx *ctx, size_t n, unsigned int **out);
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Kernels the profiler tells apart.

@@ -23,19 +23,25 @@ constexpr int kLogM = 12;
 constexpr int kM = 1 << kLogM;
 constexpr int kThreads = 256;                 // threads of a sketch block
 constexpr int kWorkers = 4;                   // chunks transformed together
-constexpr int kPlanCapacityDen = kThreads - kWorkers;  // rows per slot bound
+constexpr int kMaxSlots = 40;                 // plan rows per sketch thread
+constexpr int kPlanMaxRows = kThreads * kMaxSlots;  // rows per plan group
 
 struct plan_t {
   uint32_t *pk;   // [kgroups][slots][kThreads]
   int32_t *k;     // [kgroups][slots][kThreads]
-  uint32_t *cls;  // [kgroups][kThreads]: class (h & 3) of each thread's rows
   int slots;
   int kgroups;
   int64_t rows_per_group;
 };
 size_t plan_ws_bytes(int slots, int kgroups);
-int launch_build_plan(cudaStream_t s, const int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
-                      void *ws_sort);
+// When `gen` is set the plan kernel also draws the iid rows into idx; with
+// a sign table it also writes the first sign_words sign words of D.
+struct iid_gen {
+  uint64_t seed, inst;
+  int L;
+};
+int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
+                      const iid_gen *gen, uint64_t *sign_table, int64_t sign_words, uint64_t seed, uint64_t inst);
 
 // ---- sketch (sketch.cu) ------------------------------------------------------
 struct sketch_args_f32 {
@@ -52,7 +58,8 @@ struct sketch_args_f32 {
   float *SA;
   int64_t ldsa;
   float *Sb;
-  const int32_t *idx;
+  int32_t *idx;
+  int gen_iid;  // 1: the sketch draws the iid rows itself (idx is output only)
 };
 int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms);
 // sketch_f32 with caller-provided scratch (no allocation; see noalloc.cu)

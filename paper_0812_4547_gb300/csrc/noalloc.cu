@@ -102,5 +102,6 @@ extern "C" int rnnls_sketch_noalloc(void *stream, const float *A, int64_t lda, c
   a.ldsa = ldsa;
   a.Sb = Sb;
   a.idx = rows;
+  a.gen_iid = 0;
   return sketch_f32_scratch(s, a, num_sms, base + used, kNoAllocScratchBytes - used);
 }

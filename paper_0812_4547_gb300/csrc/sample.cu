@@ -135,127 +135,150 @@ int launch_sample_bernoulli(cudaStream_t s, uint64_t seed, uint64_t inst, int L,
 // ---------------------------------------------------------------------------
 // Combine plan of the large-n sketch.
 //
-// Row i = h * 2^kLogM + l is read from the transformed chunks at position l;
-// chunk c contributes with sign (-1)^popcount(h & c).  A sketch block
-// combines four chunks c0+0..c0+3 at a time, so the factor for those four is
-// (-1)^popcount(h & c0) * (-1)^popcount((h & 3) & w): the second factor is
-// the same for all rows with the same class h & 3.  Rows are therefore
-// grouped by class; class k gets ceil(size_k / slots) threads, which always
-// fits in kThreads when slots >= ceil(rows / (kThreads - 4)).  Within a class
-// rows are sorted by l so that the 32 lanes of a warp read 32 nearby words
-// of shared memory (few bank conflicts).
+// Row i = h * 2^kLogM + l of H_n D X is sum_c (-1)^popcount(h & c) z_c[l],
+// z_c the transformed chunk c.  A sketch block holds four transformed chunks
+// c = 4j + w (w = 0..3) at a time; thread t adds, for each of its rows,
+//   (-1)^popcount((h >> 2) & j) * sum_w (-1)^popcount((h & 3) & w) z_w[l].
+// The loads z_w[l] are shared-memory gathers, so rows are placed to keep
+// the 32 lanes of a warp on 32 different banks: the bank of row i is
+// (word of l) mod 32, and the rows of bank q go to lane q of successive
+// (warp, slot) pairs.  A bank with more than 8 * slots rows spills the rest
+// into free positions of other lanes (one extra shared-memory wavefront
+// each); empty positions read a word of their own bank and write nothing.
 //
-// Entry encoding: pk = (smem word of l) | ((h >> 2) << 12); k = row index in
-// the sketch (-1 for an unused slot).
+// Entry encoding: pk = 4 * (smem word of l) | ((h >> 2) << 14) | ((h & 1) << 31)
+// | (((h >> 1) & 1) << 30), so bits 2-13 are the byte offset of l in a
+// chunk, bit 31 the sign of chunk 4j + 1 and bit 30 that of chunk 4j + 2;
+// k = row index in the sketch (-1: empty).  n <= 2^28 keeps h >> 2 below
+// 2^14.
 // ---------------------------------------------------------------------------
 constexpr int kPlanThreads = 1024;
-constexpr int kBins = 4 * kM;
 
-__device__ __forceinline__ uint32_t smem_word(uint32_t p) {
-  // swizzle used by the sketch kernel's shared-memory chunk buffers
-  return p ^ (((p >> 8) & 7u) << 2);
-}
-
-__global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(const int32_t *__restrict__ idx, int64_t r,
+__global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(int32_t *__restrict__ idx, int64_t r,
                                                                   const int64_t *__restrict__ d_count,
                                                                   uint32_t *__restrict__ plan_pk,
-                                                                  int32_t *__restrict__ plan_k,
-                                                                  uint32_t *__restrict__ plan_cls, int slots,
-                                                                  int64_t rows_per_group) {
-  extern __shared__ uint32_t hist[];  // kBins
-  __shared__ uint32_t cls_size[4], cls_start[4], t_count[4], t_start[4];
+                                                                  int32_t *__restrict__ plan_k, int slots,
+                                                                  int64_t rows_per_group, int gen_iid, uint64_t seed,
+                                                                  uint64_t inst, int L, uint64_t *__restrict__ sign_table,
+                                                                  int64_t sign_words) {
+  __shared__ uint16_t rank_of[kPlanMaxRows];
+  __shared__ uint32_t wcnt[kPlanThreads / 32][33];
+  __shared__ uint32_t cnt[32], ov_start[32], free_start[32];
   const int g = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (g >= (int)gridDim.x - (int)((sign_words / 4 + kPlanThreads - 1) / kPlanThreads)) {
+    // sign words of D: word W is word W % 4 of Philox block W / 4 of stream 0
+    const int64_t first = (int64_t)(g - ((int)gridDim.x - (int)((sign_words / 4 + kPlanThreads - 1) / kPlanThreads)));
+    const int64_t blk = first * kPlanThreads + tid;
+    if (4 * blk < sign_words) {
+      const u64x4 u = philox4x64_10((uint64_t)blk, kStreamSigns, seed, inst);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sign_table[4 * blk + q] = u.w[q];
+    }
+    return;
+  }
   int64_t rr = r;
   if (d_count) rr = min(r, *d_count);
   const int64_t k0 = (int64_t)g * rows_per_group;
   const int64_t k1 = min(rr, k0 + rows_per_group);
   uint32_t *pk_out = plan_pk + (size_t)g * slots * kThreads;
   int32_t *k_out = plan_k + (size_t)g * slots * kThreads;
+  const uint32_t cap = 8u * (uint32_t)slots;  // rows per bank without spilling
 
-  for (int i = threadIdx.x; i < kBins; i += kPlanThreads) hist[i] = 0;
-  for (int e = threadIdx.x; e < slots * kThreads; e += kPlanThreads) {
-    pk_out[e] = 0;
+  for (int e = tid; e < slots * kThreads; e += kPlanThreads) {
+    pk_out[e] = (uint32_t)(e & 31) << 2;
     k_out[e] = -1;
   }
-  if (threadIdx.x < 4) cls_size[threadIdx.x] = 0;
+  if (gen_iid) {
+    // the iid rows of this group: draw k is word k of stream 2 (k0 is a multiple of 4)
+    for (int64_t j = k0 / 4 + tid; 4 * j < k1; j += kPlanThreads) {
+      const u64x4 u = philox4x64_10((uint64_t)j, kStreamIid, seed, inst);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int64_t k = 4 * j + w;
+        if (k < k1) idx[k] = (L == 0) ? 0 : (int32_t)(u.w[w] >> (64 - L));
+      }
+    }
+  }
   __syncthreads();
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += kPlanThreads) {
+  // 1. rank of each row within its bank, in row order (stable)
+  uint32_t seen = 0;  // thread q < 32: rows of bank q in earlier tiles
+  for (int64_t t0 = k0; t0 < k1; t0 += kPlanThreads) {
+    const int64_t k = t0 + tid;
+    const bool valid = k < k1;
+    const uint32_t bank = valid ? (swz128((uint32_t)idx[k] & (kM - 1)) & 31u) : 32u;
+    const uint32_t same = __match_any_sync(0xffffffffu, bank);
+    const uint32_t below = __popc(same & ((1u << lane) - 1u));
+    wcnt[warp][lane] = 0;
+    __syncwarp();
+    if (valid && below == 0) wcnt[warp][bank] = __popc(same);
+    __syncthreads();
+    if (tid < 32) {
+      uint32_t run = seen;
+      for (int q = 0; q < kPlanThreads / 32; ++q) {
+        const uint32_t c = wcnt[q][tid];
+        wcnt[q][tid] = run;
+        run += c;
+      }
+      seen = run;
+    }
+    __syncthreads();
+    if (valid) rank_of[k - k0] = (uint16_t)(wcnt[warp][bank] + below);
+    __syncthreads();
+  }
+  if (tid < 32) cnt[tid] = seen;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t ov = 0, fr = 0;
+    for (int q = 0; q < 32; ++q) {
+      ov_start[q] = ov;
+      free_start[q] = fr;
+      ov += cnt[q] > cap ? cnt[q] - cap : 0u;
+      fr += cnt[q] < cap ? cap - cnt[q] : 0u;
+    }
+  }
+  __syncthreads();
+  // 2. place: rank t of bank q -> lane q of (warp t % 8, slot t / 8); spilled
+  //    rows fill the free positions of the banks in bank order
+  for (int64_t k = k0 + tid; k < k1; k += kPlanThreads) {
     const uint32_t i = (uint32_t)idx[k];
     const uint32_t l = i & (kM - 1), h = i >> kLogM;
-    atomicAdd(&hist[(h & 3u) * kM + l], 1u);
-    atomicAdd(&cls_size[h & 3u], 1u);
-  }
-  __syncthreads();
-  // exclusive scan of the histogram: each thread owns kBins/kPlanThreads bins
-  {
-    constexpr int per = kBins / kPlanThreads;
-    uint32_t local[per];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-      local[q] = hist[threadIdx.x * per + q];
-      sum += local[q];
+    const uint32_t wd = swz128(l);
+    const uint32_t bank = wd & 31u;
+    const uint32_t rank = rank_of[k - k0];
+    uint32_t q = bank, pos = rank;
+    if (rank >= cap) {
+      const uint32_t e = ov_start[bank] + (rank - cap);
+      for (uint32_t b2 = 0; b2 < 32; ++b2) {
+        const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
+        if (e >= free_start[b2] && e < free_start[b2] + f) {
+          q = b2;
+          pos = cnt[b2] + (e - free_start[b2]);
+        }
+      }
     }
-    typedef cub::BlockScan<uint32_t, kPlanThreads> scan_t;
-    __shared__ typename scan_t::TempStorage tmp;
-    uint32_t ex;
-    scan_t(tmp).ExclusiveSum(sum, ex);
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-      hist[threadIdx.x * per + q] = ex;
-      ex += local[q];
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t ts = 0;
-    for (int c = 0; c < 4; ++c) {
-      cls_start[c] = hist[c * kM];
-      const uint32_t tc = (cls_size[c] + (uint32_t)slots - 1u) / (uint32_t)slots;
-      t_count[c] = tc;
-      t_start[c] = ts;
-      ts += tc;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < kThreads) {
-    uint32_t c = 0;
-    for (uint32_t q = 0; q < 4; ++q)
-      if (threadIdx.x >= t_start[q] && threadIdx.x < t_start[q] + t_count[q]) c = q;
-    plan_cls[(size_t)g * kThreads + threadIdx.x] = c;
-  }
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += kPlanThreads) {
-    const uint32_t i = (uint32_t)idx[k];
-    const uint32_t l = i & (kM - 1), h = i >> kLogM, c = h & 3u;
-    const uint32_t pos = atomicAdd(&hist[c * kM + l], 1u);
-    const uint32_t u = pos - cls_start[c];
-    const uint32_t thread = t_start[c] + u % t_count[c];
-    const uint32_t slot = u / t_count[c];
-    pk_out[(size_t)slot * kThreads + thread] = smem_word(l) | ((h >> 2) << kLogM);
+    if (pos >= cap) continue;  // unreachable: the free positions outnumber the spilled rows
+    const uint32_t thread = (pos & 7u) * 32u + q;
+    const uint32_t slot = pos >> 3;
+    pk_out[(size_t)slot * kThreads + thread] = (wd << 2) | ((h >> 2) << 14) | ((h & 1u) << 31) | (((h >> 1) & 1u) << 30);
     k_out[(size_t)slot * kThreads + thread] = (int32_t)k;
   }
 }
 
 size_t plan_ws_bytes(int slots, int kgroups) {
   const size_t e = (size_t)kgroups * slots * kThreads;
-  return align_up(e * sizeof(uint32_t), 256) + align_up(e * sizeof(int32_t), 256) +
-         align_up((size_t)kgroups * kThreads * sizeof(uint32_t), 256);
+  return align_up(e * sizeof(uint32_t), 256) + align_up(e * sizeof(int32_t), 256);
 }
 
-int launch_build_plan(cudaStream_t s, const int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
-                      void *ws_sort) {
-  (void)ws_sort;
-  const size_t smem = kBins * sizeof(uint32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(build_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return RNNLS_ECUDA;
-    attr_set = true;
-  }
-  build_plan_kernel<<<plan.kgroups, kPlanThreads, smem, s>>>(idx, r, d_count, plan.pk, plan.k, plan.cls,
-                                                              plan.slots, plan.rows_per_group);
+int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
+                      const iid_gen *gen, uint64_t *sign_table, int64_t sign_words, uint64_t seed, uint64_t inst) {
+  if (plan.rows_per_group > kPlanMaxRows || plan.rows_per_group > (int64_t)plan.slots * kThreads)
+    return RNNLS_EUNSUPPORTED;
+  if (!sign_table) sign_words = 0;
+  const int64_t sign_blocks = (sign_words / 4 + kPlanThreads - 1) / kPlanThreads;
+  build_plan_kernel<<<(unsigned)(plan.kgroups + sign_blocks), kPlanThreads, 0, s>>>(
+      idx, r, d_count, plan.pk, plan.k, plan.slots, plan.rows_per_group, gen ? 1 : 0, seed, inst, gen ? gen->L : 0,
+      sign_table, sign_words);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 

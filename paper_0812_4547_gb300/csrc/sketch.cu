@@ -5,23 +5,30 @@
 //
 // Large n (n >= 2^14): H_n = H_C (x) H_m with m = 2^12 and C = n/m, row
 // i = h*m + l.  Then (H_n y)[i] = sum_c (-1)^popcount(h & c) (H_m y_c)[l] for
-// the chunks y_c of y.  One block owns a column and a range of 4*NI chunks:
-//   - it reads each chunk once from HBM (coalesced 16-byte loads),
-//   - flips signs with D (Philox bits regenerated in the block),
-//   - transforms the chunk with two 64-point register FWHT passes joined by
-//     one swizzled shared-memory transpose (four chunks at a time, one per
-//     64-thread worker),
-//   - and accumulates, for the sampled rows only, the signed chunk values
-//     into per-row registers (the "combine"; the signs for the chunks of one
-//     step factor into a per-thread part and a per-row part that is tracked
-//     by visiting the steps in Gray-code order).
-// Only r values per column leave the block, so HBM sees one read of X plus
-// r*(d+1) partial sums per chunk range.
+// the chunks y_c of y.  The work is a list of steps, one per column and
+// group j of four chunks c = 4j..4j+3 that hold data; a persistent grid of
+// one 256-thread block per SM walks equal contiguous stretches of that list:
+//   - bulk asynchronous copies (cp.async.bulk, completion on an mbarrier)
+//     bring the four chunks of a step into shared memory two steps ahead
+//     (three stage buffers), so HBM reads never wait on compute,
+//   - each 64-thread worker flips its chunk's signs with D (Philox words made
+//     one step ahead), transforms it with two 64-point register FWHT passes
+//     joined by one swizzled transpose, in place in its stage buffer,
+//   - and every thread adds, for the sampled rows it owns (the plan, kept in
+//     registers), the four signed chunk values into per-row registers.
+// A column handled by several blocks leaves one partial-sum vector per
+// block; the last of them to finish adds them in block order.  HBM sees one
+// read of X plus, per split column, a few r-vectors.
 //
 // Small n (n <= 2^13): one block per column transforms the whole column in
 // shared memory and gathers the sampled rows.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
+
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -29,182 +36,398 @@ namespace rnnls {
 
 namespace {
 
-__device__ __forceinline__ uint32_t zword(uint32_t p) { return p ^ (((p >> 8) & 7u) << 2); }
+constexpr int kStages = 3;                                   // stage buffers (steps in flight + 1)
+constexpr int kStageFloats = kWorkers * kM;                  // one step: four chunks
+// stage buffers plus slack to place them at a 16 KiB boundary
+constexpr size_t kSketchSmem = (size_t)kStages * kStageFloats * sizeof(float) + 16384;  // 208 KiB
+constexpr uint32_t kSpinLimit = 1u << 22;                    // bounded wait on a bulk copy
 
 __device__ __forceinline__ void bar_worker(int w) {
   asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long r, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+
 // In-register unnormalised Walsh-Hadamard transform of 64 values,
-// v[i] <- sum_j (-1)^popcount(i & j) v[j].
+// v[i] <- sum_j (-1)^popcount(i & j) v[j]; strides >= 2 use packed f32x2
+// butterflies (same roundings as scalar ones).
 __device__ __forceinline__ void fwht64(float (&v)[64]) {
 #pragma unroll
-  for (int h = 1; h < 64; h <<= 1) {
+  for (int i = 0; i < 64; i += 2) {
+    const float a = v[i], b = v[i + 1];
+    v[i] = a + b;
+    v[i + 1] = a - b;
+  }
 #pragma unroll
-    for (int i = 0; i < 64; ++i) {
+  for (int h = 2; h < 64; h <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 64; i += 2) {
       if ((i & h) == 0) {
-        const float a = v[i], b = v[i + h];
-        v[i] = a + b;
-        v[i + h] = a - b;
+        const unsigned long long x = pack2(v[i], v[i + 1]);
+        const unsigned long long y = pack2(v[i + h], v[i + h + 1]);
+        unsigned long long su, df;
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(su) : "l"(x), "l"(y));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(x), "l"(y));
+        unpack2(su, v[i], v[i + 1]);
+        unpack2(df, v[i + h], v[i + h + 1]);
       }
     }
   }
 }
 
-__device__ __forceinline__ uint32_t gray(uint32_t i) { return i ^ (i >> 1); }
+__device__ __forceinline__ float xor_sign(float v, uint32_t m) { return __int_as_float(__float_as_int(v) ^ (int)m); }
 
-template <int SLOTS, bool VEC>
+// ---- mbarrier and tensor-copy primitives (PTX) -------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ uint64_t mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;" : "=l"(state) : "r"(bar), "r"(bytes) : "memory");
+  return state;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// tiled tensor copy global -> shared of box (32, 128, 1) at (0, y, z); the
+// innermost coordinate is 0, so the 16-byte alignment rule always holds
+__device__ __forceinline__ void tma_load_chunk(uint32_t dst, const CUtensorMap *map, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// order this thread's earlier generic-proxy shared accesses before later async-proxy ones
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// the four chunks' words at byte offset `a` of a step's buffer
+__device__ __forceinline__ void lds_x4(uint32_t a, float &z0, float &z1, float &z2, float &z3) {
+  asm volatile(
+      "ld.shared.f32 %0, [%4];\n\tld.shared.f32 %1, [%4+16384];\n\tld.shared.f32 %2, [%4+32768];\n\tld.shared.f32 %3, "
+      "[%4+49152];"
+      : "=f"(z0), "=f"(z1), "=f"(z2), "=f"(z3)
+      : "r"(a));
+}
+
+// Partition of the step list over the blocks.  Unit u = kg * (d + 1) + col
+// (plan group kg, column col) owns steps u*J .. u*J + J - 1.  Balanced:
+// block b takes steps [T b / B, T (b+1) / B).  Aligned: block b takes the
+// whole units [U b / B, U (b+1) / B) (no column is split).
+struct srht_part {
+  int64_t J;    // chunk groups with data per column: ceil(n_raw / 4m)
+  int64_t U;    // units
+  int64_t T;    // steps = U * J
+  int aligned;
+};
+
+__host__ __device__ __forceinline__ int64_t part_start(int64_t b, int64_t B, const srht_part &P) {
+  return P.aligned ? P.J * ((P.U * b) / B) : (P.T * b) / B;
+}
+// block holding step s (balanced partition)
+__host__ __device__ __forceinline__ int64_t part_block_of(int64_t s, int64_t B, const srht_part &P) {
+  return ((s + 1) * B - 1) / P.T;
+}
+
+// position of a step in the unit list, advanced without divisions
+struct step_cursor {
+  int64_t u, j, kg;
+  int col;
+  __device__ void init(int64_t s, const srht_part &P, int64_t D1) {
+    u = s / P.J;
+    j = s - u * P.J;
+    kg = u / D1;
+    col = (int)(u - kg * D1);
+  }
+  __device__ void next(const srht_part &P, int64_t D1) {
+    if (++j == P.J) {
+      j = 0;
+      ++u;
+      if (++col == D1) {
+        col = 0;
+        ++kg;
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The large-n sketch kernel (FP32).  Plan group kg's rows are entries
+// [kg][slot][thread] of plan_pk / plan_k (see the plan kernel).
+// tmA / tmB: column views (32, n_raw / 32, cols) of A and b for the tensor
+// copies (vec = 1); with vec = 0 the threads load X with plain loads.
+// part: [segment][unit][rows_per_group] partial sums of split units;
+// counters: one per unit, zero before and after the launch.
+//
+// Chunk layout in shared memory: position p at word swz128(p) of its 16 KiB
+// slot (the tensor copy's 128-byte swizzle).  Pass 1: thread t of a worker
+// holds rows t and t + 64 of 32 positions (bits 0-4 and 11 of p in its
+// registers); pass 2: lane l, warp h of the worker holds the 64 positions
+// with bits 0-4 = l and bit 11 = h.  Both passes read and write back the
+// same words, so only pass 2 has to wait for the other threads of the worker.
+// ---------------------------------------------------------------------------
+template <int SLOTS>
 __global__ void __launch_bounds__(kThreads, 1)
-    sketch_chunked_f32(const float *__restrict__ A, int64_t lda, const float *__restrict__ b, int64_t n_raw, int d,
-                       int iters, uint64_t seed, uint64_t inst, const uint32_t *__restrict__ plan_pk,
-                       const int32_t *__restrict__ plan_k, const uint32_t *__restrict__ plan_cls,
-                       float *__restrict__ part, int64_t r_part, float scale, float *__restrict__ SA, int64_t ldsa,
-                       float *__restrict__ Sb, int direct) {
-  extern __shared__ __align__(16) float zbuf[];  // kWorkers x kM floats
-  __shared__ uint64_t sgn[kWorkers][kM / 64];
+    sketch_srht_f32(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const float *__restrict__ A, int64_t lda, const float *__restrict__ b, int64_t n_raw, int d,
+                    srht_part P, int vec, uint64_t seed, uint64_t inst, const uint64_t *__restrict__ sign_table,
+                    const uint32_t *__restrict__ plan_pk,
+                    const int32_t *__restrict__ plan_k, int64_t rpg, float *__restrict__ part, float scale,
+                    float *__restrict__ SA, int64_t ldsa, float *__restrict__ Sb, unsigned int *__restrict__ counters) {
+  extern __shared__ __align__(1024) float dyn_smem[];  // kStages x kWorkers x kM (+ alignment slack)
+  __shared__ __align__(16) uint32_t sgn[kStages][kWorkers][kM / 32];  // D's bits, 32-bit halves of the words
+  __shared__ __align__(8) uint64_t mbar[kStages];
+  __shared__ unsigned int last_flag;
+  __shared__ int stalled;  // a tensor copy did not land within the wait limit
 
   const int tid = threadIdx.x;
-  const int w = tid >> 6;   // worker
+  const int w = tid >> 6;   // worker: chunk 4j + w of a step
   const int wt = tid & 63;  // thread within worker
-  const int col = blockIdx.x;
-  const int grp = blockIdx.y;
-  const int kg = blockIdx.z;
-  const float *__restrict__ x = (col < d) ? A + (int64_t)col * lda : b;
-  const uint32_t c0 = (uint32_t)grp * 4u * (uint32_t)iters;
+  const int64_t B = gridDim.x;
+  const int64_t bid = blockIdx.x;
+  const int64_t s0 = part_start(bid, B, P);
+  const int64_t nsteps = part_start(bid + 1, B, P) - s0;
+  if (nsteps <= 0) return;
+  const int64_t D1 = (int64_t)d + 1;
+  // stage buffers at a 16 KiB boundary: chunk slots are then addressed by OR
+  const uint32_t raw_u32 = smem_u32(dyn_smem);
+  const uint32_t stage_u32 = (raw_u32 + 16383u) & ~16383u;
+  float *stage = dyn_smem + (stage_u32 - raw_u32) / 4;
+  const int64_t nrow32 = n_raw >> 5;  // whole 32-row lines of a column
 
-  // combine state: this thread's rows (plan) and their partial sums
-  const size_t pbase = (size_t)kg * SLOTS * kThreads;
+  if (tid == 0) {
+    for (int q = 0; q < kStages; ++q) mbar_init(smem_u32(&mbar[q]), 1);
+    fence_mbar_init();
+    stalled = 0;
+  }
+  __syncthreads();
+
+  // thread 0: tensor copies of one step (4 chunks = 4 boxes of 32 x 128)
+  step_cursor ic;
+  ic.init(s0, P, D1);
+  int iq = 0;
+  auto issue = [&]() {
+    const uint32_t bar = smem_u32(&mbar[iq]);
+    mbar_arrive_expect_tx(bar, (uint32_t)(kWorkers * kM * sizeof(float)) + (sign_table ? 2048u : 0u));
+    if (sign_table) bulk_g2s(smem_u32(&sgn[iq][0][0]), sign_table + 4 * ic.j * (kM / 64), 2048u, bar);
+    const CUtensorMap *map = (ic.col < d) ? &tmA : &tmB;
+    const int z = (ic.col < d) ? ic.col : 0;
+#pragma unroll
+    for (int c = 0; c < kWorkers; ++c)
+      tma_load_chunk(stage_u32 + (uint32_t)(iq * kStageFloats + c * kM) * 4u, map, (int)((4 * ic.j + c) * (kM / 32)),
+                     z, bar);
+    ic.next(P, D1);
+    iq = (iq + 1 == kStages) ? 0 : iq + 1;
+  };
+  // sign words of this worker's chunk of a step: 64-bit word i of the chunk
+  // is Philox block 16c + i/4 (stream 0), word i % 4; stored as 32-bit halves
+  // (without tensor copies: from the table with plain loads, or from Philox)
+  auto make_signs = [&](int64_t j, int buf) {
+    if (sign_table) {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(sign_table + 4 * j * (kM / 64));
+      for (int i = tid; i < kWorkers * (kM / 32); i += kThreads) (&sgn[buf][0][0])[i] = src[i];
+    } else if (wt < 16) {
+      const uint64_t c = (uint64_t)(4 * j + w);
+      const u64x4 r4 = philox4x64_10(c * 16u + (uint64_t)wt, kStreamSigns, seed, inst);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        sgn[buf][w][8 * wt + 2 * q] = (uint32_t)r4.w[q];
+        sgn[buf][w][8 * wt + 2 * q + 1] = (uint32_t)(r4.w[q] >> 32);
+      }
+    }
+  };
+
+  if (vec && tid == 0) {
+    issue();
+    if (nsteps > 1) issue();
+  }
+  step_cursor cur;
+  cur.init(s0, P, D1);
+  const bool signs_by_copy = vec && sign_table;
+  if (!signs_by_copy) make_signs(cur.j, 0);
+
   uint32_t pk[SLOTS];
   float acc[SLOTS];
 #pragma unroll
-  for (int s = 0; s < SLOTS; ++s) {
-    pk[s] = plan_pk[pbase + (size_t)s * kThreads + tid];
-    acc[s] = 0.0f;
-  }
-  const uint32_t cls = plan_cls[(size_t)kg * kThreads + tid];
-  const float s1 = (cls & 1u) ? -1.0f : 1.0f;
-  const float s2 = (cls & 2u) ? -1.0f : 1.0f;
-  const float s3 = s1 * s2;
-  float *__restrict__ zw = zbuf + w * kM;
+  for (int s = 0; s < SLOTS; ++s) acc[s] = 0.0f;
+  int64_t kg_loaded = -1;
+  int q = 0;
+  uint32_t phase = 0;
 
-  for (int it = 0; it < iters; ++it) {
-    const uint32_t cbase = c0 + 4u * gray((uint32_t)it);
-    const uint32_t c = cbase + (uint32_t)w;
-    const int64_t row0 = (int64_t)c * kM;
+  for (int64_t ls = 0; ls < nsteps; ++ls) {
+    const int64_t j = cur.j;
+    const int col = cur.col;
+    if (cur.kg != kg_loaded) {
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) pk[s] = plan_pk[((size_t)cur.kg * SLOTS + s) * kThreads + tid];
+      kg_loaded = cur.kg;
+    }
+    float *__restrict__ zw = stage + q * kStageFloats + w * kM;
+    const uint32_t step_u32 = stage_u32 + (uint32_t)(q * kStageFloats) * 4u;
+    __syncthreads();  // step ls-1 is done with its buffer; this step's signs are visible
+    if (vec) {
+      if (tid == 0 && ls + 2 < nsteps) {
+        fence_proxy_async();
+        issue();
+      }
+      const uint32_t bar = smem_u32(&mbar[q]);
+      const uint32_t limit = *(volatile int *)&stalled ? 64u : kSpinLimit;
+      bool ok = false;
+      for (uint32_t it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, phase);
+      if (!ok) *(volatile int *)&stalled = 1;
+    }
+    // lines of this thread's two rows that the tensor copy does not cover
+    // (all of them without tensor copies, else the partial last line)
+    {
+      const float *x = (col < d) ? A + (int64_t)col * lda : b;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t line = (4 * j + w) * (int64_t)(kM / 32) + 64 * h + wt;
+        if (!vec || line == nrow32) {
+          for (int e = 0; e < 32; ++e) {
+            const int64_t row = 32 * line + e;
+            zw[swz128((uint32_t)((h << 11) | (wt << 5) | e))] = (row < n_raw) ? x[row] : 0.0f;
+          }
+        }
+      }
+    }
 
-    // 1. load this worker's chunk: v[4q + e] <- x[row0 + 4*wt + 256*q + e]
+    // pass 1 (bits 0-4, 11): v[32 h + 4 g + e] <- position (h<<11)|(wt<<5)|(4g+e), D applied
     float v[64];
-    if (row0 + kM <= n_raw) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int64_t row = row0 + 4 * wt + 256 * q;
-        if (VEC) {
-          const float4 t = __ldcs(reinterpret_cast<const float4 *>(x + row));
-          v[4 * q + 0] = t.x;
-          v[4 * q + 1] = t.y;
-          v[4 * q + 2] = t.z;
-          v[4 * q + 3] = t.w;
-        } else {
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t sw = sgn[q][w][2 * ((h << 5) | (wt >> 1)) + (wt & 1)];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) v[4 * q + e] = __ldcs(x + row + e);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int64_t row = row0 + 4 * wt + 256 * q + e;
-          v[4 * q + e] = (row < n_raw) ? __ldcs(x + row) : 0.0f;
-        }
+      for (int g = 0; g < 8; ++g) {
+        const float4 t =
+            *reinterpret_cast<const float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2)));
+        v[32 * h + 4 * g + 0] = xor_sign(t.x, (sw << (31 - (4 * g + 0))) & 0x80000000u);
+        v[32 * h + 4 * g + 1] = xor_sign(t.y, (sw << (31 - (4 * g + 1))) & 0x80000000u);
+        v[32 * h + 4 * g + 2] = xor_sign(t.z, (sw << (31 - (4 * g + 2))) & 0x80000000u);
+        v[32 * h + 4 * g + 3] = xor_sign(t.w, (sw << (31 - (4 * g + 3))) & 0x80000000u);
       }
     }
-
-    // 2. the 64 sign words of this chunk: Philox block j = 16c + wt, stream 0
-    if (wt < 16) {
-      const u64x4 u = philox4x64_10((uint64_t)c * 16u + (uint64_t)wt, kStreamSigns, seed, inst);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) sgn[w][4 * wt + q] = u.w[q];
-    }
-    __syncthreads();  // signs visible; previous combine done with zbuf
-
-    // 3. D: row 4*wt + 256*q + e uses bit (4*wt + e) mod 64 of word wt/16 + 4q
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const uint64_t word = sgn[w][(wt >> 4) + 4 * q];
-      const uint32_t nib = (uint32_t)(word >> ((4 * wt) & 63)) & 0xFu;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) v[4 * q + e] = flip_if(v[4 * q + e], (nib >> e) & 1u);
-    }
-
-    // 4. pass 1: position bits {0,1,8,9,10,11} live in the register index
     fwht64(v);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const uint32_t p = 4u * wt + 256u * q;
-      *reinterpret_cast<float4 *>(zw + zword(p)) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        *reinterpret_cast<float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2))) =
+            make_float4(v[32 * h + 4 * g], v[32 * h + 4 * g + 1], v[32 * h + 4 * g + 2], v[32 * h + 4 * g + 3]);
+    bar_worker(w);
+    // pass 2 (bits 5-10): v[s] <- position ((wt>>5)<<11) | (s<<5) | (wt & 31)
+    {
+      const uint32_t lane = (uint32_t)(wt & 31), hi = (uint32_t)(wt >> 5) << 11;
+#pragma unroll
+      for (int s = 0; s < 64; ++s) v[s] = zw[hi | ((uint32_t)s << 5) | (lane ^ (((uint32_t)s & 7u) << 2))];
+      fwht64(v);
+#pragma unroll
+      for (int s = 0; s < 64; ++s) zw[hi | ((uint32_t)s << 5) | (lane ^ (((uint32_t)s & 7u) << 2))] = v[s];
     }
-    bar_worker(w);
-    // 5. pass 2: position bits {2..7}
-    const uint32_t pfix = (wt & 3u) | ((uint32_t)(wt >> 2) << 8);
-#pragma unroll
-    for (int s = 0; s < 64; ++s) v[s] = zw[zword(pfix | ((uint32_t)s << 2))];
-    fwht64(v);
-    bar_worker(w);
-#pragma unroll
-    for (int s = 0; s < 64; ++s) zw[zword(pfix | ((uint32_t)s << 2))] = v[s];
     __syncthreads();  // the four transformed chunks are ready
 
-    // 6. combine at the sampled rows
-    const uint32_t beta = (it == 0) ? 0u : (uint32_t)(__ffs(it) - 1);
+    // combine: row (hq, c1, c2) adds (-1)^popcount(hq & j) (z0 + s1 z1 + s2 (z2 + s1 z3))[l]
+    const uint32_t jm = (uint32_t)j << 14;
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       const uint32_t p = pk[s];
-      float a = acc[s];
-      if (it > 0) a = flip_if(a, (p >> (kLogM + beta)) & 1u);
-      const uint32_t wd = p & (kM - 1);
-      float t = zbuf[wd];
-      t = fmaf(s1, zbuf[kM + wd], t);
-      t = fmaf(s2, zbuf[2 * kM + wd], t);
-      t = fmaf(s3, zbuf[3 * kM + wd], t);
-      acc[s] = a + t;
+      float z0, z1, z2, z3;
+      lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+      const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
+      const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
+      const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
+      acc[s] += xor_sign(t, (uint32_t)__popc(p & jm) << 31);
     }
-  }
+    cur.next(P, D1);
+    if (++q == kStages) {
+      q = 0;
+      phase ^= 1u;
+    }
+    if (!signs_by_copy && ls + 1 < nsteps) make_signs(cur.j, q);
 
-  // 7. undo the running sign: row factor (-1)^popcount(h & (c0 | 4 gray(iters-1)))
-  const uint32_t cmask = c0 | (4u * gray((uint32_t)(iters - 1)));
+    // end of this block's part of unit u: write or hand over the sums
+    if (j == P.J - 1 || ls == nsteps - 1) {
+      const int64_t u = cur.u - ((j == P.J - 1) ? 1 : 0);  // cursor already moved on
+      const int64_t kg = kg_loaded;
+      const bool poisoned = *(volatile int *)&stalled != 0;
+      int64_t first = bid, last = bid;
+      if (!P.aligned) {
+        first = part_block_of(u * P.J, B, P);
+        last = part_block_of(u * P.J + P.J - 1, B, P);
+      }
+      const int64_t kbase = kg * rpg;
+      if (first == last) {
 #pragma unroll
-  for (int s = 0; s < SLOTS; ++s) {
-    const int32_t k = plan_k[pbase + (size_t)s * kThreads + tid];
-    if (k < 0) continue;
-    const uint32_t h = ((pk[s] >> kLogM) << 2) | cls;
-    const float val = flip_if(acc[s], (uint32_t)__popc(h & cmask) & 1u);
-    if (direct) {
-      if (col < d)
-        SA[(int64_t)col * ldsa + k] = scale * val;
-      else
-        Sb[k] = scale * val;
-    } else {
-      part[((int64_t)grp * (d + 1) + col) * r_part + k] = val;
+        for (int s = 0; s < SLOTS; ++s) {
+          const int32_t k = plan_k[((size_t)kg * SLOTS + s) * kThreads + tid];
+          if (k < 0) continue;
+          const float val = poisoned ? __int_as_float(0x7fc00000) : scale * acc[s];
+          if (col < d)
+            SA[(int64_t)col * ldsa + k] = val;
+          else
+            Sb[k] = val;
+        }
+      } else {
+        const int64_t nseg = last - first + 1;
+        const int64_t seg = bid - first;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          const int32_t k = plan_k[((size_t)kg * SLOTS + s) * kThreads + tid];
+          if (k < 0) continue;
+          part[((size_t)seg * P.U + u) * rpg + (k - kbase)] = poisoned ? __int_as_float(0x7fc00000) : acc[s];
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) last_flag = (atomicAdd(&counters[u], 1u) == (unsigned int)(nseg - 1)) ? 1u : 0u;
+        __syncthreads();
+        if (last_flag) {
+          __threadfence();
+          int32_t kk[SLOTS];
+          float sum[SLOTS];
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) {
+            kk[s] = plan_k[((size_t)kg * SLOTS + s) * kThreads + tid];
+            sum[s] = 0.0f;
+          }
+          for (int64_t g = 0; g < nseg; ++g) {
+            const float *pg = part + ((size_t)g * P.U + u) * rpg - kbase;
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) sum[s] += (kk[s] >= 0) ? __ldcg(pg + kk[s]) : 0.0f;
+          }
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) {
+            if (kk[s] < 0) continue;
+            if (col < d)
+              SA[(int64_t)col * ldsa + kk[s]] = scale * sum[s];
+            else
+              Sb[kk[s]] = scale * sum[s];
+          }
+          if (tid == 0) counters[u] = 0u;
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) acc[s] = 0.0f;
     }
-  }
-}
-
-// Sum the per-chunk-range partial sums and apply the row scale.
-template <typename T>
-__global__ void reduce_partials(const float *__restrict__ part, int groups, int d, int64_t r_part,
-                                const int64_t *__restrict__ d_count, float scale, T *__restrict__ SA, int64_t ldsa,
-                                T *__restrict__ Sb) {
-  int64_t rr = r_part;
-  if (d_count) rr = min(r_part, *d_count);
-  const int col = blockIdx.y;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < rr; k += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.0f;
-    for (int g = 0; g < groups; ++g) s += part[((int64_t)g * (d + 1) + col) * r_part + k];
-    if (col < d)
-      SA[(int64_t)col * ldsa + k] = scale * s;
-    else
-      Sb[k] = scale * s;
   }
 }
 
@@ -310,59 +533,130 @@ __global__ void combine_f64(const double *__restrict__ Z, int d, int64_t n, cons
   }
 }
 
-template <int SLOTS, bool VEC>
-int launch_chunked(rnnls_ctx *ctx, const sketch_args_f32 &a, const plan_t &plan, int groups, int iters,
-                   float *part, int64_t r_part, int direct) {
-  auto kern = sketch_chunked_f32<SLOTS, VEC>;
-  const size_t smem = (size_t)kWorkers * kM * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    RNNLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+// rows of the plan per sketch thread: the smallest instantiated count that
+// holds r rows in one plan group (at most kMaxSlots, then several groups)
+int pick_slots(int64_t rows) {
+  const int64_t need = (rows + kThreads - 1) / kThreads;
+  static const int opts[] = {1, 2, 4, 8, 16, 24, 32, kMaxSlots};
+  for (int s : opts)
+    if (need <= s) return s;
+  return kMaxSlots;
+}
+
+typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+encode_tiled_fn tensor_map_encoder() {
+  static encode_tiled_fn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<encode_tiled_fn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Column view (32, n_raw / 32, cols) of a column-major FP32 matrix: box
+// (32, 128, 1) is one 4096-row chunk of one column, swizzled by 128 bytes;
+// lines past the end read as zero.
+int column_map(CUtensorMap *m, const float *base, int64_t n_raw, int64_t cols, int64_t ld) {
+  encode_tiled_fn enc = tensor_map_encoder();
+  if (!enc) return RNNLS_ECUDA;
+  const cuuint64_t lines = (cuuint64_t)(n_raw / 32);
+  cuuint64_t dims[3] = {32, lines, (cuuint64_t)cols};
+  cuuint64_t strides[2] = {128, (cuuint64_t)(cols > 1 ? ld : 32 * (int64_t)lines) * 4};
+  cuuint32_t box[3] = {32, kM / 32, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RNNLS_OK : RNNLS_ECUDA;
+}
+
+template <int SLOTS>
+int launch_srht(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, const srht_part &P, int blocks, int vec,
+                const uint64_t *signs, float *part, unsigned int *counters) {
+  static bool ready = false;
+  if (!ready) {
+    if (cudaFuncSetAttribute(sketch_srht_f32<SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSketchSmem) !=
+        cudaSuccess)
+      return RNNLS_ECUDA;
+    ready = true;
   }
-  dim3 grid((unsigned)(a.d + 1), (unsigned)groups, (unsigned)plan.kgroups);
-  kern<<<grid, kThreads, smem, ctx->stream>>>(a.A, a.lda, a.b, a.n_raw, a.d, iters, a.seed, a.inst, plan.pk, plan.k,
-                                               plan.cls, part, r_part, a.scale, a.SA, a.ldsa, a.Sb, direct);
+  CUtensorMap tmA, tmB;
+  memset(&tmA, 0, sizeof(tmA));
+  memset(&tmB, 0, sizeof(tmB));
+  if (vec) {
+    int st = column_map(&tmA, a.A, a.n_raw, a.d, a.lda);
+    if (!st) st = column_map(&tmB, a.b, a.n_raw, 1, a.n_raw);
+    if (st) return st;
+  }
+  sketch_srht_f32<SLOTS><<<(unsigned)blocks, kThreads, kSketchSmem, s>>>(
+      tmA, tmB, a.A, a.lda, a.b, a.n_raw, a.d, P, vec, a.seed, a.inst, signs, plan.pk, plan.k, plan.rows_per_group, part,
+      a.scale, a.SA, a.ldsa, a.Sb, counters);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 
-template <int SLOTS>
-int launch_chunked_v(rnnls_ctx *ctx, const sketch_args_f32 &a, const plan_t &plan, int groups, int iters,
-                     float *part, int64_t r_part, int direct, bool vec) {
-  return vec ? launch_chunked<SLOTS, true>(ctx, a, plan, groups, iters, part, r_part, direct)
-             : launch_chunked<SLOTS, false>(ctx, a, plan, groups, iters, part, r_part, direct);
-}
-
-int pick_slots(int64_t rows) {
-  const int64_t need = (rows + kPlanCapacityDen - 1) / kPlanCapacityDen;
-  static const int opts[] = {1, 2, 4, 8, 16, 24, 32, 40};
-  for (int s : opts)
-    if (need <= s) return s;
-  return 40;
-}
-
-template <int SLOTS>
-int occupancy_of(bool vec) {
-  int nb = 0;
-  const size_t smem = (size_t)kWorkers * kM * sizeof(float);
-  if (vec)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sketch_chunked_f32<SLOTS, true>, kThreads, smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sketch_chunked_f32<SLOTS, false>, kThreads, smem);
-  return std::max(nb, 1);
-}
-
-int occupancy_for(int slots, bool vec) {
-  switch (slots) {
-    case 1: return occupancy_of<1>(vec);
-    case 2: return occupancy_of<2>(vec);
-    case 4: return occupancy_of<4>(vec);
-    case 8: return occupancy_of<8>(vec);
-    case 16: return occupancy_of<16>(vec);
-    case 24: return occupancy_of<24>(vec);
-    case 32: return occupancy_of<32>(vec);
-    default: return occupancy_of<40>(vec);
+int launch_srht_slots(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, const srht_part &P, int blocks,
+                      int vec, const uint64_t *signs, float *part, unsigned int *counters) {
+  switch (plan.slots) {
+    case 1: return launch_srht<1>(s, a, plan, P, blocks, vec, signs, part, counters);
+    case 2: return launch_srht<2>(s, a, plan, P, blocks, vec, signs, part, counters);
+    case 4: return launch_srht<4>(s, a, plan, P, blocks, vec, signs, part, counters);
+    case 8: return launch_srht<8>(s, a, plan, P, blocks, vec, signs, part, counters);
+    case 16: return launch_srht<16>(s, a, plan, P, blocks, vec, signs, part, counters);
+    case 24: return launch_srht<24>(s, a, plan, P, blocks, vec, signs, part, counters);
+    case 32: return launch_srht<32>(s, a, plan, P, blocks, vec, signs, part, counters);
+    default: return launch_srht<kMaxSlots>(s, a, plan, P, blocks, vec, signs, part, counters);
   }
+}
+
+// Launch geometry of the large-n sketch for `sms` usable SMs.
+struct srht_geom {
+  plan_t plan;
+  srht_part P;
+  int blocks;
+  int vec;
+  int64_t maxseg;      // partial-sum segments per unit (0: no unit is split)
+  int64_t sign_words;  // sign words of D for the chunks with data
+  size_t plan_bytes, part_bytes, sign_bytes;
+};
+
+srht_geom plan_geometry(const sketch_args_f32 &a, int sms, bool force_aligned) {
+  srht_geom g{};
+  g.plan.slots = pick_slots(a.r);
+  g.plan.rows_per_group = (int64_t)kThreads * g.plan.slots;
+  g.plan.kgroups = (int)((a.r + g.plan.rows_per_group - 1) / g.plan.rows_per_group);
+  g.vec = (((uintptr_t)a.A % 16 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.b % 16 == 0)) ? 1 : 0;
+  g.P.J = (a.n_raw + 4 * (int64_t)kM - 1) / (4 * (int64_t)kM);
+  g.P.U = (int64_t)g.plan.kgroups * (a.d + 1);
+  g.P.T = g.P.U * g.P.J;
+  // many more columns than SMs: whole columns per block balance well enough
+  g.P.aligned = (force_aligned || g.P.U >= 8 * (int64_t)sms) ? 1 : 0;
+  g.blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms, g.P.aligned ? g.P.U : g.P.T));
+  g.maxseg = 0;
+  if (!g.P.aligned) {
+    for (int64_t u = 0; u < g.P.U; ++u) {
+      const int64_t f = part_block_of(u * g.P.J, g.blocks, g.P), l = part_block_of(u * g.P.J + g.P.J - 1, g.blocks, g.P);
+      if (l > f) g.maxseg = std::max<int64_t>(g.maxseg, l - f + 1);
+    }
+  }
+  g.sign_words = 4 * g.P.J * (kM / 64);
+  g.sign_bytes = align_up((size_t)g.sign_words * sizeof(uint64_t), 256);
+  g.plan_bytes = plan_ws_bytes(g.plan.slots, g.plan.kgroups);
+  g.part_bytes = align_up((size_t)g.maxseg * g.P.U * g.plan.rows_per_group * sizeof(float), 256);
+  return g;
+}
+
+void carve_plan(ws_carver &wc, plan_t &plan) {
+  plan.pk = wc.take<uint32_t>((size_t)plan.kgroups * plan.slots * kThreads);
+  plan.k = wc.take<int32_t>((size_t)plan.kgroups * plan.slots * kThreads);
 }
 
 }  // namespace
@@ -377,95 +671,28 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
                                                                a.idx, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
     return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
   }
-  const int64_t C = n / kM;  // >= 4
-  const int slots = pick_slots(a.r);
-  const int64_t rows_per_group = (int64_t)kPlanCapacityDen * slots;
-  const int kgroups = (int)((a.r + rows_per_group - 1) / rows_per_group);
-  const bool vec = ((uintptr_t)a.A % 16 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.b % 16 == 0);
-
-  // chunk groups: powers of two dividing C/4; pick the one that fills the
-  // resident block slots best (fewest partial waves), preferring fewer groups
-  const int per_sm = occupancy_for(slots, vec);
-  const int64_t slots_total = (int64_t)num_sms * per_sm;
-  int groups = 1;
-  double best = -1.0;
-  for (int64_t g = 1; g <= C / 4; g <<= 1) {
-    const int64_t units = (int64_t)(a.d + 1) * g * kgroups;
-    const int64_t waves = (units + slots_total - 1) / slots_total;
-    const double eff = (double)units / (double)(waves * slots_total);
-    const double score = eff - 0.02 * std::log2((double)g);
-    if (score > best + 1e-9) {
-      best = score;
-      groups = (int)g;
-    }
-    if (units >= 8 * slots_total) break;
-  }
-  const int iters = (int)(C / 4 / groups);
-  const int direct = (groups == 1) ? 1 : 0;
-
-  // workspace: plan + partial sums
-  const size_t plan_bytes = plan_ws_bytes(slots, kgroups);
-  const size_t part_bytes = direct ? 0 : align_up((size_t)groups * (a.d + 1) * a.r * sizeof(float), 256);
-  int st = ensure_workspace(ctx, plan_bytes + part_bytes + 256);
+  const int sms = (ctx->sketch_sms > 0) ? std::min(ctx->sketch_sms, num_sms) : num_sms;
+  srht_geom g = plan_geometry(a, sms, false);
+  int st = ensure_workspace(ctx, g.plan_bytes + g.sign_bytes + g.part_bytes + 768);
   if (st) return st;
   ws_carver wc(ctx->ws);
-  plan_t plan;
-  plan.pk = wc.take<uint32_t>((size_t)kgroups * slots * kThreads);
-  plan.k = wc.take<int32_t>((size_t)kgroups * slots * kThreads);
-  plan.cls = wc.take<uint32_t>((size_t)kgroups * kThreads);
-  plan.slots = slots;
-  plan.kgroups = kgroups;
-  plan.rows_per_group = rows_per_group;
-  float *part = direct ? nullptr : wc.take<float>((size_t)groups * (a.d + 1) * a.r);
-
+  carve_plan(wc, g.plan);
+  uint64_t *signs = wc.take<uint64_t>((size_t)g.sign_words);
+  float *part = g.maxseg ? wc.take<float>((size_t)g.maxseg * g.P.U * g.plan.rows_per_group) : nullptr;
+  unsigned int *counters = nullptr;
+  if (g.maxseg) {
+    st = ensure_counters(ctx, (size_t)g.P.U, &counters);
+    if (st) return st;
+  }
   {
     prof_scope ps(ctx, K_PLAN);
-    st = launch_build_plan(s, a.idx, a.r, a.d_count, plan, nullptr);
+    iid_gen gen{a.seed, a.inst, a.L};
+    st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, a.gen_iid ? &gen : nullptr, signs, g.sign_words, a.seed,
+                           a.inst);
   }
   if (st) return st;
-  {
-    prof_scope ps_main(ctx, K_SKETCH);
-    switch (slots) {
-    case 1: st = launch_chunked_v<1>(ctx, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 2: st = launch_chunked_v<2>(ctx, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 4: st = launch_chunked_v<4>(ctx, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 8: st = launch_chunked_v<8>(ctx, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 16: st = launch_chunked_v<16>(ctx, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 24: st = launch_chunked_v<24>(ctx, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 32: st = launch_chunked_v<32>(ctx, a, plan, groups, iters, part, a.r, direct, vec); break;
-    default: st = launch_chunked_v<40>(ctx, a, plan, groups, iters, part, a.r, direct, vec); break;
-    }
-  }
-  if (st) return st;
-  if (!direct) {
-    prof_scope ps(ctx, K_REDUCE);
-    dim3 grid((unsigned)std::min<int64_t>((a.r + 255) / 256, 64), (unsigned)(a.d + 1));
-    reduce_partials<float><<<grid, 256, 0, s>>>(part, groups, a.d, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
-    if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
-  }
-  return RNNLS_OK;
-}
-
-// Same launches as sketch_f32, but every scratch buffer comes from the
-// caller-provided region `scratch` (bytes long) and nothing is allocated.
-// Chunk groups are capped so that the partial sums fit in that region.
-template <int SLOTS, bool VEC>
-int launch_chunked_stream(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, int groups, int iters,
-                          float *part, int64_t r_part, int direct) {
-  auto kern = sketch_chunked_f32<SLOTS, VEC>;
-  const size_t smem = (size_t)kWorkers * kM * sizeof(float);
-  RNNLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)(a.d + 1), (unsigned)groups, (unsigned)plan.kgroups);
-  kern<<<grid, kThreads, smem, s>>>(a.A, a.lda, a.b, a.n_raw, a.d, iters, a.seed, a.inst, plan.pk, plan.k, plan.cls,
-                                     part, r_part, a.scale, a.SA, a.ldsa, a.Sb, direct);
-  return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
-}
-
-template <int SLOTS>
-int launch_chunked_stream_v(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, int groups, int iters,
-                            float *part, int64_t r_part, int direct, bool vec) {
-  return vec ? launch_chunked_stream<SLOTS, true>(s, a, plan, groups, iters, part, r_part, direct)
-             : launch_chunked_stream<SLOTS, false>(s, a, plan, groups, iters, part, r_part, direct);
+  prof_scope ps_main(ctx, K_SKETCH);
+  return launch_srht_slots(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
 }
 
 int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, void *scratch, size_t bytes) {
@@ -476,61 +703,26 @@ int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, vo
                                                                a.idx, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
     return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
   }
-  const int64_t C = n / kM;
-  const int slots = pick_slots(a.r);
-  const int64_t rows_per_group = (int64_t)kPlanCapacityDen * slots;
-  const int kgroups = (int)((a.r + rows_per_group - 1) / rows_per_group);
-  const bool vec = ((uintptr_t)a.A % 16 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.b % 16 == 0);
-  const size_t plan_bytes = plan_ws_bytes(slots, kgroups);
-  if (plan_bytes + 256 > bytes) return RNNLS_EUNSUPPORTED;
-  const size_t part_one = align_up((size_t)(a.d + 1) * a.r * sizeof(float), 256);
-  const int64_t fit = (int64_t)((bytes - plan_bytes - 256) / part_one);
-  const int per_sm = occupancy_for(slots, vec);
-  const int64_t slots_total = (int64_t)num_sms * per_sm;
-  int groups = 1;
-  double best = -1.0;
-  for (int64_t g = 1; g <= C / 4; g <<= 1) {
-    if (g > 1 && g > fit) break;
-    const int64_t units = (int64_t)(a.d + 1) * g * kgroups;
-    const int64_t waves = (units + slots_total - 1) / slots_total;
-    const double eff = (double)units / (double)(waves * slots_total);
-    const double score = eff - 0.02 * std::log2((double)g);
-    if (score > best + 1e-9) {
-      best = score;
-      groups = (int)g;
-    }
-    if (units >= 8 * slots_total) break;
-  }
-  const int iters = (int)(C / 4 / groups);
-  const int direct = (groups == 1) ? 1 : 0;
+  // counters first (zeroed by every call), then the plan, then partial sums;
+  // whole columns per block when the partial sums do not fit
+  srht_geom g = plan_geometry(a, num_sms, false);
+  const size_t cnt_bytes = align_up((size_t)g.P.U * sizeof(unsigned int), 256);
+  if (cnt_bytes + g.plan_bytes + g.part_bytes + 768 > bytes) g = plan_geometry(a, num_sms, true);
+  if (cnt_bytes + g.plan_bytes + g.part_bytes + 768 > bytes) return RNNLS_EUNSUPPORTED;
+  // the sign table when it fits, else the kernel draws D's words itself
+  const bool table = cnt_bytes + g.plan_bytes + g.part_bytes + g.sign_bytes + 768 <= bytes;
   ws_carver wc(scratch);
-  plan_t plan;
-  plan.pk = wc.take<uint32_t>((size_t)kgroups * slots * kThreads);
-  plan.k = wc.take<int32_t>((size_t)kgroups * slots * kThreads);
-  plan.cls = wc.take<uint32_t>((size_t)kgroups * kThreads);
-  plan.slots = slots;
-  plan.kgroups = kgroups;
-  plan.rows_per_group = rows_per_group;
-  float *part = direct ? nullptr : wc.take<float>((size_t)groups * (a.d + 1) * a.r);
-  int st = launch_build_plan(s, a.idx, a.r, a.d_count, plan, nullptr);
+  unsigned int *counters = wc.take<unsigned int>((size_t)g.P.U);
+  carve_plan(wc, g.plan);
+  uint64_t *signs = table ? wc.take<uint64_t>((size_t)g.sign_words) : nullptr;
+  float *part = g.maxseg ? wc.take<float>((size_t)g.maxseg * g.P.U * g.plan.rows_per_group) : nullptr;
+  if (g.maxseg && cudaMemsetAsync(counters, 0, (size_t)g.P.U * sizeof(unsigned int), s) != cudaSuccess)
+    return RNNLS_ECUDA;
+  iid_gen gen{a.seed, a.inst, a.L};
+  int st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, a.gen_iid ? &gen : nullptr, signs, g.sign_words, a.seed,
+                             a.inst);
   if (st) return st;
-  switch (slots) {
-    case 1: st = launch_chunked_stream_v<1>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 2: st = launch_chunked_stream_v<2>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 4: st = launch_chunked_stream_v<4>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 8: st = launch_chunked_stream_v<8>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 16: st = launch_chunked_stream_v<16>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 24: st = launch_chunked_stream_v<24>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
-    case 32: st = launch_chunked_stream_v<32>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
-    default: st = launch_chunked_stream_v<40>(s, a, plan, groups, iters, part, a.r, direct, vec); break;
-  }
-  if (st) return st;
-  if (!direct) {
-    dim3 grid((unsigned)std::min<int64_t>((a.r + 255) / 256, 64), (unsigned)(a.d + 1));
-    reduce_partials<float><<<grid, 256, 0, s>>>(part, groups, a.d, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
-    if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
-  }
-  return RNNLS_OK;
+  return launch_srht_slots(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
 }
 
 int sketch_f64(rnnls_ctx *ctx, const sketch_args_f64 &a) {

@@ -23,8 +23,12 @@ namespace rnnls {
 
 namespace {
 
+
 constexpr int kGT = 32;         // Gram tile
-constexpr int kLHThreads = 256; // Lawson-Hanson block
+#ifndef RNNLS_LH_THREADS
+#define RNNLS_LH_THREADS 256
+#endif
+constexpr int kLHThreads = RNNLS_LH_THREADS;  // Lawson-Hanson block
 
 // ---------------------------------------------------------------------------
 // Gram of X = [S | s] (m x (d+1)) in tiles of 32 x 32, split over rows.
@@ -155,6 +159,121 @@ __global__ void gram_reduce_kernel(const double *__restrict__ part, int splits, 
   }
 }
 
+// Gram, split reduction and column 1-norms in one launch.  Every block
+// writes its split's partial tile (and, on diagonal tiles, the partial
+// |.|-sums of its columns); the last block to finish a tile (counter per
+// tile, reset by that block) adds the splits in order 0..splits-1 and writes
+// Q as FP64 and as float pairs, plus the column 1-norms.
+__global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__restrict__ S, int64_t lds,
+                                                             const float *__restrict__ s, int64_t m, int d, int T,
+                                                             int64_t rows_per_split, double *__restrict__ part,
+                                                             double *__restrict__ part_abs,
+                                                             unsigned int *__restrict__ counters,
+                                                             double *__restrict__ Qd, float *__restrict__ Qhi,
+                                                             float *__restrict__ Qlo, double *__restrict__ colabs) {
+  __shared__ float Xi[kGT][kGT + 1];
+  __shared__ float Xj[kGT][kGT + 1];
+  __shared__ unsigned int last_flag;
+  int ti, tj;
+  tile_coords(blockIdx.x, T, ti, tj);
+  const int ntiles = T * (T + 1) / 2;
+  const int splits = gridDim.y;
+  const int64_t k0 = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t k1 = min(m, k0 + rows_per_split);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool diag = (ti == tj);
+  dot2 acc[2][2];
+  dot2 absacc[4];
+  for (int64_t kb = k0; kb < k1; kb += kGT) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int kk = e & 31, cc = e >> 5;
+      const int64_t k = kb + kk;
+      const float *ci = gram_col(S, lds, s, d, ti * kGT + cc);
+      const float *cj = gram_col(S, lds, s, d, tj * kGT + cc);
+      const float vi = (ci && k < k1) ? ci[k] : 0.0f;
+      Xi[kk][cc] = vi;
+      Xj[kk][cc] = (cj && k < k1) ? cj[k] : 0.0f;
+      if (diag) absacc[q].add(fabsf(vi));
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kGT; ++kk) {
+      const float a0 = Xi[kk][2 * ty], a1 = Xi[kk][2 * ty + 1];
+      const float b0 = Xj[kk][2 * tx], b1 = Xj[kk][2 * tx + 1];
+      acc[0][0].add_prod(a0, b0);
+      acc[0][1].add_prod(a0, b1);
+      acc[1][0].add_prod(a1, b0);
+      acc[1][1].add_prod(a1, b1);
+    }
+    __syncthreads();
+  }
+  double *out = part + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (kGT * kGT);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const ff v = acc[a][c].value();
+      out[(2 * ty + a) * kGT + 2 * tx + c] = (double)v.hi + (double)v.lo;
+    }
+  if (diag) {
+    // column ti*32 + (warp + 8q): the 32 lanes of a warp hold 32 rows of it
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const ff v = absacc[q].value();
+      double t = (double)v.hi + (double)v.lo;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if ((threadIdx.x & 31) == 0) part_abs[(int64_t)blockIdx.y * (T * kGT) + ti * kGT + (threadIdx.x >> 5) + 8 * q] = t;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int done = atomicAdd(&counters[blockIdx.x], 1u);
+    last_flag = (done == (unsigned int)(splits - 1)) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!last_flag) return;
+  __threadfence();
+  const int D1 = d + 1;
+  // fixed order sp = 0..splits-1; the thread's four positions in flight per sp
+  double v4[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int sp = 0; sp < splits; ++sp) {
+    const double *src = part + ((int64_t)sp * ntiles + blockIdx.x) * (kGT * kGT);
+    double t4[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) t4[u] = __ldcg(src + threadIdx.x + 256 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v4[u] += t4[u];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int pos = threadIdx.x + 256 * u;
+    const int i = ti * kGT + pos / kGT, j = tj * kGT + pos % kGT;
+    if (i >= D1 || j >= D1 || i > j) continue;
+    const double v = v4[u];
+    const float h = (float)v;
+    const float l = (float)(v - (double)h);
+    Qd[(int64_t)i * D1 + j] = v;
+    Qd[(int64_t)j * D1 + i] = v;
+    Qhi[(int64_t)i * D1 + j] = h;
+    Qhi[(int64_t)j * D1 + i] = h;
+    Qlo[(int64_t)i * D1 + j] = l;
+    Qlo[(int64_t)j * D1 + i] = l;
+  }
+  if (diag) {
+    for (int c = threadIdx.x; c < kGT; c += blockDim.x) {
+      const int col = ti * kGT + c;
+      if (col >= d) continue;
+      double v = 0.0;
+      for (int sp = 0; sp < splits; ++sp) v += __ldcg(part_abs + (int64_t)sp * (T * kGT) + col);
+      colabs[col] = v;
+    }
+  }
+  if (threadIdx.x == 0) counters[blockIdx.x] = 0u;
+}
+
 // ||S||_1 = max_j sum_k |S_kj| (compensated), one warp per column.
 template <typename T>
 __global__ void colabs_kernel(const T *__restrict__ S, int64_t lds, int64_t m, int d, double *__restrict__ out) {
@@ -190,6 +309,7 @@ struct lh_job {
   int d;
   double *x;
   rnnls_info *info;
+  int q_smem;  // 1: copy Q into shared memory (it fits); 0: read it from global memory
 };
 
 // float-float dot accumulator with float-float inputs (Dot2 on the leading
@@ -215,6 +335,9 @@ struct dotff {
 };
 
 struct lh_shared {
+  uint32_t wkey[kLHThreads / 32];  // per-warp candidate keys / partial sums (fast path)
+  int widx[kLHThreads / 32];
+  float wsum[kLHThreads / 32];
   int p;       // passive count
   int t;       // candidate / chosen index
   int status;
@@ -225,11 +348,6 @@ struct lh_shared {
   ff vred[kLHThreads / 32];
   float fred[kLHThreads / 32];
 };
-
-__device__ __forceinline__ ff qld(const lh_job &jb, int i, int j) {
-  const int64_t e = (int64_t)i * (jb.d + 1) + j;
-  return ff{jb.Qhi[e], jb.Qlo[e]};
-}
 
 // block sum of floats (all threads get the result)
 __device__ float block_sum_f(float v, lh_shared &sh) {
@@ -292,54 +410,291 @@ __device__ int block_argmax_ff(bool valid, ff v, int idx, lh_shared &sh, ff &bes
   return bi;
 }
 
-// argmin with ties to the smallest index
-__device__ int block_argmin_ff(bool valid, ff v, int idx, lh_shared &sh, ff &best) {
-  return block_argmax_ff(valid, ff_neg(v), idx, sh, best);
+// Order-preserving map of a float onto unsigned integers.
+__device__ __forceinline__ uint32_t fkey(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Warp-wide argmax of float-float values with ties to the smallest index
+// (lanes without a candidate pass idx < 0); -1 if no lane has one.
+__device__ __forceinline__ int warp_argmax_ff(ff v, int idx, ff &best) {
+  const bool valid = idx >= 0;
+  const uint32_t kh = valid ? fkey(v.hi) : 0u;
+  const uint32_t mh = __reduce_max_sync(0xffffffffu, kh);
+  const uint32_t kl = (valid && kh == mh) ? fkey(v.lo) : 0u;
+  const uint32_t ml = __reduce_max_sync(0xffffffffu, kl);
+  const uint32_t ci = (valid && kh == mh && kl == ml) ? (uint32_t)idx : 0xffffffffu;
+  const uint32_t mi = __reduce_min_sync(0xffffffffu, ci);
+  const uint32_t win = __ballot_sync(0xffffffffu, ci == mi && mi != 0xffffffffu);
+  const int src = win ? __ffs(win) - 1 : 0;
+  best.hi = __shfl_sync(0xffffffffu, v.hi, src);
+  best.lo = __shfl_sync(0xffffffffu, v.lo, src);
+  return (mi == 0xffffffffu) ? -1 : (int)mi;
 }
 
 struct lh_vecs {
-  float *B;     // ldB x p FP32 inverse of D Q_PP D, slot indexed
+  float *B;           // FP32 inverse of D Q_PP D, slot indexed, leading dimension ldB (odd)
   int ldB;
-  float *Dsc;   // d: D_jj = Q_jj^(-1/2)
-  float *qh;    // d: D q in FP32
+  const float *Qh, *Ql;  // Q (d+1 x d+1) as float pairs, leading dimension ldQ (shared memory when it fits)
+  int ldQ;
+  float *Dsc;         // d: D_jj = Q_jj^(-1/2)
+  float *qh;          // d: D q in FP32
+  ff *qv;             // d: q
+  ff *w;              // d: dual w = q - Q x
+  int *varslot;       // d: slot of variable j, or -1
+  unsigned char *rej; // d: rejected in the current selection
+  int *slotvar;       // d+1: variable of slot s
+  ff *xs, *zs, *res;  // d+1: x, z and residual per slot
   float *f1, *f2, *f3;  // d+1 FP32 temporaries
-  ff *x, *z, *w, *res;  // d float-float vectors
-  int *slotvar;  // p: variable at slot
-  int *varslot;  // d: slot of variable or -1
-  unsigned char *rej;
 };
 
-// y[s] = sum_s' B[s][s'] g[s'] for s < p (B symmetric: read column s)
+__host__ __device__ __forceinline__ int odd_ld(int d) { return (d % 2 == 1) ? d : d + 1; }
+
+// Threads cooperating on one output of a length-n dot product (power of 2,
+// consecutive lanes of one warp): more threads for shorter outputs.
+__device__ __forceinline__ int lanes_per_row(int rows) {
+  return (rows <= 32) ? 8 : (rows <= 64 ? 4 : (rows <= 128 ? 2 : 1));
+}
+
+// y[s] = sum_q B[s][q] g[q] for s < p (B symmetric: lanes of row s read
+// column s, rows of B at odd stride, so a warp touches distinct banks)
 __device__ __forceinline__ void apply_B(const lh_vecs &V, int p, const float *g, float *y) {
-  for (int s = threadIdx.x; s < p; s += kLHThreads) {
-    float acc = 0.0f;
-    for (int q = 0; q < p; ++q) acc = fmaf(V.B[(int64_t)q * V.ldB + s], g[q], acc);
-    y[s] = acc;
+  const int tpr = lanes_per_row(p);
+  const int part = threadIdx.x & (tpr - 1);
+  for (int base = 0; base < p; base += kLHThreads / tpr) {
+    const int s = base + threadIdx.x / tpr;
+    const bool ok = s < p;
+    float a0 = 0.0f, a1 = 0.0f;
+    if (ok) {
+      int q = part;
+      for (; q + tpr < p; q += 2 * tpr) {
+        a0 = fmaf(V.B[q * V.ldB + s], g[q], a0);
+        a1 = fmaf(V.B[(q + tpr) * V.ldB + s], g[q + tpr], a1);
+      }
+      if (q < p) a0 = fmaf(V.B[q * V.ldB + s], g[q], a0);
+    }
+    float a = a0 + a1;
+    for (int o = 1; o < tpr; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (ok && part == 0) y[s] = a;
   }
 }
 
-// Accurate passive solve for the current slots 0..np-1 (variables slotvar),
-// z = Q_PP^{-1} q_P.  B holds the inverse of D Q_PP D when `bordered` is
-// false; when true, slots 0..np-2 use B and slot np-1 is the candidate added
-// by the bordering formulas with vector v = f3 (B u) and Schur value sc.
-__device__ void passive_solve(const lh_job &jb, const lh_vecs &V, lh_shared &sh, int np, bool bordered, float sc,
-                              int iters) {
-  const int d = jb.d;
+// w_j = q_j - sum_s Q[j][slotvar[s]] x_s for every j (float-float)
+__device__ __noinline__ void compute_w(const lh_vecs &V, int d, int p) {
+  const int tpj = lanes_per_row(d);
+  const int part = threadIdx.x & (tpj - 1);
+  for (int base = 0; base < d; base += kLHThreads / tpj) {
+    const int j = base + threadIdx.x / tpj;
+    const bool ok = j < d;
+    dotff a0;
+    if (ok) {
+      if (part == 0) a0.init(V.qv[j]);
+      for (int s = part; s < p; s += tpj) {
+        const int e = V.slotvar[s] * V.ldQ + j;
+        a0.sub_prod(ff{V.Qh[e], V.Ql[e]}, V.xs[s]);
+      }
+    }
+    ff a = a0.value();
+    for (int o = 1; o < tpj; o <<= 1) {
+      const ff u{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+      a = ff_add(a, u);
+    }
+    if (ok && part == 0) V.w[j] = a;
+  }
+}
+
+// Fast path, phase 1: FP32 dual for every j and each warp's best candidate
+// (largest w_j outside P, ties to the smallest j) into sh.wkey / sh.widx.
+__device__ __forceinline__ void dual_and_warp_best(const lh_vecs &V, int d, int p, lh_shared &sh) {
+  const int tpj = lanes_per_row(d);
+  const int part = threadIdx.x & (tpj - 1);
+  uint32_t bkey = 0u;
+  uint32_t bidx = 0xffffffffu;
+  for (int base = 0; base < d; base += kLHThreads / tpj) {
+    const int j = base + threadIdx.x / tpj;
+    const bool ok = j < d;
+    float a0 = 0.0f, a1 = 0.0f;
+    if (ok) {
+      int s = part;
+      for (; s + tpj < p; s += 2 * tpj) {
+        a0 = fmaf(-V.Qh[V.slotvar[s] * V.ldQ + j], V.xs[s].hi, a0);
+        a1 = fmaf(-V.Qh[V.slotvar[s + tpj] * V.ldQ + j], V.xs[s + tpj].hi, a1);
+      }
+      if (s < p) a0 = fmaf(-V.Qh[V.slotvar[s] * V.ldQ + j], V.xs[s].hi, a0);
+    }
+    float a = a0 + a1;
+    for (int o = 1; o < tpj; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (ok && part == 0) {
+      const float wj = V.qv[j].hi + a;
+      V.w[j] = ff{wj, 0.0f};
+      if (V.varslot[j] < 0) {
+        const uint32_t k = fkey(wj);
+        if (bidx == 0xffffffffu || k > bkey) {  // j increases along this lane: first wins ties
+          bkey = k;
+          bidx = (uint32_t)j;
+        }
+      }
+    }
+  }
+  const uint32_t mk = __reduce_max_sync(0xffffffffu, bidx != 0xffffffffu ? bkey : 0u);
+  const uint32_t mi = __reduce_min_sync(0xffffffffu, (bidx != 0xffffffffu && bkey == mk) ? bidx : 0xffffffffu);
+  if ((threadIdx.x & 31) == 0) {
+    sh.wkey[threadIdx.x >> 5] = mk;
+    sh.widx[threadIdx.x >> 5] = (int)mi;
+  }
+}
+
+// After the barrier: the block's candidate from the per-warp winners.
+__device__ __forceinline__ int merge_warp_best(const lh_shared &sh) {
+  uint32_t bk = 0u;
+  int bi = -1;
+  for (int q = 0; q < kLHThreads / 32; ++q) {
+    const int i = sh.widx[q];
+    if (i < 0) continue;
+    const uint32_t k = sh.wkey[q];
+    if (bi < 0 || k > bk || (k == bk && i < bi)) {
+      bk = k;
+      bi = i;
+    }
+  }
+  return bi;
+}
+
+// Fast path, phase 2: v = B u with u_s = D_s Q[v_s][t] D_t made on the fly,
+// v into f3, per-warp partial sums of u'v into sh.wsum.
+__device__ __forceinline__ void bordered_v(const lh_vecs &V, int p, int t, float dt, lh_shared &sh) {
+  const int tpr = lanes_per_row(p);
+  const int part = threadIdx.x & (tpr - 1);
+  const float *qt = V.Qh + t * V.ldQ;
+  float uv = 0.0f;
+  for (int base = 0; base < p; base += kLHThreads / tpr) {
+    const int s = base + threadIdx.x / tpr;
+    const bool ok = s < p;
+    float a0 = 0.0f, a1 = 0.0f;
+    if (ok) {
+      int q = part;
+      for (; q + tpr < p; q += 2 * tpr) {
+        const int v0 = V.slotvar[q], v1 = V.slotvar[q + tpr];
+        a0 = fmaf(V.B[q * V.ldB + s], qt[v0] * V.Dsc[v0], a0);
+        a1 = fmaf(V.B[(q + tpr) * V.ldB + s], qt[v1] * V.Dsc[v1], a1);
+      }
+      if (q < p) {
+        const int v0 = V.slotvar[q];
+        a0 = fmaf(V.B[q * V.ldB + s], qt[v0] * V.Dsc[v0], a0);
+      }
+    }
+    float a = (a0 + a1) * dt;
+    for (int o = 1; o < tpr; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (ok && part == 0) {
+      V.f3[s] = a;
+      const int vs = V.slotvar[s];
+      uv = fmaf(qt[vs] * V.Dsc[vs] * dt, a, uv);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) uv += __shfl_xor_sync(0xffffffffu, uv, o);
+  if ((threadIdx.x & 31) == 0) sh.wsum[threadIdx.x >> 5] = uv;
+}
+
+// The entering candidate: argmax of w over j outside P and not rejected
+// (ties to the smallest j).  Warp 0 decides; everyone gets the result.
+__device__ __noinline__ int select_candidate(const lh_vecs &V, int d, lh_shared &sh, ff &best) {
+  if (threadIdx.x < 32) {
+    ff bv{0.0f, 0.0f};
+    int bj = -1;
+    for (int j = threadIdx.x; j < d; j += 32) {
+      if (V.varslot[j] < 0 && !V.rej[j]) {
+        const ff wj = V.w[j];
+        if (bj < 0 || ff_gt(wj, bv)) {
+          bv = wj;
+          bj = j;
+        }
+      }
+    }
+    ff b;
+    const int t = warp_argmax_ff(bv, bj, b);
+    if (threadIdx.x == 0) {
+      sh.t = t;
+      sh.ffscal = b;
+    }
+  }
+  __syncthreads();
+  best = sh.ffscal;
+  return sh.t;
+}
+
+// The interpolation step: over slots with z <= 0, the minimum of
+// x/(x - z) (ties to the smallest variable).  Warp 0 decides.
+__device__ __noinline__ int select_alpha(const lh_vecs &V, int p, lh_shared &sh, ff &amin) {
+  if (threadIdx.x < 32) {
+    ff bv{0.0f, 0.0f};
+    int bj = -1;
+    for (int s = threadIdx.x; s < p; s += 32) {
+      if (ff_le0(V.zs[s])) {
+        const int v = V.slotvar[s];
+        const ff xv = V.xs[s];
+        const ff a = ff_div(xv, ff_sub(xv, V.zs[s]));
+        if (bj < 0 || ff_lt(a, bv) || (!ff_gt(a, bv) && v < bj)) {
+          bv = a;
+          bj = v;
+        }
+      }
+    }
+    ff b;
+    const int t = warp_argmax_ff(ff_neg(bv), bj, b);
+    if (threadIdx.x == 0) {
+      sh.t = t;
+      sh.ffscal = ff_neg(b);
+    }
+  }
+  __syncthreads();
+  amin = sh.ffscal;
+  return sh.t;
+}
+
+// res_i = q_{v_i} - sum_q Q[v_i][v_q] z_q for slots i < np (float-float)
+__device__ __noinline__ void residual_slots(const lh_vecs &V, int np) {
+  for (int i = threadIdx.x; i < np; i += kLHThreads) {
+    const int vi = V.slotvar[i];
+    const float *rh = V.Qh + vi * V.ldQ;
+    const float *rl = V.Ql + vi * V.ldQ;
+    dotff a0, a1;
+    a0.init(V.qv[vi]);
+    int q = 0;
+    for (; q + 1 < np; q += 2) {
+      const int v0 = V.slotvar[q], v1 = V.slotvar[q + 1];
+      a0.sub_prod(ff{rh[v0], rl[v0]}, V.zs[q]);
+      a1.sub_prod(ff{rh[v1], rl[v1]}, V.zs[q + 1]);
+    }
+    if (q < np) {
+      const int v0 = V.slotvar[q];
+      a0.sub_prod(ff{rh[v0], rl[v0]}, V.zs[q]);
+    }
+    V.res[i] = ff_add(a0.value(), a1.value());
+  }
+}
+
+// Passive solve z = Q_PP^{-1} q_P for slots 0..np-1.  Without bordering, B
+// is the inverse of D Q_PP D.  With bordering, B covers slots 0..np-2 and
+// the candidate in slot np-1 enters through v = f3 = B u and the Schur
+// value sc.  Unless `have_initial` (zs already holds an FP32 estimate), one
+// FP32 solve comes first; then `iters` float-float refinement steps.
+__device__ __noinline__ void passive_solve(const lh_vecs &V, lh_shared &sh, int np, bool bordered, float sc,
+                                           int iters, bool have_initial = false) {
   const int pb = bordered ? np - 1 : np;
-  // initial FP32 solve in scaled variables: g = D q_P
-  // step 0 uses g = qh; subsequent steps use g = D res
-  for (int step = 0; step <= iters; ++step) {
-    // g into f1
+  for (int step = have_initial ? 1 : 0; step <= iters; ++step) {
+    if (step > 0) {
+      residual_slots(V, np);
+      __syncthreads();
+    }
     for (int s = threadIdx.x; s < np; s += kLHThreads) {
       const int v = V.slotvar[s];
       V.f1[s] = (step == 0) ? V.qh[v] : V.res[s].hi * V.Dsc[v];
     }
     __syncthreads();
-    // y = B g on the first pb slots -> f2
     apply_B(V, pb, V.f1, V.f2);
     __syncthreads();
     if (bordered) {
-      // y_t = (g_t - v'g_P) / sc ; y_P = B g_P - v y_t
       float part = 0.0f;
       for (int s = threadIdx.x; s < pb; s += kLHThreads) part = fmaf(V.f3[s], V.f1[s], part);
       const float vg = block_sum_f(part, sh);
@@ -348,58 +703,35 @@ __device__ void passive_solve(const lh_job &jb, const lh_vecs &V, lh_shared &sh,
       if (threadIdx.x == 0) V.f2[pb] = yt;
       __syncthreads();
     }
-    // z (+)= D y
     for (int s = threadIdx.x; s < np; s += kLHThreads) {
-      const int v = V.slotvar[s];
-      const float dz = V.f2[s] * V.Dsc[v];
-      V.z[s] = (step == 0) ? ff_make(dz) : ff_add(V.z[s], ff_make(dz));
-    }
-    __syncthreads();
-    if (step == iters) break;
-    // residual res = q_P - Q_PP z (float-float)
-    for (int s = threadIdx.x; s < np; s += kLHThreads) {
-      const int vi = V.slotvar[s];
-      dotff acc;
-      acc.init(qld(jb, vi, d));
-      for (int q = 0; q < np; ++q) acc.sub_prod(qld(jb, V.slotvar[q], vi), V.z[q]);
-      V.res[s] = acc.value();
+      const float dz = V.f2[s] * V.Dsc[V.slotvar[s]];
+      V.zs[s] = (step == 0) ? ff_make(dz) : ff_add(V.zs[s], ff_make(dz));
     }
     __syncthreads();
   }
 }
 
-__device__ void compute_w(const lh_job &jb, const lh_vecs &V, int p) {
-  const int d = jb.d;
-  for (int j = threadIdx.x; j < d; j += kLHThreads) {
-    dotff acc;
-    acc.init(qld(jb, j, d));
-    for (int s = 0; s < p; ++s) {
-      const int v = V.slotvar[s];
-      acc.sub_prod(qld(jb, v, j), V.x[v]);
-    }
-    V.w[j] = acc.value();
-  }
-}
-
-// Remove slot s from the inverse (Schur complement) and move the last slot
-// into its place.  p is the count before removal.
-__device__ void downdate(const lh_vecs &V, lh_shared &sh, int s, int p) {
+// Drop slot s (Schur-complement downdate of B), then move the last slot
+// into s (B row/column, Q row, x, slot maps).  p = count before the drop.
+__device__ __noinline__ void drop_slot(const lh_vecs &V, int d, int s, int p) {
   const float bss = V.B[(int64_t)s * V.ldB + s];
-  // save column s
   for (int q = threadIdx.x; q < p; q += kLHThreads) V.f1[q] = V.B[(int64_t)q * V.ldB + s];
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < (int64_t)p * p; e += kLHThreads) {
-    const int a = (int)(e / p), c = (int)(e % p);
-    V.B[(int64_t)a * V.ldB + c] -= V.f1[a] * V.f1[c] / bss;
+  const float ibss = 1.0f / bss;
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int a = warp; a < p; a += kLHThreads / 32) {
+      const float fa = V.f1[a] * ibss;
+      for (int c = lane; c < p; c += 32) V.B[a * V.ldB + c] = fmaf(-fa, V.f1[c], V.B[a * V.ldB + c]);
+    }
   }
   __syncthreads();
   const int last = p - 1;
   if (s != last) {
-    // move row/column `last` into s
     for (int q = threadIdx.x; q < p; q += kLHThreads) V.f1[q] = V.B[(int64_t)last * V.ldB + q];
     __syncthreads();
     for (int q = threadIdx.x; q < p; q += kLHThreads) {
-      if (q == s) continue;  // the removed slot's own entries are dropped
+      if (q == s) continue;
       const float val = V.f1[q];
       const int qq = (q == last) ? s : q;
       V.B[(int64_t)s * V.ldB + qq] = val;
@@ -409,53 +741,102 @@ __device__ void downdate(const lh_vecs &V, lh_shared &sh, int s, int p) {
       const int v = V.slotvar[last];
       V.slotvar[s] = v;
       V.varslot[v] = s;
+      V.xs[s] = V.xs[last];
     }
   }
   __syncthreads();
 }
 
+struct lh_layout {
+  size_t bytes;
+  size_t off_B, off_Qh, off_Ql, off_Dsc, off_qh, off_qv, off_w, off_varslot, off_rej, off_slotvar, off_xs, off_zs,
+      off_res, off_f1, off_f2, off_f3;
+};
+
+__host__ __device__ inline lh_layout lh_make_layout(int d, bool q_smem) {
+  lh_layout L;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    const size_t at = o;
+    o += (b + 15) & ~(size_t)15;
+    return at;
+  };
+  const int ldB = odd_ld(d), ldQ = odd_ld(d + 1);
+  L.off_B = take((size_t)ldB * d * 4);
+  L.off_Qh = q_smem ? take((size_t)(d + 1) * ldQ * 4) : 0;
+  L.off_Ql = q_smem ? take((size_t)(d + 1) * ldQ * 4) : 0;
+  L.off_Dsc = take((size_t)d * 4);
+  L.off_qh = take((size_t)d * 4);
+  L.off_qv = take((size_t)d * 8);
+  L.off_w = take((size_t)d * 8);
+  L.off_varslot = take((size_t)d * 4);
+  L.off_rej = take((size_t)d);
+  L.off_slotvar = take((size_t)(d + 1) * 4);
+  L.off_xs = take((size_t)(d + 1) * 8);
+  L.off_zs = take((size_t)(d + 1) * 8);
+  L.off_res = take((size_t)(d + 1) * 8);
+  L.off_f1 = take((size_t)(d + 1) * 4);
+  L.off_f2 = take((size_t)(d + 1) * 4);
+  L.off_f3 = take((size_t)(d + 1) * 4);
+  L.bytes = o;
+  return L;
+}
+
 __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &sh, int max_outer, int max_inner) {
   const int d = jb.d;
+  const int D1 = d + 1;
   const int tid = threadIdx.x;
+  const bool q_smem = jb.q_smem;
+  const lh_layout L = lh_make_layout(d, q_smem);
   lh_vecs V;
-  V.ldB = (d % 2 == 0) ? d + 1 : d + 2;
-  char *ptr = (char *)smem_raw;
-  auto take = [&](size_t bytes) {
-    char *q = ptr;
-    ptr += (bytes + 15) & ~(size_t)15;
-    return (void *)q;
-  };
-  V.B = (float *)take((size_t)V.ldB * d * sizeof(float));
-  V.Dsc = (float *)take(d * sizeof(float));
-  V.qh = (float *)take(d * sizeof(float));
-  V.f1 = (float *)take((d + 1) * sizeof(float));
-  V.f2 = (float *)take((d + 1) * sizeof(float));
-  V.f3 = (float *)take((d + 1) * sizeof(float));
-  V.x = (ff *)take(d * sizeof(ff));
-  V.z = (ff *)take((d + 1) * sizeof(ff));
-  V.w = (ff *)take(d * sizeof(ff));
-  V.res = (ff *)take((d + 1) * sizeof(ff));
-  V.slotvar = (int *)take((d + 1) * sizeof(int));
-  V.varslot = (int *)take(d * sizeof(int));
-  V.rej = (unsigned char *)take(d);
+  V.ldB = odd_ld(d);
+  V.B = (float *)(smem_raw + L.off_B);
+  if (q_smem) {
+    float *qh = (float *)(smem_raw + L.off_Qh);
+    float *ql = (float *)(smem_raw + L.off_Ql);
+    const int ld = odd_ld(D1);
+    for (int e = tid; e < D1 * D1; e += kLHThreads) {
+      const int i = e / D1, j = e - i * D1;
+      qh[i * ld + j] = jb.Qhi[e];
+      ql[i * ld + j] = jb.Qlo[e];
+    }
+    V.Qh = qh;
+    V.Ql = ql;
+    V.ldQ = ld;
+  } else {
+    V.Qh = jb.Qhi;
+    V.Ql = jb.Qlo;
+    V.ldQ = D1;
+  }
+  V.Dsc = (float *)(smem_raw + L.off_Dsc);
+  V.qh = (float *)(smem_raw + L.off_qh);
+  V.qv = (ff *)(smem_raw + L.off_qv);
+  V.w = (ff *)(smem_raw + L.off_w);
+  V.varslot = (int *)(smem_raw + L.off_varslot);
+  V.rej = (unsigned char *)(smem_raw + L.off_rej);
+  V.slotvar = (int *)(smem_raw + L.off_slotvar);
+  V.xs = (ff *)(smem_raw + L.off_xs);
+  V.zs = (ff *)(smem_raw + L.off_zs);
+  V.res = (ff *)(smem_raw + L.off_res);
+  V.f1 = (float *)(smem_raw + L.off_f1);
+  V.f2 = (float *)(smem_raw + L.off_f2);
+  V.f3 = (float *)(smem_raw + L.off_f3);
 
   // tolerance 10 eps ||S||_1 max(r, d) ||s||_2 (FP64 scalar work, once)
   __shared__ double tol_d;
   if (tid == 0) {
     double n1 = 0.0;
     for (int j = 0; j < d; ++j) n1 = fmax(n1, jb.colabs[j]);
-    const double ss = jb.Qd[(int64_t)d * (d + 1) + d];
+    const double ss = jb.Qd[(int64_t)d * D1 + d];
     tol_d = 10.0 * 2.220446049250313e-16 * n1 * (double)max(jb.r, (int64_t)d) * sqrt(fmax(ss, 0.0));
     sh.p = 0;
     sh.status = RNNLS_OK;
-    sh.flag = 0;
   }
   __syncthreads();
   const ff tol = ff_from_double(tol_d);
-  // finiteness of Q, q
   {
     int bad = 0;
-    for (int64_t e = tid; e < (int64_t)(d + 1) * (d + 1); e += kLHThreads) bad |= !isfinite(jb.Qd[e]);
+    for (int64_t e = tid; e < (int64_t)D1 * D1; e += kLHThreads) bad |= !isfinite(jb.Qd[e]);
     if (__syncthreads_or(bad)) {
       for (int j = tid; j < d; j += kLHThreads) jb.x[j] = 0.0;
       if (tid == 0 && jb.info) {
@@ -471,120 +852,157 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
     }
   }
   for (int j = tid; j < d; j += kLHThreads) {
-    const double qjj = jb.Qd[(int64_t)j * (d + 1) + j];
+    const double qjj = jb.Qd[(int64_t)j * D1 + j];
     const float dj = (qjj > 0.0) ? (float)(1.0 / sqrt(qjj)) : 0.0f;
     V.Dsc[j] = dj;
-    V.qh[j] = (float)jb.Qd[(int64_t)j * (d + 1) + d] * dj;
-    V.x[j] = ff{0.0f, 0.0f};
+    const ff qj{jb.Qhi[(int64_t)j * D1 + d], jb.Qlo[(int64_t)j * D1 + d]};
+    V.qv[j] = qj;
+    V.qh[j] = qj.hi * dj;
     V.varslot[j] = -1;
   }
   __syncthreads();
 
+  // Iterations run in FP32 (inverse of the equilibrated passive block,
+  // FP32 dual).  When they stop, the result is verified in float-float: a
+  // refined passive solve must be positive and the float-float dual must
+  // not exceed tol off the passive set.  If either check fails the method
+  // continues from there with every passive solve refined and the dual in
+  // float-float, exactly as the FP64 algorithm would.
   int outer = 0, inner = 0;
-  const int refine = 2;
+  bool accurate = false;
+  bool go_inner = false;
   for (;;) {
-    // dual vector
-    compute_w(jb, V, sh.p);
-    for (int j = tid; j < d; j += kLHThreads) V.rej[j] = 0;
-    __syncthreads();
-    bool accepted = false;
-    for (;;) {
-      // candidate: argmax over j not in P, not rejected
-      bool valid = false;
-      ff wv{0.0f, 0.0f};
-      int jj = -1;
-      ff bestl{-3.0e38f, 0.0f};
-      int bi = -1;
-      for (int j = tid; j < d; j += kLHThreads) {
-        if (V.varslot[j] < 0 && !V.rej[j]) {
-          const ff wj = V.w[j];
-          if (jj < 0 || ff_gt(wj, bestl)) {
-            bestl = wj;
-            jj = j;
+    bool need_inner = true;
+    if (!go_inner) {
+      bool accepted = false;
+      int t = -1;
+      ff best{0.0f, 0.0f};
+      if (accurate) {
+        compute_w(V, d, sh.p);
+        for (int j = tid; j < d; j += kLHThreads) V.rej[j] = 0;
+        __syncthreads();
+        t = select_candidate(V, d, sh, best);
+      } else {
+        dual_and_warp_best(V, d, sh.p, sh);
+        for (int j = tid; j < d; j += kLHThreads) V.rej[j] = 0;
+        __syncthreads();
+        t = merge_warp_best(sh);
+        if (t >= 0) best = V.w[t];
+      }
+      for (;;) {
+        if (t < 0 || !ff_gt(best, tol)) break;
+        const int p = sh.p;
+        const float dt = V.Dsc[t];
+        // v = B u and the Schur value sc = 1 - u'v (fixed summation order)
+        bordered_v(V, p, t, dt, sh);
+        __syncthreads();
+        float uv = 0.0f;
+        for (int q = 0; q < kLHThreads / 32; ++q) uv += sh.wsum[q];
+        const float sc = 1.0f - uv;
+        if (!(sc > 1e-13f) || dt == 0.0f) {
+          if (tid == 0) V.rej[t] = 1;
+          __syncthreads();
+          t = select_candidate(V, d, sh, best);
+          continue;
+        }
+        // x_P solves the current passive set, so the bordered solution is
+        // z_t = D_t^2 w_t / sc > 0 and z_P = x_P - D_P v (D_t w_t / sc)
+        const float yt = dt * best.hi / sc;
+        const float isc = 1.0f / sc;
+        int neg = 0;
+        for (int s2 = tid; s2 < p; s2 += kLHThreads) {
+          const float zf = fmaf(-V.Dsc[V.slotvar[s2]] * V.f3[s2], yt, V.xs[s2].hi);
+          V.zs[s2] = ff_make(zf);
+          neg |= (zf <= 0.0f) ? 1 : 0;
+        }
+        if (tid == 0) {
+          V.zs[p] = ff_make(dt * yt);
+          V.slotvar[p] = t;
+        }
+        if (accurate) {
+          __syncthreads();
+          passive_solve(V, sh, p + 1, true, sc, 2, true);
+          if (!ff_gt0(V.zs[p])) {
+            if (tid == 0) V.rej[t] = 1;
+            __syncthreads();
+            t = select_candidate(V, d, sh, best);
+            continue;
+          }
+          neg = 0;
+          for (int s2 = tid; s2 < p; s2 += kLHThreads) neg |= ff_le0(V.zs[s2]) ? 1 : 0;
+        }
+        // commit the bordered inverse: B += v v'/sc, new row/col -v/sc, corner 1/sc
+        {
+          const int warp = tid >> 5, lane = tid & 31;
+          for (int a = warp; a < p; a += kLHThreads / 32) {
+            const float fa = V.f3[a] * isc;
+            for (int c = lane; c < p; c += 32) V.B[a * V.ldB + c] = fmaf(fa, V.f3[c], V.B[a * V.ldB + c]);
           }
         }
+        for (int s2 = tid; s2 < p; s2 += kLHThreads) {
+          V.B[s2 * V.ldB + p] = -V.f3[s2] * isc;
+          V.B[p * V.ldB + s2] = -V.f3[s2] * isc;
+        }
+        if (tid == 0) {
+          V.B[p * V.ldB + p] = isc;
+          V.varslot[t] = p;
+          V.xs[p] = ff{0.0f, 0.0f};
+          sh.p = p + 1;
+        }
+        neg = __syncthreads_or(neg);
+        accepted = true;
+        need_inner = (neg != 0);
+        if (!neg) {
+          // x = z on the new passive set: swap the vectors instead of copying
+          ff *tmp = V.xs;
+          V.xs = V.zs;
+          V.zs = tmp;
+        }
+        break;
       }
-      valid = jj >= 0;
-      wv = bestl;
-      ff best;
-      bi = block_argmax_ff(valid, wv, jj, sh, best);
-      if (bi < 0 || !ff_gt(best, tol)) break;
-      const int t = bi;
-      const int p = sh.p;
-      // bordering: u = D Q[P, t] D_t, v = B u, sc = 1 - u'v
-      for (int s = tid; s < p; s += kLHThreads) {
-        const int v = V.slotvar[s];
-        V.f1[s] = jb.Qhi[(int64_t)v * (d + 1) + t] * V.Dsc[v] * V.Dsc[t];
-      }
-      __syncthreads();
-      apply_B(V, p, V.f1, V.f3);
-      __syncthreads();
-      float part = 0.0f;
-      for (int s = tid; s < p; s += kLHThreads) part = fmaf(V.f1[s], V.f3[s], part);
-      const float uv = block_sum_f(part, sh);
-      const float sc = 1.0f - uv;
-      if (!(sc > 1e-13f) || V.Dsc[t] == 0.0f) {
-        if (tid == 0) V.rej[t] = 1;
+      if (!accepted) {
+        if (accurate) break;
+        // verify the FP32 end point
+        const int p = sh.p;
+        if (p > 0) passive_solve(V, sh, p, false, 0.0f, 3);
+        int neg = 0;
+        for (int s = tid; s < p; s += kLHThreads) neg |= ff_le0(V.zs[s]) ? 1 : 0;
+        if (__syncthreads_or(neg)) {
+          accurate = true;
+          go_inner = true;
+          continue;
+        }
+        for (int s = tid; s < p; s += kLHThreads) V.xs[s] = V.zs[s];
         __syncthreads();
+        compute_w(V, d, p);
+        __syncthreads();
+        int up = 0;
+        for (int j = tid; j < d; j += kLHThreads) up |= (V.varslot[j] < 0 && ff_gt(V.w[j], tol)) ? 1 : 0;
+        if (__syncthreads_or(up)) {
+          accurate = true;
+          continue;
+        }
+        break;
+      }
+      if (outer >= max_outer) {
+        if (tid == 0) sh.status = RNNLS_EMAXITER;
+        __syncthreads();
+        break;
+      }
+      ++outer;
+      if (!need_inner) {
+        ++inner;  // the interpolation loop's check found every z_j > 0
         continue;
       }
-      if (tid == 0) V.slotvar[p] = t;
-      __syncthreads();
-      passive_solve(jb, V, sh, p + 1, true, sc, refine);
-      if (!ff_gt0(V.z[p])) {
-        if (tid == 0) V.rej[t] = 1;
-        __syncthreads();
-        continue;
-      }
-      // commit the bordered inverse: B += v v'/sc, new row/col -v/sc, corner 1/sc
-      for (int64_t e = tid; e < (int64_t)p * p; e += kLHThreads) {
-        const int a = (int)(e / p), c = (int)(e % p);
-        V.B[(int64_t)a * V.ldB + c] += V.f3[a] * V.f3[c] / sc;
-      }
-      for (int s = tid; s < p; s += kLHThreads) {
-        V.B[(int64_t)s * V.ldB + p] = -V.f3[s] / sc;
-        V.B[(int64_t)p * V.ldB + s] = -V.f3[s] / sc;
-      }
-      if (tid == 0) {
-        V.B[(int64_t)p * V.ldB + p] = 1.0f / sc;
-        V.varslot[t] = p;
-        sh.p = p + 1;
-      }
-      __syncthreads();
-      accepted = true;
-      break;
     }
-    if (!accepted) break;
-    if (outer >= max_outer) {
-      if (tid == 0) sh.status = RNNLS_EMAXITER;
-      __syncthreads();
-      break;
-    }
-    ++outer;
-    // interpolation loop; z holds the passive solution for the current slots
+    go_inner = false;
     for (;;) {
       ++inner;
       const int p = sh.p;
-      // alpha = min over slots with z <= 0 of x/(x - z), ties -> smallest variable
-      bool valid = false;
-      ff aval{0.0f, 0.0f};
-      int jv = -1;
-      for (int s = tid; s < p; s += kLHThreads) {
-        const int v = V.slotvar[s];
-        if (ff_le0(V.z[s])) {
-          const ff xv = V.x[v];
-          const ff a = ff_div(xv, ff_sub(xv, V.z[s]));
-          if (jv < 0 || ff_lt(a, aval) || (!ff_gt(a, aval) && v < jv)) {
-            aval = a;
-            jv = v;
-          }
-        }
-      }
-      valid = jv >= 0;
       ff amin;
-      const int jmin = block_argmin_ff(valid, aval, jv, sh, amin);
+      const int jmin = select_alpha(V, p, sh, amin);
       if (jmin < 0) {
-        for (int s = tid; s < p; s += kLHThreads) V.x[V.slotvar[s]] = V.z[s];
+        for (int s = tid; s < p; s += kLHThreads) V.xs[s] = V.zs[s];
         __syncthreads();
         break;
       }
@@ -593,41 +1011,34 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
         __syncthreads();
         break;
       }
-      const ff alpha = ff_neg(amin);  // argmin returned the negated value
-      for (int s = tid; s < p; s += kLHThreads) {
-        const int v = V.slotvar[s];
-        V.x[v] = ff_add(V.x[v], ff_mul(alpha, ff_sub(V.z[s], V.x[v])));
-      }
+      for (int s = tid; s < p; s += kLHThreads) V.xs[s] = ff_add(V.xs[s], ff_mul(amin, ff_sub(V.zs[s], V.xs[s])));
       __syncthreads();
-      if (tid == 0) V.x[jmin] = ff{0.0f, 0.0f};
+      if (tid == 0) V.xs[V.varslot[jmin]] = ff{0.0f, 0.0f};
       __syncthreads();
-      // drop every passive variable with x <= 0 (highest slot first keeps
-      // the slot moves simple)
       for (int s = p - 1; s >= 0; --s) {
-        const int v = V.slotvar[s];
-        if (ff_le0(V.x[v])) {
+        if (ff_le0(V.xs[s])) {
+          const int v = V.slotvar[s];
           __syncthreads();
-          if (tid == 0) {
-            V.x[v] = ff{0.0f, 0.0f};
-            V.varslot[v] = -1;
-          }
-          downdate(V, sh, s, sh.p);
+          if (tid == 0) V.varslot[v] = -1;
+          drop_slot(V, d, s, sh.p);
           if (tid == 0) sh.p = sh.p - 1;
           __syncthreads();
         }
       }
       if (sh.p == 0) break;
-      passive_solve(jb, V, sh, sh.p, false, 0.0f, refine);
+      passive_solve(V, sh, sh.p, false, 0.0f, accurate ? 2 : 0);
     }
     if (sh.status != RNNLS_OK) break;
   }
 
-  // outputs
-  compute_w(jb, V, sh.p);
+  // outputs: x, dual maximum over the active set, objective
+  compute_w(V, d, sh.p);
   __syncthreads();
-  for (int j = tid; j < d; j += kLHThreads) jb.x[j] = ff_to_double(V.x[j]);
-  // dual max over the active set and objective x'Qx - 2q'x + s's
-  ff dmax{-3.0e38f, 0.0f};
+  for (int j = tid; j < d; j += kLHThreads) {
+    const int s = V.varslot[j];
+    jb.x[j] = (s >= 0) ? ff_to_double(V.xs[s]) : 0.0;
+  }
+  ff dmax{0.0f, 0.0f};
   int dj = -1;
   for (int j = tid; j < d; j += kLHThreads)
     if (V.varslot[j] < 0 && (dj < 0 || ff_gt(V.w[j], dmax))) {
@@ -636,12 +1047,11 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
     }
   ff dbest;
   const int dbi = block_argmax_ff(dj >= 0, dmax, dj, sh, dbest);
-  // objective = s's - q'x - x'w  (since w = q - Qx: x'Qx = q'x - x'w)
+  // objective = s's - sum over P of x_j (q_j + w_j)   (w = q - Qx)
   ff part{0.0f, 0.0f};
-  for (int j = tid; j < d; j += kLHThreads) {
-    const ff xj = V.x[j];
-    const ff qj = qld(jb, j, d);
-    part = ff_add(part, ff_mul(xj, ff_add(qj, V.w[j])));
+  for (int s = tid; s < sh.p; s += kLHThreads) {
+    const int v = V.slotvar[s];
+    part = ff_add(part, ff_mul(V.xs[s], ff_add(V.qv[v], V.w[v])));
   }
   const ff qxpxw = block_sum_ff(part, sh);
   if (tid == 0 && jb.info) {
@@ -652,17 +1062,9 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
     inf.passive_count = sh.p;
     inf.tol = tol_d;
     inf.dual_max = (dbi >= 0) ? ff_to_double(dbest) : 0.0;
-    inf.objective = jb.Qd[(int64_t)d * (d + 1) + d] - ff_to_double(qxpxw);
+    inf.objective = jb.Qd[(int64_t)d * D1 + d] - ff_to_double(qxpxw);
     *jb.info = inf;
   }
-}
-
-size_t lh_smem_bytes(int d) {
-  const int ldB = (d % 2 == 0) ? d + 1 : d + 2;
-  auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  size_t b = r16((size_t)ldB * d * 4) + 2 * r16(d * 4) + 3 * r16((d + 1) * 4) + r16(d * 8) + r16((d + 1) * 8) +
-             r16(d * 8) + r16((d + 1) * 8) + r16((d + 1) * 4) + r16(d * 4) + r16(d);
-  return b;
 }
 
 __global__ void __launch_bounds__(kLHThreads, 1) lh_kernel(const lh_job *__restrict__ jobs, int max_outer_mul,
@@ -718,6 +1120,7 @@ gram_plan plan_gram(int64_t m, int d, int num_sms) {
   g.T = (d + 1 + kGT - 1) / kGT;
   g.ntiles = g.T * (g.T + 1) / 2;
   int64_t want = std::max<int64_t>(1, (2 * (int64_t)num_sms + g.ntiles - 1) / g.ntiles);
+  want = std::min<int64_t>(want, std::max<int64_t>(1, (m + 255) / 256));
   int64_t rps = (m + want - 1) / want;
   rps = std::max<int64_t>(kGT, (rps + kGT - 1) / kGT * kGT);
   g.rows_per_split = rps;
@@ -728,6 +1131,7 @@ gram_plan plan_gram(int64_t m, int d, int num_sms) {
 
 struct solve_ws {
   double *part;
+  double *part_abs;
   double *Qd;
   float *Qhi, *Qlo;
   double *colabs;
@@ -736,15 +1140,23 @@ struct solve_ws {
 
 size_t solve_ws_bytes(const gram_plan &g, int d, int64_t njobs) {
   const size_t D1 = d + 1;
-  return align_up((size_t)g.splits * g.ntiles * kGT * kGT * 8, 256) + align_up(D1 * D1 * 8, 256) +
+  return align_up((size_t)g.splits * g.ntiles * kGT * kGT * 8, 256) + align_up((size_t)g.splits * g.T * kGT * 8, 256) +
+         align_up(D1 * D1 * 8, 256) +
          2 * align_up(D1 * D1 * 4, 256) + align_up((size_t)d * 8, 256) + align_up((size_t)njobs * sizeof(lh_job), 256) +
          1024;
 }
 
-int lh_launch(rnnls_ctx *ctx, const lh_job *d_jobs, int64_t count, int dmax) {
+// Shared memory a Lawson-Hanson block needs, and whether its passive Q rows
+// fit there (else the block reads Q from global memory).
+constexpr size_t kLHStaticSmem = 2048;
+bool lh_q_fits(rnnls_ctx *ctx, int d) {
+  return lh_make_layout(d, true).bytes + kLHStaticSmem <= (size_t)ctx->max_smem_optin;
+}
+size_t lh_smem_for(rnnls_ctx *ctx, int d) { return lh_make_layout(d, lh_q_fits(ctx, d)).bytes; }
+
+int lh_launch(rnnls_ctx *ctx, const lh_job *d_jobs, int64_t count, size_t smem) {
   prof_scope ps(ctx, K_LH);
-  const size_t smem = lh_smem_bytes(dmax);
-  if (smem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
+  if (smem + kLHStaticSmem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
   RNNLS_CUDA_TRY(cudaFuncSetAttribute(lh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   lh_kernel<<<(unsigned)count, kLHThreads, smem, ctx->stream>>>(d_jobs, 3, 30);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
@@ -752,8 +1164,8 @@ int lh_launch(rnnls_ctx *ctx, const lh_job *d_jobs, int64_t count, int dmax) {
 
 int lh_launch_one(rnnls_ctx *ctx, const lh_job &jb) {
   prof_scope ps(ctx, K_LH);
-  const size_t smem = lh_smem_bytes(jb.d);
-  if (smem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
+  const size_t smem = lh_make_layout(jb.d, jb.q_smem != 0).bytes;
+  if (smem + kLHStaticSmem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
   static int attr_bytes = 0;
   if ((int)smem > attr_bytes) {
     RNNLS_CUDA_TRY(cudaFuncSetAttribute(lh_kernel_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -767,6 +1179,7 @@ template <typename T>
 int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r, int64_t d, double *x,
               rnnls_info *info) {
   const gram_plan g = plan_gram(r, (int)d, ctx->num_sms);
+  const bool fits = lh_q_fits(ctx, (int)d);
   const size_t bytes = solve_ws_bytes(g, (int)d, 1);
   int st = ensure_workspace(ctx, bytes);
   if (st) return st;
@@ -778,25 +1191,32 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
   w.Qhi = wc.take<float>(D1 * D1);
   w.Qlo = wc.take<float>(D1 * D1);
   w.colabs = wc.take<double>((size_t)d);
+  w.part_abs = wc.take<double>((size_t)g.splits * g.T * kGT);
   cudaStream_t s = ctx->stream;
   dim3 grid((unsigned)g.ntiles, (unsigned)g.splits);
-  {
+  if (sizeof(T) == 4) {
+    unsigned int *counters = nullptr;
+    st = ensure_counters(ctx, (size_t)g.ntiles, &counters);
+    if (st) return st;
     prof_scope ps(ctx, K_GRAM);
-    if (sizeof(T) == 4)
-      gram_f32_kernel<<<grid, 256, 0, s>>>((const float *)SA, ldsa, (const float *)Sb, r, (int)d, g.T,
-                                           g.rows_per_split, w.part);
-    else
+    gram_fused_f32_kernel<<<grid, 256, 0, s>>>((const float *)SA, ldsa, (const float *)Sb, r, (int)d, g.T,
+                                               g.rows_per_split, w.part, w.part_abs, counters, w.Qd, w.Qhi, w.Qlo,
+                                               w.colabs);
+  } else {
+    {
+      prof_scope ps(ctx, K_GRAM);
       gram_f64_kernel<<<grid, 256, 0, s>>>((const double *)SA, ldsa, (const double *)Sb, r, (int)d, g.T,
                                            g.rows_per_split, w.part);
-  }
-  {
-    prof_scope ps(ctx, K_GRAM_REDUCE);
-    gram_reduce_kernel<<<(unsigned)std::min<int64_t>((D1 * D1 + 255) / 256, 1024), 256, 0, s>>>(
-        w.part, g.splits, (int)d, g.T, w.Qd, w.Qhi, w.Qlo);
-  }
-  {
-    prof_scope ps(ctx, K_COLABS);
-    colabs_kernel<T><<<(unsigned)((d * 32 + 255) / 256), 256, 0, s>>>(SA, ldsa, r, (int)d, w.colabs);
+    }
+    {
+      prof_scope ps(ctx, K_GRAM_REDUCE);
+      gram_reduce_kernel<<<(unsigned)std::min<int64_t>((D1 * D1 + 255) / 256, 1024), 256, 0, s>>>(
+          w.part, g.splits, (int)d, g.T, w.Qd, w.Qhi, w.Qlo);
+    }
+    {
+      prof_scope ps(ctx, K_COLABS);
+      colabs_kernel<T><<<(unsigned)((d * 32 + 255) / 256), 256, 0, s>>>(SA, ldsa, r, (int)d, w.colabs);
+    }
   }
   lh_job jb;
   jb.Qd = w.Qd;
@@ -807,6 +1227,7 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
   jb.d = (int)d;
   jb.x = x;
   jb.info = info;
+  jb.q_smem = fits ? 1 : 0;
   if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
   return lh_launch_one(ctx, jb);
 }
@@ -833,9 +1254,12 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   }
   std::vector<gram_plan> plans((size_t)count);
   size_t bytes = align_up((size_t)count * sizeof(lh_job), 256) + 256;
+  size_t smem = 0;
   for (int64_t i = 0; i < count; ++i) {
-    plans[(size_t)i] = plan_gram(probs[i].r, (int)probs[i].d, std::max(1, ctx->num_sms / 8));
-    bytes += solve_ws_bytes(plans[(size_t)i], (int)probs[i].d, 0);
+    const int di = (int)probs[i].d;
+    plans[(size_t)i] = plan_gram(probs[i].r, di, std::max(1, ctx->num_sms / 8));
+    bytes += solve_ws_bytes(plans[(size_t)i], di, 0);
+    smem = std::max(smem, lh_smem_for(ctx, di));
   }
   int st = ensure_workspace(ctx, bytes);
   if (st) return st;
@@ -867,6 +1291,7 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
     jb.d = (int)pb.d;
     jb.x = pb.x;
     jb.info = pb.info;
+    jb.q_smem = lh_q_fits(ctx, (int)pb.d) ? 1 : 0;
   }
   if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
   // job table: staged through the context's pinned buffer (the previous
@@ -877,7 +1302,8 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   memcpy(ctx->pinned, jobs.data(), jbytes);
   RNNLS_CUDA_TRY(cudaMemcpyAsync(d_jobs, ctx->pinned, jbytes, cudaMemcpyHostToDevice, s));
   RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
-  return lh_launch(ctx, d_jobs, count, dmax);
+  (void)dmax;
+  return lh_launch(ctx, d_jobs, count, smem);
 }
 
 int residual_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
@@ -893,3 +1319,4 @@ int residual_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, in
 }
 
 }  // namespace rnnls
+

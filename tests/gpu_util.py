@@ -9,7 +9,11 @@ def dev_colmajor(a: np.ndarray, dtype=None):
     a = np.asarray(a)
     if dtype is not None:
         a = a.astype(dtype)
-    t = torch.from_numpy(np.ascontiguousarray(a.T)).cuda()  # (d, n) row-major == (n, d) column-major
+    src = torch.from_numpy(np.ascontiguousarray(a.T))
+    # (d, n) row-major == (n, d) column-major; torch.empty fixes the leading
+    # dimension at n even when d == 1
+    t = torch.empty(src.shape, dtype=src.dtype, device="cuda")
+    t.copy_(src)
     return t.t()
 
 

@@ -176,3 +176,20 @@ def test_full_size_sampled_entries(ctx, orc, config):
     # column norms: ||SX e_j||^2 estimates ||X e_j||^2 (Lemma 1) -- sanity bound
     nrm = np.linalg.norm(SAh[:, 0]) / np.linalg.norm(p.A[:, 0].astype(np.float64))
     assert 0.7 < nrm < 1.3
+
+
+@pytest.mark.parametrize("sms", [1, 3, 17, 150])
+def test_sketch_sm_cap(orc, sms):
+    """A cap on the sketch's SMs changes how columns are split over blocks
+    (whole columns per block when columns outnumber 8 blocks per SM-slot,
+    balanced step ranges with partial sums otherwise), not the result."""
+    import paper_0812_4547_gb300 as P
+
+    c = P.Context(0)
+    try:
+        c.set_sketch_sms(sms)
+        rng = np.random.default_rng(sms)
+        for n, d, r in [((1 << 18) + 5, 6, 3000), (50000, 40, 1500)]:
+            run_case(c, orc, rng.standard_normal((n, d)), rng.standard_normal(n), r, seed=sms, inst=4, mode=0)
+    finally:
+        c.close()

@@ -40,7 +40,9 @@ def _noalloc(B, stream, A, b, n, d, r, seed, with_idx=True):
     return st, SA, Sb, idx
 
 
-@pytest.mark.parametrize("n,d,r", [((1 << 20) + 77, 9, 4096), (70000, 65, 16384), (3000, 3, 100)])
+# the last case is too tall for the sign table to fit the scratch: the kernel then draws D itself
+@pytest.mark.parametrize("n,d,r", [((1 << 20) + 77, 9, 4096), (70000, 65, 16384), (3000, 3, 100),
+                                   ((1 << 26) + 3, 1, 2000)])
 def test_noalloc_matches_regular_sketch_on_two_calls(n, d, r):
     import torch
 
