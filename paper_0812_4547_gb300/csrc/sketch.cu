@@ -375,7 +375,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         first = part_block_of(u * P.J, B, P);
         last = part_block_of(u * P.J + P.J - 1, B, P);
       }
-      const int64_t kbase = kg * rpg;
       if (first == last) {
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
@@ -394,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < SLOTS; ++s) {
           const int32_t k = plan_k[((size_t)kg * SLOTS + s) * kThreads + tid];
           if (k < 0) continue;
-          part[((size_t)seg * P.U + u) * rpg + (k - kbase)] = poisoned ? __int_as_float(0x7fc00000) : acc[s];
+          part[((size_t)seg * P.U + u) * rpg + (size_t)s * kThreads + tid] = poisoned ? __int_as_float(0x7fc00000) : acc[s];
         }
         __threadfence();
         __syncthreads();
@@ -410,9 +409,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             sum[s] = 0.0f;
           }
           for (int64_t g = 0; g < nseg; ++g) {
-            const float *pg = part + ((size_t)g * P.U + u) * rpg - kbase;
+            const float *pg = part + ((size_t)g * P.U + u) * rpg + tid;
 #pragma unroll
-            for (int s = 0; s < SLOTS; ++s) sum[s] += (kk[s] >= 0) ? __ldcg(pg + kk[s]) : 0.0f;
+            for (int s = 0; s < SLOTS; ++s) sum[s] += (kk[s] >= 0) ? __ldcg(pg + (size_t)s * kThreads) : 0.0f;
           }
 #pragma unroll
           for (int s = 0; s < SLOTS; ++s) {
