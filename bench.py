@@ -96,8 +96,8 @@ def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged since."""
     try:
         with open(TRAFFIC_FILE) as f:
-            rec = json.load(f)[kernel]
-        if rec.get("source_sha256") == source_hash() and rec.get("workload") == workload:
+            rec = json.load(f)[kernel][workload]
+        if rec.get("source_sha256") == source_hash():
             return float(rec["dram_bytes_per_launch"])
     except Exception:
         pass
