@@ -62,6 +62,23 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(base: int, rank: int, ws: int) -> int:
+    """Seed of this rank's instance: each rank solves its own problem (weak scaling)."""
+    return base + 1000 * rank if ws > 1 else base
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks (the slowest rank sets the whole job's time)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_desc(cfg: int, p) -> dict:
     names = {1: "c1: A 4096x20 uniform FP64, r=512", 2: "c2: A 2^20x64 term-doc FP32, r=4096",
              3: "c3: A 2^22x128 term-doc FP32, r=8192"}
@@ -225,7 +242,7 @@ def main():
 
     dev = torch.device("cuda", local)
     base = workloads.CONFIGS[cfg]["seed"]
-    p = workloads.problem(cfg, seed=base + 1000 * rank) if ws > 1 else workloads.problem(cfg)
+    p = workloads.problem(cfg, seed=rank_seed(base, rank, ws))
     f64 = cfg == 1
     dt_np = np.float64 if f64 else np.float32
     tdt = torch.float64 if f64 else torch.float32
@@ -311,11 +328,8 @@ def main():
                 a = prof.get(k, (0, 0.0))
                 prof[k] = (a[0] + v[0], a[1] + v[1])
     clk = clocks.stop(w0, w1)
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     ms_per_step = ms / args.steps
     value = ws * args.steps / (ms / 1e3)
@@ -340,11 +354,7 @@ def main():
         seq_step(i)
         x_host.copy_(x, non_blocking=True)
         stream.synchronize()
-    e_dt = time.perf_counter() - e0
-    if ws > 1:
-        t = torch.tensor([e_dt], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e_dt = float(t.item())
+    e_dt = max_over_ranks(time.perf_counter() - e0, dev)
     e2e = {"value": ws * e2e_steps / e_dt, "unit": "solves/s",
            "h2d_bytes_per_step": int(A_host.numel() * elt + b_host.numel() * elt),
            "d2h_bytes_per_step": int(x_host.numel() * 8)}

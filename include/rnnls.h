@@ -126,6 +126,40 @@ int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, in
                  int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, float *SA, int64_t ldsa, float *Sb,
                  int32_t *idx, int64_t cap, int64_t *r_out);
 
+/* Sketch shared by several targets (the multiple right-hand-side problem
+ * min_{x_t >= 0} ||A x_t - B[:, t]||, which Sec. 5 lists as an extension;
+ * one S H D is applied to X = [A | B]):
+ *   SA[k, j] = s * sum_i H_n[idx[k], i] D_ii A[i, j]      (j < d)
+ *   SB[k, t] = s * sum_i H_n[idx[k], i] D_ii B[i, t]      (t < nrhs)
+ * iid sampling (r rows, s = 1/sqrt(r)), the same rows and signs as
+ * rnnls_sketch with the same seed and instance (which is the nrhs = 1 case).
+ * A: n_raw x d, lda >= n_raw.  B: n_raw x nrhs, ldb >= n_raw.  SA: r x d,
+ * ldsa >= r.  SB: r x nrhs, ldsb >= r.  idx: r int32 (nullable).  All device,
+ * column-major, caller-owned.  Errors: EINVAL (null pointer, a size < 1, a
+ * leading dimension too small), EUNSUPPORTED (n_raw > 2^28 or
+ * d + nrhs > 2^20), ENOMEM, ECUDA. */
+int rnnls_sketch_multi(rnnls_ctx *ctx, const float *A, int64_t lda, const float *B, int64_t ldb, int64_t n_raw,
+                       int64_t d, int64_t nrhs, int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa,
+                       float *SB, int64_t ldsb, int32_t *idx);
+
+/* Part of the sketch contributed by rows row0 .. row0 + rows - 1 of the
+ * full problem (A: n_raw x d, b: n_raw).  H_n = H_G (x) H_{n/G} for any
+ * split into row blocks, so with P_g this function's output for block g,
+ *   sum_g P_g = the output of rnnls_sketch (iid mode, same seed/instance),
+ * which lets each GPU sketch only the rows it holds and one sum-reduce of
+ * r x (d + 1) floats finish the sketch.  A and b hold ONLY the shard's rows
+ * that carry data, v = min(rows, n_raw - row0) of them (A: v x d,
+ * lda >= max(v, 1); b: v); the shard's rows past n_raw are zero.
+ * n_raw is the full problem's row count (it fixes the padding, the sampled
+ * rows and D).  row0 must be a multiple of 16384 and below the padded n;
+ * rows >= 1.  SA: r x d (ldsa >= r), Sb: r, idx: r (nullable; the full
+ * problem's sampled rows, the same in every shard).  row0 = 0 with
+ * rows >= n_raw is exactly rnnls_sketch; other shards need n > 8192
+ * (EUNSUPPORTED otherwise).  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+int rnnls_sketch_shard(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t row0,
+                       int64_t rows, int64_t d, int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa,
+                       float *Sb, int32_t *idx);
+
 /* The same sketch in FP64 throughout (for FP64 inputs). */
 int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double *b, int64_t n_raw, int64_t d,
                      int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, double *SA, int64_t ldsa,

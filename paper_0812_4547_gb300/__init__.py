@@ -113,6 +113,40 @@ class Context:
                   SA.data_ptr(), _ld(SA), Sb.data_ptr(), idx.data_ptr(), cap, want_count)
         return SA, Sb, idx, rows
 
+    def sketch_multi(self, A, Bm, r: int, seed: int, instance: int = 0, SA=None, SB=None, idx=None):
+        """SA, SB, idx: one sketch of [A | Bm] for the nrhs columns of Bm (FP32)."""
+        torch = _torch()
+        A, Bm = colmajor(A), colmajor(Bm)
+        n_raw, d = A.shape
+        if Bm.shape[0] != n_raw or A.dtype != torch.float32 or Bm.dtype != torch.float32:
+            raise ValueError("A and B must be FP32 with the same number of rows")
+        nrhs = Bm.shape[1]
+        if SA is None:
+            SA = torch.empty((d, r), dtype=A.dtype, device=A.device).t()
+        if SB is None:
+            SB = torch.empty((nrhs, r), dtype=A.dtype, device=A.device).t()
+        if idx is None:
+            idx = torch.empty(r, dtype=torch.int32, device=A.device)
+        B.rnnls_sketch_multi(self.handle, A.data_ptr(), _ld(A), Bm.data_ptr(), _ld(Bm), n_raw, d, nrhs, r, seed,
+                              instance, SA.data_ptr(), _ld(SA), SB.data_ptr(), _ld(SB), idx.data_ptr())
+        return SA, SB, idx
+
+    def sketch_shard(self, A_rows, b_rows, n_raw: int, row0: int, r: int, seed: int, instance: int = 0, SA=None,
+                     Sb=None, idx=None):
+        """This row block's additive part of the full sketch (FP32, iid); A_rows holds rows row0.. only."""
+        torch = _torch()
+        A_rows = colmajor(A_rows)
+        rows, d = A_rows.shape
+        if SA is None:
+            SA = torch.empty((d, r), dtype=A_rows.dtype, device=A_rows.device).t()
+        if Sb is None:
+            Sb = torch.empty(r, dtype=A_rows.dtype, device=A_rows.device)
+        if idx is None:
+            idx = torch.empty(r, dtype=torch.int32, device=A_rows.device)
+        B.rnnls_sketch_shard(self.handle, A_rows.data_ptr(), _ld(A_rows), b_rows.data_ptr(), n_raw, row0, rows, d, r,
+                              seed, instance, SA.data_ptr(), _ld(SA), Sb.data_ptr(), idx.data_ptr())
+        return SA, Sb, idx
+
     # -- solve ----------------------------------------------------------------------------
     def solve(self, SA, Sb, r: int | None = None, x=None, info=None):
         """x = argmin_{x>=0} ||SA x - Sb||^2 (Lawson-Hanson); returns (x, info bytes)."""

@@ -30,7 +30,7 @@ RNNLS_SAMPLE_BERNOULLI = 1
 EXPORTS = (
     "rnnls_create", "rnnls_destroy", "rnnls_set_stream", "rnnls_sketch", "rnnls_sketch_f64", "rnnls_solve",
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
-    "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms",
+    "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
 )
 
 
@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.rnnls_profile_begin.argtypes = [P, I32]
         L.rnnls_profile_end.argtypes = [P, ctypes.POINTER(rnnls_kernel_time), I32, ctypes.POINTER(I32)]
         L.rnnls_sketch_noalloc.argtypes = [P, P, I64, P, I64, I64, I64, U64, U64, P, I64, P, P]
+        L.rnnls_sketch_multi.argtypes = [P, P, I64, P, I64, I64, I64, I64, I64, U64, U64, P, I64, P, I64, P]
+        L.rnnls_sketch_shard.argtypes = [P, P, I64, P, I64, I64, I64, I64, I64, U64, U64, P, I64, P, P]
         L.rnnls_strerror.argtypes = [I32]
         L.rnnls_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -158,6 +160,18 @@ def rnnls_sketch(ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA, ldsa, S
 def rnnls_sketch_f64(ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA, ldsa, Sb, idx, cap, want_count=True):
     return _sketch(lib().rnnls_sketch_f64, "rnnls_sketch_f64", ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA,
                    ldsa, Sb, idx, cap, want_count)
+
+
+def rnnls_sketch_multi(ctx, A, lda, B, ldb, n_raw, d, nrhs, r, seed, instance, SA, ldsa, SB, ldsb, idx) -> None:
+    check(lib().rnnls_sketch_multi(ctypes.c_void_p(ctx), ctypes.c_void_p(A), lda, ctypes.c_void_p(B), ldb, n_raw, d,
+                                   nrhs, r, seed, instance, ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(SB), ldsb,
+                                   ctypes.c_void_p(idx)), "rnnls_sketch_multi")
+
+
+def rnnls_sketch_shard(ctx, A, lda, b, n_raw, row0, rows, d, r, seed, instance, SA, ldsa, Sb, idx) -> None:
+    check(lib().rnnls_sketch_shard(ctypes.c_void_p(ctx), ctypes.c_void_p(A), lda, ctypes.c_void_p(b), n_raw, row0,
+                                   rows, d, r, seed, instance, ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb),
+                                   ctypes.c_void_p(idx)), "rnnls_sketch_shard")
 
 
 def rnnls_solve(ctx, SA, ldsa, Sb, r, d, x, info) -> None:

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "kernels.h"
@@ -295,6 +296,10 @@ int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, in
   a.SA = SA;
   a.ldsa = ldsa;
   a.Sb = Sb;
+  a.ldb = n_raw;
+  a.nb = 1;
+  a.ldsb = ldsa;
+  a.chunk0 = 0;
   a.idx = rows_idx;
   st = sketch_f32(ctx, a, ctx->num_sms);
   if (st) return st;
@@ -307,6 +312,101 @@ int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, in
     }
   }
   return RNNLS_OK;
+}
+
+int rnnls_sketch_multi(rnnls_ctx *ctx, const float *A, int64_t lda, const float *B, int64_t ldb, int64_t n_raw,
+                       int64_t d, int64_t nrhs, int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa,
+                       float *SB, int64_t ldsb, int32_t *idx) {
+  if (!ctx || !A || !B || !SA || !SB) return RNNLS_EINVAL;
+  if (n_raw < 1 || d < 1 || nrhs < 1 || r < 1 || lda < n_raw || ldb < n_raw || ldsa < r || ldsb < r)
+    return RNNLS_EINVAL;
+  if (n_raw > kMaxRows || d + nrhs > (1 << 20) || r > ((int64_t)1 << 30)) return RNNLS_EUNSUPPORTED;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int L = log2_ceil64(n_raw);
+  aux_view av;
+  int st = get_aux(ctx, r, (int64_t)1 << L, idx == nullptr, av);
+  if (st) return st;
+  int32_t *rows_idx = idx ? idx : av.idx;
+  const bool fused_iid = ((int64_t)1 << L) > 8192;
+  double scale = 1.0 / sqrt((double)r);
+  if (!fused_iid) {
+    st = sample_rows(ctx, L, r, seed, instance, RNNLS_SAMPLE_IID, rows_idx, r, av, scale);
+    if (st) return st;
+  }
+  sketch_args_f32 a;
+  a.gen_iid = fused_iid ? 1 : 0;
+  a.A = A;
+  a.lda = lda;
+  a.b = B;
+  a.ldb = ldb;
+  a.nb = (int)nrhs;
+  a.n_raw = n_raw;
+  a.d = (int)d;
+  a.L = L;
+  a.chunk0 = 0;
+  a.r = r;
+  a.d_count = nullptr;
+  a.seed = seed;
+  a.inst = instance;
+  a.scale = (float)scale;
+  a.SA = SA;
+  a.ldsa = ldsa;
+  a.Sb = SB;
+  a.ldsb = ldsb;
+  a.idx = rows_idx;
+  return sketch_f32(ctx, a, ctx->num_sms);
+}
+
+int rnnls_sketch_shard(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t row0,
+                       int64_t rows, int64_t d, int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa,
+                       float *Sb, int32_t *idx) {
+  if (!ctx || !A || !b || !SA || !Sb) return RNNLS_EINVAL;
+  if (n_raw < 1 || d < 1 || r < 1 || rows < 1 || row0 < 0 || ldsa < r) return RNNLS_EINVAL;
+  if (lda < std::max<int64_t>(1, std::min<int64_t>(rows, n_raw - row0))) return RNNLS_EINVAL;
+  if (n_raw > kMaxRows || d > (1 << 20) || r > ((int64_t)1 << 30)) return RNNLS_EUNSUPPORTED;
+  const int L = log2_ceil64(n_raw);
+  const int64_t n = (int64_t)1 << L;
+  const int64_t group_rows = 4 * (int64_t)kM;  // shards start on a group of four chunks
+  if (row0 % group_rows != 0 || row0 >= n) return RNNLS_EINVAL;
+  // the whole problem in one piece: the plain sketch (also covers n <= 2^13)
+  if (row0 == 0 && rows >= n_raw)
+    return rnnls_sketch(ctx, A, lda, b, n_raw, d, r, seed, instance, RNNLS_SAMPLE_IID, SA, ldsa, Sb, idx, r, nullptr);
+  if (n <= 8192) return RNNLS_EUNSUPPORTED;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  aux_view av;
+  int st = get_aux(ctx, r, n, idx == nullptr, av);
+  if (st) return st;
+  sketch_args_f32 a;
+  a.gen_iid = 1;
+  a.A = A;
+  a.lda = lda;
+  a.b = b;
+  a.ldb = lda;
+  a.nb = 1;
+  // rows of this shard that hold data; the rest (and the padding) are zero
+  a.n_raw = std::max<int64_t>(0, std::min<int64_t>(rows, n_raw - row0));
+  a.d = (int)d;
+  a.L = L;
+  a.chunk0 = row0 / kM;
+  a.r = r;
+  a.d_count = nullptr;
+  a.seed = seed;
+  a.inst = instance;
+  a.scale = (float)(1.0 / sqrt((double)r));
+  a.SA = SA;
+  a.ldsa = ldsa;
+  a.Sb = Sb;
+  a.ldsb = ldsa;
+  a.idx = idx ? idx : av.idx;
+  if (a.n_raw == 0) {
+    // no data in this shard: its part is zero (the rows are still drawn)
+    RNNLS_CUDA_TRY(cudaMemset2DAsync(SA, (size_t)ldsa * sizeof(float), 0, (size_t)r * sizeof(float), (size_t)d,
+                                     ctx->stream));
+    RNNLS_CUDA_TRY(cudaMemsetAsync(Sb, 0, (size_t)r * sizeof(float), ctx->stream));
+    double scale = 0.0;
+    return sample_rows(ctx, L, r, seed, instance, RNNLS_SAMPLE_IID, a.idx, r, av, scale);
+  }
+  return sketch_f32(ctx, a, ctx->num_sms);
 }
 
 int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double *b, int64_t n_raw, int64_t d,

@@ -41,23 +41,31 @@ struct iid_gen {
   int L;
 };
 int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
-                      const iid_gen *gen, uint64_t *sign_table, int64_t sign_words, uint64_t seed, uint64_t inst);
+                      const iid_gen *gen, uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed,
+                      uint64_t inst);
 
 // ---- sketch (sketch.cu) ------------------------------------------------------
+// Columns of X = [A | B]: d columns of A, then nb columns of B (nb = 1: the
+// target b).  A row shard (rows chunk0 * 2^12 ... of the full problem, A and
+// B holding only those rows) gives its additive part of the full sketch.
 struct sketch_args_f32 {
   const float *A;
   int64_t lda;
-  const float *b;
-  int64_t n_raw;
+  const float *b;     // B (nb columns, leading dimension ldb)
+  int64_t ldb;
+  int nb;
+  int64_t n_raw;      // rows of A / B with data (of the shard)
   int d;
-  int L;
+  int L;              // log2 of the padded row count of the full problem
+  int64_t chunk0;     // full-problem index of the first 2^12-row chunk (multiple of 4)
   int64_t r;          // rows (iid) or capacity bound (Bernoulli)
   const int64_t *d_count;  // device row count (Bernoulli) or null
   uint64_t seed, inst;
   float scale;
   float *SA;
   int64_t ldsa;
-  float *Sb;
+  float *Sb;          // SB (nb columns, leading dimension ldsb)
+  int64_t ldsb;
   int32_t *idx;
   int gen_iid;  // 1: the sketch draws the iid rows itself (idx is output only)
 };

@@ -101,6 +101,10 @@ extern "C" int rnnls_sketch_noalloc(void *stream, const float *A, int64_t lda, c
   a.SA = SA;
   a.ldsa = ldsa;
   a.Sb = Sb;
+  a.ldb = n_raw;
+  a.nb = 1;
+  a.ldsb = ldsa;
+  a.chunk0 = 0;
   a.idx = rows;
   a.gen_iid = 0;
   return sketch_f32_scratch(s, a, num_sms, base + used, kNoAllocScratchBytes - used);

@@ -160,18 +160,19 @@ __global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(int32_t *__res
                                                                   int32_t *__restrict__ plan_k, int slots,
                                                                   int64_t rows_per_group, int gen_iid, uint64_t seed,
                                                                   uint64_t inst, int L, uint64_t *__restrict__ sign_table,
-                                                                  int64_t sign_words) {
+                                                                  int64_t sign_words, int64_t sign_block0) {
   __shared__ uint16_t rank_of[kPlanMaxRows];
   __shared__ uint32_t wcnt[kPlanThreads / 32][33];
   __shared__ uint32_t cnt[32], ov_start[32], free_start[32];
   const int g = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (g >= (int)gridDim.x - (int)((sign_words / 4 + kPlanThreads - 1) / kPlanThreads)) {
-    // sign words of D: word W is word W % 4 of Philox block W / 4 of stream 0
+    // sign words of D: word W (counted from the table's first chunk) is word
+    // W % 4 of Philox block sign_block0 + W / 4 of stream 0
     const int64_t first = (int64_t)(g - ((int)gridDim.x - (int)((sign_words / 4 + kPlanThreads - 1) / kPlanThreads)));
     const int64_t blk = first * kPlanThreads + tid;
     if (4 * blk < sign_words) {
-      const u64x4 u = philox4x64_10((uint64_t)blk, kStreamSigns, seed, inst);
+      const u64x4 u = philox4x64_10((uint64_t)(sign_block0 + blk), kStreamSigns, seed, inst);
 #pragma unroll
       for (int q = 0; q < 4; ++q) sign_table[4 * blk + q] = u.w[q];
     }
@@ -271,14 +272,15 @@ size_t plan_ws_bytes(int slots, int kgroups) {
 }
 
 int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
-                      const iid_gen *gen, uint64_t *sign_table, int64_t sign_words, uint64_t seed, uint64_t inst) {
+                      const iid_gen *gen, uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed,
+                      uint64_t inst) {
   if (plan.rows_per_group > kPlanMaxRows || plan.rows_per_group > (int64_t)plan.slots * kThreads)
     return RNNLS_EUNSUPPORTED;
   if (!sign_table) sign_words = 0;
   const int64_t sign_blocks = (sign_words / 4 + kPlanThreads - 1) / kPlanThreads;
   build_plan_kernel<<<(unsigned)(plan.kgroups + sign_blocks), kPlanThreads, 0, s>>>(
       idx, r, d_count, plan.pk, plan.k, plan.slots, plan.rows_per_group, gen ? 1 : 0, seed, inst, gen ? gen->L : 0,
-      sign_table, sign_words);
+      sign_table, sign_words, sign_block0);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 

@@ -174,8 +174,11 @@ struct step_cursor {
 // ---------------------------------------------------------------------------
 // The large-n sketch kernel (FP32).  Plan group kg's rows are entries
 // [kg][slot][thread] of plan_pk / plan_k (see the plan kernel).
-// tmA / tmB: column views (32, n_raw / 32, cols) of A and b for the tensor
-// copies (vec = 1); with vec = 0 the threads load X with plain loads.
+// Columns: d of A, then nb of B (outputs SA, SB).  jg0: full-problem index of
+// the first chunk group (row shards; 0 otherwise), which sets the Hadamard
+// signs and D's words.  tmA / tmB: column views (32, n_raw / 32, cols) of A
+// and B for the tensor copies (vec = 1); with vec = 0 the threads load X with
+// plain loads.
 // part: [segment][unit][rows_per_group] partial sums of split units;
 // counters: one per unit, zero before and after the launch.
 //
@@ -189,11 +192,12 @@ struct step_cursor {
 template <int SLOTS>
 __global__ void __launch_bounds__(kThreads, 1)
     sketch_srht_f32(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                    const float *__restrict__ A, int64_t lda, const float *__restrict__ b, int64_t n_raw, int d,
-                    srht_part P, int vec, uint64_t seed, uint64_t inst, const uint64_t *__restrict__ sign_table,
-                    const uint32_t *__restrict__ plan_pk,
+                    const float *__restrict__ A, int64_t lda, const float *__restrict__ Bm, int64_t ldb,
+                    int64_t n_raw, int d, int nb, int64_t jg0, srht_part P, int vec, uint64_t seed, uint64_t inst,
+                    const uint64_t *__restrict__ sign_table, const uint32_t *__restrict__ plan_pk,
                     const int32_t *__restrict__ plan_k, int64_t rpg, float *__restrict__ part, float scale,
-                    float *__restrict__ SA, int64_t ldsa, float *__restrict__ Sb, unsigned int *__restrict__ counters) {
+                    float *__restrict__ SA, int64_t ldsa, float *__restrict__ SB, int64_t ldsb,
+                    unsigned int *__restrict__ counters) {
   extern __shared__ __align__(1024) float dyn_smem[];  // kStages x kWorkers x kM (+ alignment slack)
   __shared__ __align__(16) uint32_t sgn[kStages][kWorkers][kM / 32];  // D's bits, 32-bit halves of the words
   __shared__ __align__(8) uint64_t mbar[kStages];
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t s0 = part_start(bid, B, P);
   const int64_t nsteps = part_start(bid + 1, B, P) - s0;
   if (nsteps <= 0) return;
-  const int64_t D1 = (int64_t)d + 1;
+  const int64_t D1 = (int64_t)d + nb;
   // stage buffers at a 16 KiB boundary: chunk slots are then addressed by OR
   const uint32_t raw_u32 = smem_u32(dyn_smem);
   const uint32_t stage_u32 = (raw_u32 + 16383u) & ~16383u;
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_arrive_expect_tx(bar, (uint32_t)(kWorkers * kM * sizeof(float)) + (sign_table ? 2048u : 0u));
     if (sign_table) bulk_g2s(smem_u32(&sgn[iq][0][0]), sign_table + 4 * ic.j * (kM / 64), 2048u, bar);
     const CUtensorMap *map = (ic.col < d) ? &tmA : &tmB;
-    const int z = (ic.col < d) ? ic.col : 0;
+    const int z = (ic.col < d) ? ic.col : ic.col - d;
 #pragma unroll
     for (int c = 0; c < kWorkers; ++c)
       tma_load_chunk(stage_u32 + (uint32_t)(iq * kStageFloats + c * kM) * 4u, map, (int)((4 * ic.j + c) * (kM / 32)),
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t *src = reinterpret_cast<const uint32_t *>(sign_table + 4 * j * (kM / 64));
       for (int i = tid; i < kWorkers * (kM / 32); i += kThreads) (&sgn[buf][0][0])[i] = src[i];
     } else if (wt < 16) {
-      const uint64_t c = (uint64_t)(4 * j + w);
+      const uint64_t c = (uint64_t)(4 * (j + jg0) + w);
       const u64x4 r4 = philox4x64_10(c * 16u + (uint64_t)wt, kStreamSigns, seed, inst);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // lines of this thread's two rows that the tensor copy does not cover
     // (all of them without tensor copies, else the partial last line)
     {
-      const float *x = (col < d) ? A + (int64_t)col * lda : b;
+      const float *x = (col < d) ? A + (int64_t)col * lda : Bm + (int64_t)(col - d) * ldb;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int64_t line = (4 * j + w) * (int64_t)(kM / 32) + 64 * h + wt;
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();  // the four transformed chunks are ready
 
     // combine: row (hq, c1, c2) adds (-1)^popcount(hq & j) (z0 + s1 z1 + s2 (z2 + s1 z3))[l]
-    const uint32_t jm = (uint32_t)j << 14;
+    const uint32_t jm = (uint32_t)(j + jg0) << 14;
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       const uint32_t p = pk[s];
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (col < d)
             SA[(int64_t)col * ldsa + k] = val;
           else
-            Sb[k] = val;
+            SB[(int64_t)(col - d) * ldsb + k] = val;
         }
       } else {
         const int64_t nseg = last - first + 1;
@@ -419,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (col < d)
               SA[(int64_t)col * ldsa + kk[s]] = scale * sum[s];
             else
-              Sb[kk[s]] = scale * sum[s];
+              SB[(int64_t)(col - d) * ldsb + kk[s]] = scale * sum[s];
           }
           if (tid == 0) counters[u] = 0u;
         }
@@ -435,16 +439,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) sketch_small(const T *__restrict__ A, int64_t lda, const T *__restrict__ b,
-                                                    int64_t n_raw, int d, int L, uint64_t seed, uint64_t inst,
-                                                    const int32_t *__restrict__ idx, int64_t r,
+                                                    int64_t ldb, int64_t n_raw, int d, int L, uint64_t seed,
+                                                    uint64_t inst, const int32_t *__restrict__ idx, int64_t r,
                                                     const int64_t *__restrict__ d_count, T scale, T *__restrict__ SA,
-                                                    int64_t ldsa, T *__restrict__ Sb) {
+                                                    int64_t ldsa, T *__restrict__ Sb, int64_t ldsb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = 1 << L;
   uint64_t *words = reinterpret_cast<uint64_t *>(smem_raw);  // max(n/64, 4) sign words
   T *buf = reinterpret_cast<T *>(words + (n / 64 > 4 ? n / 64 : 4));
   const int col = blockIdx.x;
-  const T *__restrict__ x = (col < d) ? A + (int64_t)col * lda : b;
+  const T *__restrict__ x = (col < d) ? A + (int64_t)col * lda : b + (int64_t)(col - d) * ldb;
   const int calls = (n + 255) / 256;
   for (int j = threadIdx.x; j < calls; j += blockDim.x) {
     const u64x4 u = philox4x64_10((uint64_t)j, kStreamSigns, seed, inst);
@@ -469,7 +473,7 @@ __global__ void __launch_bounds__(256) sketch_small(const T *__restrict__ A, int
   }
   int64_t rr = r;
   if (d_count) rr = min(r, *d_count);
-  T *out = (col < d) ? SA + (int64_t)col * ldsa : Sb;
+  T *out = (col < d) ? SA + (int64_t)col * ldsa : Sb + (int64_t)(col - d) * ldsb;
   for (int64_t k = threadIdx.x; k < rr; k += blockDim.x) out[k] = scale * buf[idx[k]];
 }
 
@@ -593,12 +597,12 @@ int launch_srht(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, co
   memset(&tmB, 0, sizeof(tmB));
   if (vec) {
     int st = column_map(&tmA, a.A, a.n_raw, a.d, a.lda);
-    if (!st) st = column_map(&tmB, a.b, a.n_raw, 1, a.n_raw);
+    if (!st) st = column_map(&tmB, a.b, a.n_raw, a.nb, a.ldb);
     if (st) return st;
   }
   sketch_srht_f32<SLOTS><<<(unsigned)blocks, kThreads, kSketchSmem, s>>>(
-      tmA, tmB, a.A, a.lda, a.b, a.n_raw, a.d, P, vec, a.seed, a.inst, signs, plan.pk, plan.k, plan.rows_per_group, part,
-      a.scale, a.SA, a.ldsa, a.Sb, counters);
+      tmA, tmB, a.A, a.lda, a.b, a.ldb, a.n_raw, a.d, a.nb, a.chunk0 / 4, P, vec, a.seed, a.inst, signs, plan.pk, plan.k,
+      plan.rows_per_group, part, a.scale, a.SA, a.ldsa, a.Sb, a.ldsb, counters);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 
@@ -632,9 +636,12 @@ srht_geom plan_geometry(const sketch_args_f32 &a, int sms, bool force_aligned) {
   g.plan.slots = pick_slots(a.r);
   g.plan.rows_per_group = (int64_t)kThreads * g.plan.slots;
   g.plan.kgroups = (int)((a.r + g.plan.rows_per_group - 1) / g.plan.rows_per_group);
-  g.vec = (((uintptr_t)a.A % 16 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.b % 16 == 0)) ? 1 : 0;
+  g.vec = (((uintptr_t)a.A % 16 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.b % 16 == 0) &&
+           (a.nb == 1 || a.ldb % 4 == 0))
+              ? 1
+              : 0;
   g.P.J = (a.n_raw + 4 * (int64_t)kM - 1) / (4 * (int64_t)kM);
-  g.P.U = (int64_t)g.plan.kgroups * (a.d + 1);
+  g.P.U = (int64_t)g.plan.kgroups * (a.d + a.nb);
   g.P.T = g.P.U * g.P.J;
   // many more columns than SMs: whole columns per block balance well enough
   g.P.aligned = (force_aligned || g.P.U >= 8 * (int64_t)sms) ? 1 : 0;
@@ -666,8 +673,9 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
   if (n <= 8192) {
     const size_t smem = (size_t)n * sizeof(float) + (size_t)std::max<int64_t>(n / 64, 4) * sizeof(uint64_t);
     prof_scope ps(ctx, K_SKETCH_SMALL);
-    sketch_small<float><<<(unsigned)(a.d + 1), 256, smem, s>>>(a.A, a.lda, a.b, a.n_raw, a.d, a.L, a.seed, a.inst,
-                                                               a.idx, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
+    sketch_small<float><<<(unsigned)(a.d + a.nb), 256, smem, s>>>(a.A, a.lda, a.b, a.ldb, a.n_raw, a.d, a.L, a.seed,
+                                                                  a.inst, a.idx, a.r, a.d_count, a.scale, a.SA,
+                                                                  a.ldsa, a.Sb, a.ldsb);
     return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
   }
   const int sms = (ctx->sketch_sms > 0) ? std::min(ctx->sketch_sms, num_sms) : num_sms;
@@ -686,8 +694,8 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
   {
     prof_scope ps(ctx, K_PLAN);
     iid_gen gen{a.seed, a.inst, a.L};
-    st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, a.gen_iid ? &gen : nullptr, signs, g.sign_words, a.seed,
-                           a.inst);
+    st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, a.gen_iid ? &gen : nullptr, signs, g.sign_words,
+                           16 * a.chunk0, a.seed, a.inst);
   }
   if (st) return st;
   prof_scope ps_main(ctx, K_SKETCH);
@@ -698,8 +706,9 @@ int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, vo
   const int64_t n = (int64_t)1 << a.L;
   if (n <= 8192) {
     const size_t smem = (size_t)n * sizeof(float) + (size_t)std::max<int64_t>(n / 64, 4) * sizeof(uint64_t);
-    sketch_small<float><<<(unsigned)(a.d + 1), 256, smem, s>>>(a.A, a.lda, a.b, a.n_raw, a.d, a.L, a.seed, a.inst,
-                                                               a.idx, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
+    sketch_small<float><<<(unsigned)(a.d + a.nb), 256, smem, s>>>(a.A, a.lda, a.b, a.ldb, a.n_raw, a.d, a.L, a.seed,
+                                                                  a.inst, a.idx, a.r, a.d_count, a.scale, a.SA,
+                                                                  a.ldsa, a.Sb, a.ldsb);
     return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
   }
   // counters first (zeroed by every call), then the plan, then partial sums;
@@ -718,8 +727,8 @@ int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, vo
   if (g.maxseg && cudaMemsetAsync(counters, 0, (size_t)g.P.U * sizeof(unsigned int), s) != cudaSuccess)
     return RNNLS_ECUDA;
   iid_gen gen{a.seed, a.inst, a.L};
-  int st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, a.gen_iid ? &gen : nullptr, signs, g.sign_words, a.seed,
-                             a.inst);
+  int st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, a.gen_iid ? &gen : nullptr, signs, g.sign_words,
+                             16 * a.chunk0, a.seed, a.inst);
   if (st) return st;
   return launch_srht_slots(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
 }
@@ -736,8 +745,9 @@ int sketch_f64(rnnls_ctx *ctx, const sketch_args_f64 &a) {
                                           (int)(8192 * sizeof(double) + 128 * sizeof(uint64_t))));
       attr = true;
     }
-    sketch_small<double><<<(unsigned)(a.d + 1), 256, smem, s>>>(a.A, a.lda, a.b, a.n_raw, a.d, a.L, a.seed, a.inst,
-                                                                a.idx, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
+    sketch_small<double><<<(unsigned)(a.d + 1), 256, smem, s>>>(a.A, a.lda, a.b, a.n_raw, a.n_raw, a.d, a.L, a.seed,
+                                                                a.inst, a.idx, a.r, a.d_count, a.scale, a.SA, a.ldsa,
+                                                                a.Sb, a.r);
     return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
   }
   const size_t zbytes = align_up((size_t)(a.d + 1) * n * sizeof(double), 256);

@@ -1,0 +1,96 @@
+"""GPU parity of the multi-target sketch and of the row-shard sketch.
+
+rnnls_sketch_multi applies one S H D to [A | B]: every target column must
+match the oracle's sketch of (A, B[:, t]) with the same seed, and the
+one-target case must equal rnnls_sketch exactly.  rnnls_sketch_shard gives
+a row block's part of the sketch: the parts of any split into blocks that
+start on 16384-row boundaries must add up to the full sketch.
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_util import dev_colmajor, dev_vec, host, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5  # FP32 sketch vs the FP64 oracle on the same FP32 bytes
+TOL_SUM = 1e-6  # sum of shard parts vs the one-piece FP32 sketch (different summation order)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_0812_4547_gb300 as P
+
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,d,nrhs,r", [(5000, 3, 4, 300), ((1 << 16) + 5, 6, 5, 700), (300000, 20, 33, 5000),
+                                        (1 << 18, 2, 3, 12000)])
+def test_sketch_multi_matches_oracle_per_target(ctx, orc, n, d, nrhs, r):
+    rng = np.random.default_rng(n + nrhs)
+    A = rng.standard_normal((n, d)).astype(np.float32)
+    Bm = rng.random((n, nrhs)).astype(np.float32)
+    SA, SB, idx = ctx.sketch_multi(dev_colmajor(A), dev_colmajor(Bm), r, seed=5, instance=1)
+    SA, SB, idx = host(SA), host(SB), host(idx)
+    for t in sorted({0, nrhs // 2, nrhs - 1}):
+        SA_o, Sb_o, idx_o = orc.sketch(A.astype(np.float64), Bm[:, t].astype(np.float64), r, 5, 1)
+        assert np.array_equal(idx, idx_o)
+        assert rel_fro(SA, SA_o) <= TOL_F32
+        assert rel_fro(SB[:, t], Sb_o) <= TOL_F32
+
+
+@pytest.mark.parametrize("n", [3000, (1 << 17) + 77])
+def test_sketch_multi_one_target_is_the_plain_sketch(ctx, n):
+    rng = np.random.default_rng(n)
+    A = dev_colmajor(rng.standard_normal((n, 7)), np.float32)
+    b = rng.standard_normal(n).astype(np.float32)
+    SA1, Sb1, idx1, _ = ctx.sketch(A, dev_vec(b), 2048, seed=9, instance=3)
+    SA2, SB2, idx2 = ctx.sketch_multi(A, dev_colmajor(b[:, None]), 2048, seed=9, instance=3)
+    assert np.array_equal(host(idx1), host(idx2))
+    assert np.array_equal(host(SA1), host(SA2))
+    assert np.array_equal(host(Sb1), host(SB2)[:, 0])
+
+
+def _bounds(n: int, parts: int):
+    """Row blocks of the padded n starting on multiples of 16384 (uneven when they must be)."""
+    groups = n // 16384
+    cuts = [round(g * groups / parts) * 16384 for g in range(parts + 1)]
+    return [(cuts[g], cuts[g + 1] - cuts[g]) for g in range(parts) if cuts[g + 1] > cuts[g]]
+
+
+@pytest.mark.parametrize("n_raw,d,r,parts", [((1 << 18) + 1000, 5, 3000, 2), ((1 << 18) + 1000, 5, 3000, 4),
+                                             (200000, 8, 5000, 3), (1 << 17, 3, 700, 8)])
+def test_shard_parts_add_up_to_the_sketch(ctx, orc, n_raw, d, r, parts):
+    import torch
+
+    rng = np.random.default_rng(n_raw + parts)
+    A = rng.standard_normal((n_raw, d)).astype(np.float32)
+    b = rng.standard_normal(n_raw).astype(np.float32)
+    SA_full, Sb_full, idx_full, _ = ctx.sketch(dev_colmajor(A), dev_vec(b), r, seed=13, instance=2)
+    n = orc.padded_n(n_raw)
+    SA_sum = torch.zeros((r, d), dtype=torch.float64, device="cuda")
+    Sb_sum = torch.zeros(r, dtype=torch.float64, device="cuda")
+    for row0, rows in _bounds(n, parts):
+        v = max(0, min(rows, n_raw - row0))
+        A_rows = dev_colmajor(A[row0:row0 + v] if v else np.zeros((1, d), np.float32))
+        b_rows = dev_vec(b[row0:row0 + v] if v else np.zeros(1, np.float32))
+        SA_g, Sb_g, idx_g = ctx.sketch_shard(A_rows, b_rows, n_raw, row0, r, seed=13, instance=2)
+        assert np.array_equal(host(idx_g), host(idx_full))
+        SA_sum += SA_g.double()
+        Sb_sum += Sb_g.double()
+    assert rel_fro(host(SA_sum), host(SA_full).astype(np.float64)) <= TOL_SUM
+    assert rel_fro(host(Sb_sum), host(Sb_full).astype(np.float64)) <= TOL_SUM
+    SA_o, Sb_o, _ = orc.sketch(A.astype(np.float64), b.astype(np.float64), r, 13, 2)
+    assert rel_fro(host(SA_sum), SA_o) <= TOL_F32
+    assert rel_fro(host(Sb_sum), Sb_o) <= TOL_F32
+
+
+def test_shard_rejects_unaligned_start(ctx):
+    import paper_0812_4547_gb300 as P
+
+    A = dev_colmajor(np.ones((20000, 2)), np.float32)
+    b = dev_vec(np.ones(20000), np.float32)
+    with pytest.raises(P.RNNLSError):
+        ctx.sketch_shard(A, b, 1 << 16, 1000, 100, seed=1)
