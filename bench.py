@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -81,7 +81,8 @@ def max_over_ranks(x: float, device) -> float:
 
 def workload_desc(cfg: int, p) -> dict:
     names = {1: "c1: A 4096x20 uniform FP64, r=512", 2: "c2: A 2^20x64 term-doc FP32, r=4096",
-             3: "c3: A 2^22x128 term-doc FP32, r=8192"}
+             3: "c3: A 2^22x128 term-doc FP32, r=8192",
+             4: "c4: A 2^20x100 term-doc FP32, 256 targets sharing one sketch, r=4096"}
     return {"workload": names[cfg], "n": int(p.n), "d": int(p.d), "r": int(p.r), "sampling": "iid",
             "l2": "inputs larger than L2 (no flush)" if p.A.nbytes > 129e6 else "inputs in L2 (small case)",
             "parallelism": "independent instance per GPU"}
@@ -183,7 +184,7 @@ def run_reference(args, cfg: int):
     import oracle
 
     oracle.build()
-    p = workloads.problem(cfg)
+    p = multi_problem(rank_seed(workloads.CONFIGS[4]["seed"], 0, 1)) if cfg == 4 else workloads.problem(cfg)
     threads = os.cpu_count() or 1
     for i in range(args.warmup):
         oracle.randomized_nnls(p.A, p.b, p.r, seed=i, nthreads=threads)
@@ -201,6 +202,21 @@ def run_reference(args, cfg: int):
                             "sample": f"{args.steps} full solves of the workload (FP64 C oracle, OpenMP over columns)"},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+class MultiProblem:
+    """Workload 4 (A shared by nrhs targets B) with the fields the single-target helpers read."""
+
+    def __init__(self, A, Bm, r):
+        self.A, self.B, self.r = A, Bm, r
+        self.b = Bm[:, 0]
+        self.n, self.d = A.shape
+        self.nrhs = Bm.shape[1]
+
+
+def multi_problem(seed: int) -> MultiProblem:
+    A, Bm, _, r = workloads.multi_rhs(seed=seed)
+    return MultiProblem(A, Bm, r)
 
 
 def cpu_baseline(p, seconds: float) -> dict:
@@ -242,6 +258,11 @@ def main():
 
     dev = torch.device("cuda", local)
     base = workloads.CONFIGS[cfg]["seed"]
+    if cfg == 4:
+        run_multi(args, ws, rank, local, dev)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
     p = workloads.problem(cfg, seed=rank_seed(base, rank, ws))
     f64 = cfg == 1
     dt_np = np.float64 if f64 else np.float32
@@ -413,6 +434,118 @@ def main():
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_multi(args, ws: int, rank: int, local: int, dev):
+    """Workload 4: one step sketches [A | B] once and solves all 256 targets on it
+    (rnnls_sketch_multi + rnnls_solve_multi); solves/s counts targets."""
+    import torch
+
+    import paper_0812_4547_gb300 as P
+    from paper_0812_4547_gb300 import _binding as B
+
+    p = multi_problem(rank_seed(workloads.CONFIGS[4]["seed"], rank, ws))
+    n, d, nrhs, r = p.n, p.d, p.nrhs, p.r
+    A_host = torch.from_numpy(np.ascontiguousarray(p.A.astype(np.float32).T)).pin_memory()
+    B_host = torch.from_numpy(np.ascontiguousarray(p.B.astype(np.float32).T)).pin_memory()
+    A = A_host.to(dev).t()
+    Bm = B_host.to(dev).t()
+    stream = torch.cuda.current_stream(dev)
+    ctx = P.Context(local, stream)
+    SA = torch.empty((d, r), dtype=torch.float32, device=dev).t()
+    SB = torch.empty((nrhs, r), dtype=torch.float32, device=dev).t()
+    idx = torch.empty(r, dtype=torch.int32, device=dev)
+    X = torch.empty((nrhs, d), dtype=torch.float64, device=dev).t()
+    infos = torch.zeros((nrhs, P.INFO_BYTES), dtype=torch.uint8, device=dev)
+    X_host = torch.empty((nrhs, d), dtype=torch.float64).pin_memory()
+
+    def step(i: int):
+        ctx.sketch_multi(A, Bm, r, seed=i, instance=rank, SA=SA, SB=SB, idx=idx)
+        ctx.solve_multi(SA, SB, r=r, X=X, infos=infos)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.15)
+    B.rnnls_profile_begin(ctx.handle, 16 * args.steps + 64)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    w0 = time.time()
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    prof = B.rnnls_profile_end(ctx.handle)
+    clk = clocks.stop(w0, w1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    value = ws * args.steps * nrhs / (ms / 1e3)
+
+    # e2e through the public calls: A and B in from pinned host memory, X back, every step
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, min(args.steps, 20))
+    for i in range(1 + e2e_steps):
+        if i == 1:
+            e0 = time.perf_counter()
+        A.copy_(A_host.t(), non_blocking=True)
+        Bm.copy_(B_host.t(), non_blocking=True)
+        step(i)
+        X_host.copy_(X.t(), non_blocking=True)
+        stream.synchronize()
+    e_dt = max_over_ranks(time.perf_counter() - e0, dev)
+    e2e = {"value": ws * e2e_steps * nrhs / e_dt, "unit": "solves/s",
+           "h2d_bytes_per_step": int((A_host.numel() + B_host.numel()) * 4),
+           "d2h_bytes_per_step": int(X_host.numel() * 8)}
+
+    # residual ratios (evaluation, off the timed path) for a few targets:
+    # x~ of the shared sketch vs the exact NNLS on the full A
+    step(0)
+    ratios = []
+    for t in (0, nrhs // 2, nrhs - 1):
+        bt = Bm[:, t].contiguous()
+        x_opt, _ = ctx.solve(A, bt, r=n)
+        xt = X[:, t].contiguous()
+        ratios.append(float(ctx.residual(A, bt, xt).item()) / float(ctx.residual(A, bt, x_opt).item()))
+    stat = [P.info_dict(infos[t])["status"] for t in range(nrhs)]
+
+    kname = "sketch_srht_f32"
+    launches, kms = prof[kname]
+    abytes = int(4 * n * (d + nrhs) + 4 * r * (d + nrhs) + 4 * r)
+    achieved = abytes / (kms / launches / 1e3) / 1e9
+    peak, peak_src = measured_hbm_peak()
+    wl = {"workload": "c4: A 2^20x100 term-doc FP32, 256 targets sharing one sketch, r=4096", "n": n, "d": d,
+          "nrhs": nrhs, "r": r, "sampling": "iid", "l2": "inputs larger than L2 (no flush)",
+          "parallelism": "independent instance per GPU",
+          "pipeline": "per step: one sketch of [A | B], one shared Gram, 256 Lawson-Hanson blocks"}
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded term-document-like stand-in for TechTC300)",
+        "config": wl,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": recorded_traffic(kname, wl["workload"]), "kernel": kname,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "algorithmic_bytes_per_launch": abytes, "avg_launch_us": 1e3 * kms / launches},
+        "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "e2e": e2e, "clocks": clk,
+        "residual_ratio": max(ratios), "residual_ratio_le_1.01": max(ratios) <= 1.01,
+        "solve_status_nonzero": int(sum(1 for x in stat if x != 0)),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    elif rank == 0:
+        out["cpu_baseline"] = None
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

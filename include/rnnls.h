@@ -185,6 +185,18 @@ int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, 
 int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,
                     double *x, rnnls_info *info);
 
+/* The small NNLS problems of Alg. 1 step 5 for nrhs targets that share one
+ * sketch (rnnls_sketch_multi): X[:, t] = argmin_{x >= 0} ||SA x - SB[:, t]||_2
+ * for t < nrhs, each by the Lawson-Hanson method of rnnls_solve with the
+ * same rules and tolerance; the Gram of SA is formed once for all targets.
+ * SA: r x d (ldsa >= r), SB: r x nrhs (ldsb >= r), FP32, device.  X: device
+ * FP64 d x nrhs, column-major, ldx >= d.  infos: device, nrhs entries
+ * (nullable).  Requires 1 <= d <= 256 (EUNSUPPORTED otherwise).  Errors:
+ * EINVAL, EUNSUPPORTED, ENOMEM, ECUDA; each target's own outcome is
+ * infos[t].status. */
+int rnnls_solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, int64_t ldsb, int64_t r,
+                      int64_t d, int64_t nrhs, double *X, int64_t ldx, rnnls_info *infos);
+
 /* Many independent small NNLS problems in one launch sequence (one
  * Lawson-Hanson block per problem, uneven d and r allowed).  `probs` is a
  * HOST array of `count` descriptors whose pointers are device pointers. */

@@ -148,6 +148,20 @@ class Context:
         return SA, Sb, idx
 
     # -- solve ----------------------------------------------------------------------------
+    def solve_multi(self, SA, SB, r: int | None = None, X=None, infos=None):
+        """X (d x nrhs FP64) and raw infos (nrhs x INFO_BYTES) for targets sharing the sketch SA."""
+        torch = _torch()
+        SA, SB = colmajor(SA), colmajor(SB)
+        r = SA.shape[0] if r is None else r
+        d, nrhs = SA.shape[1], SB.shape[1]
+        if X is None:
+            X = torch.empty((nrhs, d), dtype=torch.float64, device=SA.device).t()
+        if infos is None:
+            infos = torch.zeros((nrhs, INFO_BYTES), dtype=torch.uint8, device=SA.device)
+        B.rnnls_solve_multi(self.handle, SA.data_ptr(), _ld(SA), SB.data_ptr(), _ld(SB), r, d, nrhs, X.data_ptr(),
+                            _ld(X), infos.data_ptr())
+        return X, infos
+
     def solve(self, SA, Sb, r: int | None = None, x=None, info=None):
         """x = argmin_{x>=0} ||SA x - Sb||^2 (Lawson-Hanson); returns (x, info bytes)."""
         torch = _torch()

@@ -31,6 +31,7 @@ EXPORTS = (
     "rnnls_create", "rnnls_destroy", "rnnls_set_stream", "rnnls_sketch", "rnnls_sketch_f64", "rnnls_solve",
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
+    "rnnls_solve_multi",
 )
 
 
@@ -96,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_solve.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_f64.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_batched.argtypes = [P, ctypes.POINTER(rnnls_problem), I64, U32]
+        L.rnnls_solve_multi.argtypes = [P, P, I64, P, I64, I64, I64, I64, P, I64, P]
         L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_profile_begin.argtypes = [P, I32]
         L.rnnls_profile_end.argtypes = [P, ctypes.POINTER(rnnls_kernel_time), I32, ctypes.POINTER(I32)]
@@ -182,6 +184,11 @@ def rnnls_solve(ctx, SA, ldsa, Sb, r, d, x, info) -> None:
 def rnnls_solve_f64(ctx, SA, ldsa, Sb, r, d, x, info) -> None:
     check(lib().rnnls_solve_f64(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
                                 ctypes.c_void_p(x), ctypes.c_void_p(info)), "rnnls_solve_f64")
+
+
+def rnnls_solve_multi(ctx, SA, ldsa, SB, ldsb, r, d, nrhs, X, ldx, infos) -> None:
+    check(lib().rnnls_solve_multi(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(SB), ldsb, r, d,
+                                  nrhs, ctypes.c_void_p(X), ldx, ctypes.c_void_p(infos)), "rnnls_solve_multi")
 
 
 def rnnls_solve_batched(ctx, problems, flags: int = 0) -> None:

@@ -481,6 +481,15 @@ int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t coun
   return solve_batched(ctx, probs, count);
 }
 
+int rnnls_solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, int64_t ldsb, int64_t r,
+                      int64_t d, int64_t nrhs, double *X, int64_t ldx, rnnls_info *infos) {
+  if (!ctx || !SA || !SB || !X) return RNNLS_EINVAL;
+  if (r < 1 || d < 1 || nrhs < 1 || ldsa < r || ldsb < r || ldx < d) return RNNLS_EINVAL;
+  if (d > 256) return RNNLS_EUNSUPPORTED;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  return solve_multi(ctx, SA, ldsa, SB, ldsb, r, d, nrhs, X, ldx, infos);
+}
+
 int rnnls_residual(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
                    const double *x, double *out) {
   if (!ctx || !A || !b || !x || !out || n < 1 || d < 1 || lda < n) return RNNLS_EINVAL;

@@ -97,6 +97,9 @@ int solve_f32(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, in
 int solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d, double *x,
               rnnls_info *info);
 int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count);
+// nrhs targets sharing one sketch SA: X (d x nrhs, leading dimension ldx), infos nrhs (nullable)
+int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, int64_t ldsb, int64_t r, int64_t d,
+                int64_t nrhs, double *X, int64_t ldx, rnnls_info *infos);
 int residual_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
                  const double *x, double *out);
 

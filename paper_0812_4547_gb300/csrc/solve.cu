@@ -46,6 +46,11 @@ template <typename T>
 __device__ __forceinline__ const T *gram_col(const T *S, int64_t lds, const T *s, int d, int g) {
   return (g < d) ? S + (int64_t)g * lds : (g == d ? s : nullptr);
 }
+// column g of [S | s_0 .. s_{nb-1}] (targets with leading dimension ldt)
+__device__ __forceinline__ const float *gram_col_nb(const float *S, int64_t lds, const float *s, int64_t ldt, int d,
+                                                    int nb, int g) {
+  return (g < d) ? S + (int64_t)g * lds : (g < d + nb ? s + (int64_t)(g - d) * ldt : nullptr);
+}
 
 __global__ void __launch_bounds__(256) gram_f32_kernel(const float *__restrict__ S, int64_t lds,
                                                        const float *__restrict__ s, int64_t m, int d, int T,
@@ -165,7 +170,8 @@ __global__ void gram_reduce_kernel(const double *__restrict__ part, int splits, 
 // tile, reset by that block) adds the splits in order 0..splits-1 and writes
 // Q as FP64 and as float pairs, plus the column 1-norms.
 __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__restrict__ S, int64_t lds,
-                                                             const float *__restrict__ s, int64_t m, int d, int T,
+                                                             const float *__restrict__ s, int64_t ldt, int nb,
+                                                             int64_t m, int d, int T,
                                                              int64_t rows_per_split, double *__restrict__ part,
                                                              double *__restrict__ part_abs,
                                                              unsigned int *__restrict__ counters,
@@ -176,6 +182,8 @@ __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__rest
   __shared__ unsigned int last_flag;
   int ti, tj;
   tile_coords(blockIdx.x, T, ti, tj);
+  // target-by-target products are needed on the diagonal only
+  if (ti != tj && ti * kGT >= d) return;
   const int ntiles = T * (T + 1) / 2;
   const int splits = gridDim.y;
   const int64_t k0 = (int64_t)blockIdx.y * rows_per_split;
@@ -190,8 +198,8 @@ __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__rest
       const int e = threadIdx.x + 256 * q;
       const int kk = e & 31, cc = e >> 5;
       const int64_t k = kb + kk;
-      const float *ci = gram_col(S, lds, s, d, ti * kGT + cc);
-      const float *cj = gram_col(S, lds, s, d, tj * kGT + cc);
+      const float *ci = gram_col_nb(S, lds, s, ldt, d, nb, ti * kGT + cc);
+      const float *cj = gram_col_nb(S, lds, s, ldt, d, nb, tj * kGT + cc);
       const float vi = (ci && k < k1) ? ci[k] : 0.0f;
       Xi[kk][cc] = vi;
       Xj[kk][cc] = (cj && k < k1) ? cj[k] : 0.0f;
@@ -236,7 +244,7 @@ __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__rest
   __syncthreads();
   if (!last_flag) return;
   __threadfence();
-  const int D1 = d + 1;
+  const int D1 = d + nb;
   // fixed order sp = 0..splits-1; the thread's four positions in flight per sp
   double v4[4] = {0.0, 0.0, 0.0, 0.0};
   for (int sp = 0; sp < splits; ++sp) {
@@ -301,9 +309,10 @@ __global__ void colabs_kernel(const T *__restrict__ S, int64_t lds, int64_t m, i
 // Lawson-Hanson block.
 // ---------------------------------------------------------------------------
 struct lh_job {
-  const double *Qd;  // (d+1) x (d+1): Q, q = column d, ||s||^2 = entry (d, d)
-  const float *Qhi;
+  const double *Qd;  // Gram of [S | targets], leading dimension ldq: Q = leading d x d block,
+  const float *Qhi;  // q = column qcol, ||s||^2 = entry (qcol, qcol)
   const float *Qlo;
+  int ldq, qcol;
   const double *colabs;  // d column 1-norms of the sketch
   int64_t r;
   int d;
@@ -797,16 +806,17 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
     const int ld = odd_ld(D1);
     for (int e = tid; e < D1 * D1; e += kLHThreads) {
       const int i = e / D1, j = e - i * D1;
-      qh[i * ld + j] = jb.Qhi[e];
-      ql[i * ld + j] = jb.Qlo[e];
+      const int64_t src = (int64_t)(i < d ? i : jb.qcol) * jb.ldq + (j < d ? j : jb.qcol);
+      qh[i * ld + j] = jb.Qhi[src];
+      ql[i * ld + j] = jb.Qlo[src];
     }
     V.Qh = qh;
     V.Ql = ql;
     V.ldQ = ld;
   } else {
-    V.Qh = jb.Qhi;
+    V.Qh = jb.Qhi;  // read at rows and columns < d only
     V.Ql = jb.Qlo;
-    V.ldQ = D1;
+    V.ldQ = jb.ldq;
   }
   V.Dsc = (float *)(smem_raw + L.off_Dsc);
   V.qh = (float *)(smem_raw + L.off_qh);
@@ -827,7 +837,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
   if (tid == 0) {
     double n1 = 0.0;
     for (int j = 0; j < d; ++j) n1 = fmax(n1, jb.colabs[j]);
-    const double ss = jb.Qd[(int64_t)d * D1 + d];
+    const double ss = jb.Qd[(int64_t)jb.qcol * jb.ldq + jb.qcol];
     tol_d = 10.0 * 2.220446049250313e-16 * n1 * (double)max(jb.r, (int64_t)d) * sqrt(fmax(ss, 0.0));
     sh.p = 0;
     sh.status = RNNLS_OK;
@@ -836,7 +846,10 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
   const ff tol = ff_from_double(tol_d);
   {
     int bad = 0;
-    for (int64_t e = tid; e < (int64_t)D1 * D1; e += kLHThreads) bad |= !isfinite(jb.Qd[e]);
+    for (int64_t e = tid; e < (int64_t)D1 * D1; e += kLHThreads) {
+      const int64_t i = e / D1, j = e - i * D1;
+      bad |= !isfinite(jb.Qd[(i < d ? i : jb.qcol) * jb.ldq + (j < d ? j : jb.qcol)]);
+    }
     if (__syncthreads_or(bad)) {
       for (int j = tid; j < d; j += kLHThreads) jb.x[j] = 0.0;
       if (tid == 0 && jb.info) {
@@ -852,10 +865,10 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
     }
   }
   for (int j = tid; j < d; j += kLHThreads) {
-    const double qjj = jb.Qd[(int64_t)j * D1 + j];
+    const double qjj = jb.Qd[(int64_t)j * jb.ldq + j];
     const float dj = (qjj > 0.0) ? (float)(1.0 / sqrt(qjj)) : 0.0f;
     V.Dsc[j] = dj;
-    const ff qj{jb.Qhi[(int64_t)j * D1 + d], jb.Qlo[(int64_t)j * D1 + d]};
+    const ff qj{jb.Qhi[(int64_t)j * jb.ldq + jb.qcol], jb.Qlo[(int64_t)j * jb.ldq + jb.qcol]};
     V.qv[j] = qj;
     V.qh[j] = qj.hi * dj;
     V.varslot[j] = -1;
@@ -1062,7 +1075,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
     inf.passive_count = sh.p;
     inf.tol = tol_d;
     inf.dual_max = (dbi >= 0) ? ff_to_double(dbest) : 0.0;
-    inf.objective = jb.Qd[(int64_t)d * D1 + d] - ff_to_double(qxpxw);
+    inf.objective = jb.Qd[(int64_t)jb.qcol * jb.ldq + jb.qcol] - ff_to_double(qxpxw);
     *jb.info = inf;
   }
 }
@@ -1199,7 +1212,7 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
     st = ensure_counters(ctx, (size_t)g.ntiles, &counters);
     if (st) return st;
     prof_scope ps(ctx, K_GRAM);
-    gram_fused_f32_kernel<<<grid, 256, 0, s>>>((const float *)SA, ldsa, (const float *)Sb, r, (int)d, g.T,
+    gram_fused_f32_kernel<<<grid, 256, 0, s>>>((const float *)SA, ldsa, (const float *)Sb, r, 1, r, (int)d, g.T,
                                                g.rows_per_split, w.part, w.part_abs, counters, w.Qd, w.Qhi, w.Qlo,
                                                w.colabs);
   } else {
@@ -1222,6 +1235,8 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
   jb.Qd = w.Qd;
   jb.Qhi = w.Qhi;
   jb.Qlo = w.Qlo;
+  jb.ldq = (int)d + 1;
+  jb.qcol = (int)d;
   jb.colabs = w.colabs;
   jb.r = r;
   jb.d = (int)d;
@@ -1286,6 +1301,8 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
     jb.Qd = Qd;
     jb.Qhi = Qhi;
     jb.Qlo = Qlo;
+    jb.ldq = (int)pb.d + 1;
+    jb.qcol = (int)pb.d;
     jb.colabs = colabs;
     jb.r = pb.r;
     jb.d = (int)pb.d;
@@ -1304,6 +1321,60 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
   (void)dmax;
   return lh_launch(ctx, d_jobs, count, smem);
+}
+
+int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, int64_t ldsb, int64_t r, int64_t d,
+                int64_t nrhs, double *X, int64_t ldx, rnnls_info *infos) {
+  // one Gram of [SA | SB] (the target-by-target block only on its diagonal),
+  // then one Lawson-Hanson block per target, all reading the same Q
+  const int64_t D1 = d + nrhs;
+  const gram_plan g = plan_gram(r, (int)(D1 - 1), ctx->num_sms);
+  const bool fits = lh_q_fits(ctx, (int)d);
+  const size_t bytes = solve_ws_bytes(g, (int)(D1 - 1), nrhs);
+  int st = ensure_workspace(ctx, bytes);
+  if (st) return st;
+  ws_carver wc(ctx->ws);
+  solve_ws w;
+  w.part = wc.take<double>((size_t)g.splits * g.ntiles * kGT * kGT);
+  w.Qd = wc.take<double>((size_t)(D1 * D1));
+  w.Qhi = wc.take<float>((size_t)(D1 * D1));
+  w.Qlo = wc.take<float>((size_t)(D1 * D1));
+  w.colabs = wc.take<double>((size_t)D1);
+  w.part_abs = wc.take<double>((size_t)g.splits * g.T * kGT);
+  lh_job *d_jobs = wc.take<lh_job>((size_t)nrhs);
+  cudaStream_t s = ctx->stream;
+  unsigned int *counters = nullptr;
+  st = ensure_counters(ctx, (size_t)g.ntiles, &counters);
+  if (st) return st;
+  {
+    prof_scope ps(ctx, K_GRAM);
+    dim3 grid((unsigned)g.ntiles, (unsigned)g.splits);
+    gram_fused_f32_kernel<<<grid, 256, 0, s>>>(SA, ldsa, SB, ldsb, (int)nrhs, r, (int)d, g.T, g.rows_per_split, w.part,
+                                               w.part_abs, counters, w.Qd, w.Qhi, w.Qlo, w.colabs);
+  }
+  if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
+  std::vector<lh_job> jobs((size_t)nrhs);
+  for (int64_t t = 0; t < nrhs; ++t) {
+    lh_job &jb = jobs[(size_t)t];
+    jb.Qd = w.Qd;
+    jb.Qhi = w.Qhi;
+    jb.Qlo = w.Qlo;
+    jb.ldq = (int)D1;
+    jb.qcol = (int)(d + t);
+    jb.colabs = w.colabs;
+    jb.r = r;
+    jb.d = (int)d;
+    jb.x = X + t * ldx;
+    jb.info = infos ? infos + t : nullptr;
+    jb.q_smem = fits ? 1 : 0;
+  }
+  const size_t jbytes = (size_t)nrhs * sizeof(lh_job);
+  st = ensure_pinned(ctx, jbytes);
+  if (st) return st;
+  memcpy(ctx->pinned, jobs.data(), jbytes);
+  RNNLS_CUDA_TRY(cudaMemcpyAsync(d_jobs, ctx->pinned, jbytes, cudaMemcpyHostToDevice, s));
+  RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
+  return lh_launch(ctx, d_jobs, nrhs, lh_smem_for(ctx, (int)d));
 }
 
 int residual_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,

@@ -94,3 +94,49 @@ def test_shard_rejects_unaligned_start(ctx):
     b = dev_vec(np.ones(20000), np.float32)
     with pytest.raises(P.RNNLSError):
         ctx.sketch_shard(A, b, 1 << 16, 1000, 100, seed=1)
+
+
+def _infos(raw):
+    import paper_0812_4547_gb300 as P
+
+    return [P.info_dict(raw[t]) for t in range(raw.shape[0])]
+
+
+@pytest.mark.parametrize("m,d,nrhs,seed", [(300, 5, 7, 0), (4096, 64, 40, 1), (2000, 100, 256, 2), (8192, 128, 3, 3)])
+def test_solve_multi_matches_oracle_per_target(ctx, orc, m, d, nrhs, seed):
+    """Every target's Lawson-Hanson solve on the shared sketch: identical passive set, x within 1e-6."""
+    rng = np.random.default_rng(seed)
+    S = rng.standard_normal((m, d)).astype(np.float32)
+    Xt = np.maximum(rng.standard_normal((d, nrhs)), 0) * (rng.random((d, nrhs)) < 0.5)
+    SB = (S.astype(np.float64) @ Xt + 0.1 * rng.standard_normal((m, nrhs))).astype(np.float32)
+    X, raw = ctx.solve_multi(dev_colmajor(S), dev_colmajor(SB))
+    X = host(X)
+    infos = _infos(raw)
+    for t in sorted({0, 1 % nrhs, nrhs // 2, nrhs - 1}):
+        xo, io = orc.nnls(S.astype(np.float64), SB[:, t].astype(np.float64))
+        assert infos[t]["status"] == io["status"] == 0, (t, infos[t], io)
+        assert np.array_equal(X[:, t] > 0, xo > 0), t
+        assert np.linalg.norm(X[:, t] - xo) / max(np.linalg.norm(xo), 1e-300) <= 1e-6
+        assert infos[t]["passive_count"] == io["passive_count"]
+    assert all(inf["status"] == 0 for inf in infos)
+
+
+def test_multi_target_pipeline_end_to_end(ctx, orc):
+    """Workload-4 shape at reduced size: one sketch of [A | B], one shared Gram, per-target solves,
+    each equal to the single-target path of the same seed."""
+    A, Bm, _ = workloads_multi(n=1 << 16, d=20, nrhs=12)
+    SA, SB, idx = ctx.sketch_multi(dev_colmajor(A, np.float32), dev_colmajor(Bm, np.float32), 1024, seed=3, instance=0)
+    X, raw = ctx.solve_multi(SA, SB)
+    X = host(X)
+    for t in (0, 5, 11):
+        SA1, Sb1, _, _ = ctx.sketch(dev_colmajor(A, np.float32), dev_vec(Bm[:, t], np.float32), 1024, seed=3, instance=0)
+        x1, _ = ctx.solve(SA1, Sb1)
+        x1 = host(x1)
+        assert np.array_equal(X[:, t] > 0, x1 > 0)
+        assert np.linalg.norm(X[:, t] - x1) / max(np.linalg.norm(x1), 1e-300) <= 1e-6
+
+
+def workloads_multi(n, d, nrhs):
+    import workloads
+
+    return workloads.multi_rhs(n=n, d=d, nrhs=nrhs, r=1024)[:3]
