@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--batch-streams", type=int, default=8,
+                    help="workload 5: streams (one library context each) the instances are spread over")
+    ap.add_argument("--instances", type=int, default=None, help="workload 5: instance count (default 512)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -258,8 +261,8 @@ def main():
 
     dev = torch.device("cuda", local)
     base = workloads.CONFIGS[cfg]["seed"]
-    if cfg == 4:
-        run_multi(args, ws, rank, local, dev)
+    if cfg in (4, 5):
+        (run_multi if cfg == 4 else run_batch)(args, ws, rank, local, dev)
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
@@ -544,6 +547,163 @@ def run_multi(args, ws: int, rank: int, local: int, dev):
     elif rank == 0:
         out["cpu_baseline"] = None
     ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def device_batch(shapes, seed: int, dev):
+    """Workload-5 instances generated on the device (the recipe of workload 2:
+    Bernoulli(0.02) * LogNormal(0, 1) * (j+1)^-1.1 entries, x with half zeros,
+    b = A x + 5 % noise); torch's Philox generator, seeded per instance."""
+    import torch
+
+    out = []
+    hrng = np.random.default_rng(seed)
+    for i, (n_raw, d, r) in enumerate(shapes):
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed * 100003 + i)
+        colw = torch.arange(1, d + 1, device=dev, dtype=torch.float32).pow(-1.1)[:, None]
+        At = torch.where(torch.rand((d, n_raw), generator=g, device=dev) < 0.02,
+                         torch.randn((d, n_raw), generator=g, device=dev).exp_() * colw,
+                         torch.zeros((), device=dev))
+        x = workloads.planted_x(d, int(round(0.5 * d)), hrng)
+        y = At.t().double() @ torch.from_numpy(x).to(dev)
+        sigma = 0.05 * float(torch.linalg.vector_norm(y)) / math.sqrt(n_raw)
+        b = (y + sigma * torch.randn(n_raw, generator=g, device=dev, dtype=torch.float64)).float()
+        out.append((At.t(), b, r))
+    return out
+
+
+def run_batch(args, ws: int, rank: int, local: int, dev):
+    """Workload 5: 512 uneven instances per step, each sketched and solved by
+    the library, spread over --batch-streams streams and replayed as one CUDA
+    graph; also times the plain per-instance form (one stream, no graph)."""
+    import torch
+
+    import paper_0812_4547_gb300 as P
+    from paper_0812_4547_gb300 import _binding as B
+
+    c5 = workloads.CONFIGS[5]
+    shapes = workloads.batch_shapes(count=args.instances, seed=rank_seed(c5["seed"], rank, ws))
+    insts = device_batch(shapes, rank_seed(c5["seed"], rank, ws), dev)
+    count = len(insts)
+    S = max(1, args.batch_streams)
+    main_s = torch.cuda.Stream(dev)
+    streams = [torch.cuda.Stream(dev) for _ in range(S)]
+    ctxs = [P.Context(local, st) for st in streams]
+    bufs = []
+    for (A, b, r) in insts:
+        d = A.shape[1]
+        bufs.append((torch.empty((d, r), dtype=torch.float32, device=dev).t(), torch.empty(r, device=dev),
+                     torch.empty(r, dtype=torch.int32, device=dev), torch.empty(d, dtype=torch.float64, device=dev),
+                     torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device=dev)))
+    fork = torch.cuda.Event()
+    joins = [torch.cuda.Event() for _ in range(S)]
+
+    ctx_solve = P.Context(local, main_s)
+    problems = [(bufs[i][0], bufs[i][1], bufs[i][3], bufs[i][4]) for i in range(count)]
+
+    def enqueue(seed0: int, spread: bool = True):
+        fork.record(main_s)
+        for st in streams:
+            st.wait_event(fork)
+        if spread:
+            # phase 1: sketch of instance i on stream i % S; phase 2: every solve in one batched call
+            for i, (A, b, r) in enumerate(insts):
+                SA, Sb, idx, x, info = bufs[i]
+                ctxs[i % S].sketch(A, b, r, seed=seed0 + i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
+        else:
+            # the plain per-instance form: sketch and solve each instance in turn on one stream
+            for i, (A, b, r) in enumerate(insts):
+                SA, Sb, idx, x, info = bufs[i]
+                ctxs[0].sketch(A, b, r, seed=seed0 + i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
+                ctxs[0].solve(SA, Sb, r=r, x=x, info=info)
+        for k, st in enumerate(streams):
+            joins[k].record(st)
+            main_s.wait_event(joins[k])
+        if spread:
+            ctx_solve.solve_batched(problems)
+
+    with torch.cuda.stream(main_s):
+        for w in range(max(1, args.warmup)):
+            enqueue(0)
+        torch.cuda.synchronize()
+        # per-kernel times of one step (profiled, not in the graph)
+        for c in ctxs + [ctx_solve]:
+            B.rnnls_profile_begin(c.handle, 8 * count + 64)
+        enqueue(0)
+        torch.cuda.synchronize()
+        prof = {}
+        for c in ctxs + [ctx_solve]:
+            for k, v in B.rnnls_profile_end(c.handle).items():
+                a = prof.get(k, (0, 0.0))
+                prof[k] = (a[0] + v[0], a[1] + v[1])
+        # the plain per-instance form: one stream, no graph
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(main_s)
+        enqueue(0, spread=False)
+        t1.record(main_s)
+        torch.cuda.synchronize()
+        plain_ms = t0.elapsed_time(t1)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=main_s, capture_error_mode="relaxed"):
+            enqueue(0)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.15)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
+        ev0.record(main_s)
+        for _ in range(args.steps):
+            graph.replay()
+        ev1.record(main_s)
+        torch.cuda.synchronize()
+        w1 = time.time()
+        clk = clocks.stop(w0, w1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    value = ws * args.steps * count / (ms / 1e3)
+    stat = [P.info_dict(bufs[i][4])["status"] for i in range(count)]
+    total_bytes = sum(int(4 * A.shape[0] * (A.shape[1] + 1) + 4 * r * (A.shape[1] + 1) + 4 * r)
+                      for (A, b, r) in insts)
+    kname = "sketch_srht_f32"
+    launches, kms = prof.get(kname, (0, 0.0))
+    sketch_bytes = sum(int(4 * A.shape[0] * (A.shape[1] + 1) + 4 * r * (A.shape[1] + 1) + 4 * r)
+                       for (A, b, r) in insts if A.shape[0] > 8192)
+    achieved = sketch_bytes / (kms / 1e3) / 1e9 if kms > 0 else None
+    peak, peak_src = measured_hbm_peak()
+    wl = {"workload": f"c5: {count} uneven instances, n 2^U[14,20], d U{{16..200}}, r pow2 of 8(d+1)ln n",
+          "instances": count, "total_input_gb": total_bytes / 1e9, "sampling": "iid",
+          "l2": "inputs larger than L2 (no flush)", "parallelism": "independent instances per GPU",
+          "pipeline": f"one CUDA graph per step: the sketch of instance i on stream i % {S} (one library context "
+                      "per stream), then one rnnls_solve_batched over all instances; every replay redoes every "
+                      "kernel with the same seeds"}
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (term-document-like, generated on the device)",
+        "config": wl,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None, "kernel": kname,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "algorithmic_bytes_per_step": sketch_bytes, "kernel_ms_per_step": kms,
+                     "note": "sum over the step's sketch launches, timed by CUDA events in a profiled (non-graph) step"},
+        "plain_per_instance": {"value": ws * count / (plain_ms / 1e3), "unit": "solves/s",
+                               "ms_per_step": plain_ms, "form": "one stream, no graph"},
+        "kernel_ms_per_step": {k: v[1] for k, v in prof.items()},
+        "gpu_launches": int(args.steps * sum(v[0] for v in prof.values())),
+        "e2e": None, "clocks": clk,
+        "solve_status_nonzero": int(sum(1 for x in stat if x != 0)),
+        "cpu_baseline": None,
+    }
+    for c in ctxs + [ctx_solve]:
+        c.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
 

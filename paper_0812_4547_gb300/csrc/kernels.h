@@ -23,7 +23,7 @@ constexpr int kLogM = 12;
 constexpr int kM = 1 << kLogM;
 constexpr int kThreads = 256;                 // threads of a sketch block
 constexpr int kWorkers = 4;                   // chunks transformed together
-constexpr int kMaxSlots = 40;                 // plan rows per sketch thread
+constexpr int kMaxSlots = 128;                // plan rows per sketch thread (TMEM columns)
 constexpr int kPlanMaxRows = kThreads * kMaxSlots;  // rows per plan group
 
 struct plan_t {

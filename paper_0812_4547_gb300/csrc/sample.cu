@@ -152,16 +152,16 @@ int launch_sample_bernoulli(cudaStream_t s, uint64_t seed, uint64_t inst, int L,
 // k = row index in the sketch (-1: empty).  n <= 2^28 keeps h >> 2 below
 // 2^14.
 // ---------------------------------------------------------------------------
-constexpr int kPlanThreads = 1024;
+constexpr int kPlanThreads = 512;  // half an SM's registers: plans run beside other work
 
-__global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(int32_t *__restrict__ idx, int64_t r,
+__global__ void __launch_bounds__(kPlanThreads, 2) build_plan_kernel(int32_t *__restrict__ idx, int64_t r,
                                                                   const int64_t *__restrict__ d_count,
                                                                   uint32_t *__restrict__ plan_pk,
                                                                   int32_t *__restrict__ plan_k, int slots,
                                                                   int64_t rows_per_group, int gen_iid, uint64_t seed,
                                                                   uint64_t inst, int L, uint64_t *__restrict__ sign_table,
                                                                   int64_t sign_words, int64_t sign_block0) {
-  __shared__ uint16_t rank_of[kPlanMaxRows];
+  extern __shared__ uint16_t rank_of[];  // rows_per_group entries
   __shared__ uint32_t wcnt[kPlanThreads / 32][33];
   __shared__ uint32_t cnt[32], ov_start[32], free_start[32];
   const int g = blockIdx.x;
@@ -278,7 +278,15 @@ int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_
     return RNNLS_EUNSUPPORTED;
   if (!sign_table) sign_words = 0;
   const int64_t sign_blocks = (sign_words / 4 + kPlanThreads - 1) / kPlanThreads;
-  build_plan_kernel<<<(unsigned)(plan.kgroups + sign_blocks), kPlanThreads, 0, s>>>(
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(build_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kPlanMaxRows * sizeof(uint16_t))) != cudaSuccess)
+      return RNNLS_ECUDA;
+    attr_set = true;
+  }
+  const size_t smem = (size_t)plan.rows_per_group * sizeof(uint16_t);
+  build_plan_kernel<<<(unsigned)(plan.kgroups + sign_blocks), kPlanThreads, smem, s>>>(
       idx, r, d_count, plan.pk, plan.k, plan.slots, plan.rows_per_group, gen ? 1 : 0, seed, inst, gen ? gen->L : 0,
       sign_table, sign_words, sign_block0);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;

@@ -130,6 +130,27 @@ __device__ __forceinline__ void lds_x4(uint32_t a, float &z0, float &z1, float &
       : "r"(a));
 }
 
+// ---- tensor memory (TMEM) ----------------------------------------------------
+// The block allocates all 512 columns.  Thread (warp w, lane l) owns TMEM lane
+// 32 (w % 4) + l, columns (w / 4) * 2 kMaxSlots ...: its plan words first,
+// then its row sums (kMaxSlots each), moved eight columns at a time.
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t *r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(ta)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const uint32_t *r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(ta), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+constexpr uint32_t kTmemCols = 512;
+
 // Partition of the step list over the blocks.  Unit u = kg * (d + 1) + col
 // (plan group kg, column col) owns steps u*J .. u*J + J - 1.  Balanced:
 // block b takes steps [T b / B, T (b+1) / B).  Aligned: block b takes the
@@ -195,14 +216,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float *__restrict__ A, int64_t lda, const float *__restrict__ Bm, int64_t ldb,
                     int64_t n_raw, int d, int nb, int64_t jg0, srht_part P, int vec, uint64_t seed, uint64_t inst,
                     const uint64_t *__restrict__ sign_table, const uint32_t *__restrict__ plan_pk,
-                    const int32_t *__restrict__ plan_k, int64_t rpg, float *__restrict__ part, float scale,
-                    float *__restrict__ SA, int64_t ldsa, float *__restrict__ SB, int64_t ldsb,
+                    const int32_t *__restrict__ plan_k, int slots, int64_t rpg, float *__restrict__ part,
+                    float scale, float *__restrict__ SA, int64_t ldsa, float *__restrict__ SB, int64_t ldsb,
                     unsigned int *__restrict__ counters) {
   extern __shared__ __align__(1024) float dyn_smem[];  // kStages x kWorkers x kM (+ alignment slack)
   __shared__ __align__(16) uint32_t sgn[kStages][kWorkers][kM / 32];  // D's bits, 32-bit halves of the words
   __shared__ __align__(8) uint64_t mbar[kStages];
   __shared__ unsigned int last_flag;
   __shared__ int stalled;  // a tensor copy did not land within the wait limit
+  __shared__ uint32_t tmem_base_s;
 
   const int tid = threadIdx.x;
   const int w = tid >> 6;   // worker: chunk 4j + w of a step
@@ -224,7 +246,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_mbar_init();
     stalled = 0;
   }
+  // SLOTS > 0: that many plan rows per thread, words and sums in registers;
+  // SLOTS == 0: `slots` rows (a multiple of 8, up to kMaxSlots) kept in TMEM
+  if constexpr (SLOTS == 0) {
+    if (tid < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+  }
+  tmem_fence_before();
   __syncthreads();
+  tmem_fence_after();
+  const uint32_t t_pk = tmem_base_s + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * 2 * kMaxSlots);
+  const uint32_t t_acc = t_pk + kMaxSlots;
+  const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  constexpr int RS = SLOTS > 0 ? SLOTS : 1;
+  uint32_t pk_r[RS];
+  float acc_r[RS];
+#pragma unroll
+  for (int e = 0; e < RS; ++e) acc_r[e] = 0.0f;
 
   // thread 0: tensor copies of one step (4 chunks = 4 boxes of 32 x 128)
   step_cursor ic;
@@ -270,10 +312,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const bool signs_by_copy = vec && sign_table;
   if (!signs_by_copy) make_signs(cur.j, 0);
 
-  uint32_t pk[SLOTS];
-  float acc[SLOTS];
-#pragma unroll
-  for (int s = 0; s < SLOTS; ++s) acc[s] = 0.0f;
   int64_t kg_loaded = -1;
   int q = 0;
   uint32_t phase = 0;
@@ -281,9 +319,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int64_t ls = 0; ls < nsteps; ++ls) {
     const int64_t j = cur.j;
     const int col = cur.col;
-    if (cur.kg != kg_loaded) {
+    if (cur.kg != kg_loaded) {  // this plan group's words (row sums are zero here)
+      if constexpr (SLOTS > 0) {
 #pragma unroll
-      for (int s = 0; s < SLOTS; ++s) pk[s] = plan_pk[((size_t)cur.kg * SLOTS + s) * kThreads + tid];
+        for (int e = 0; e < SLOTS; ++e) pk_r[e] = plan_pk[((size_t)cur.kg * SLOTS + e) * kThreads + tid];
+      } else {
+        tmem_wait_st();
+        for (int s8 = 0; s8 < slots; s8 += 8) {
+          uint32_t r8[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) r8[e] = plan_pk[((size_t)cur.kg * slots + s8 + e) * kThreads + tid];
+          tmem_st8(t_pk + s8, r8);
+          tmem_st8(t_acc + s8, zero8);
+        }
+      }
       kg_loaded = cur.kg;
     }
     float *__restrict__ zw = stage + q * kStageFloats + w * kM;
@@ -350,17 +399,53 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();  // the four transformed chunks are ready
 
-    // combine: row (hq, c1, c2) adds (-1)^popcount(hq & j) (z0 + s1 z1 + s2 (z2 + s1 z3))[l]
+    // combine: row (hq, c1, c2) adds (-1)^popcount(hq & j) (z0 + s1 z1 + s2 (z2 + s1 z3))[l],
+    // eight rows at a time (plan words and sums move between TMEM and registers)
     const uint32_t jm = (uint32_t)(j + jg0) << 14;
+    if constexpr (SLOTS > 0) {
 #pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      const uint32_t p = pk[s];
-      float z0, z1, z2, z3;
-      lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
-      const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
-      const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
-      const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
-      acc[s] += xor_sign(t, (uint32_t)__popc(p & jm) << 31);
+      for (int e = 0; e < SLOTS; ++e) {
+        const uint32_t p = pk_r[e];
+        float z0, z1, z2, z3;
+        lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+        const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
+        const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
+        const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
+        acc_r[e] += xor_sign(t, (uint32_t)__popc(p & jm) << 31);
+      }
+    } else {
+      // batch k+1 is loaded from TMEM while batch k is combined
+      uint32_t pk[8], acc[8], pkn[8], accn[8];
+      tmem_wait_st();
+      tmem_ld8(t_pk, pk);
+      tmem_ld8(t_acc, acc);
+      tmem_wait_ld();
+      for (int s8 = 0; s8 < slots; s8 += 8) {
+        const bool more = s8 + 8 < slots;
+        if (more) {
+          tmem_ld8(t_pk + s8 + 8, pkn);
+          tmem_ld8(t_acc + s8 + 8, accn);
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const uint32_t p = pk[e];
+          float z0, z1, z2, z3;
+          lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+          const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
+          const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
+          const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
+          acc[e] = __float_as_uint(__uint_as_float(acc[e]) + xor_sign(t, (uint32_t)__popc(p & jm) << 31));
+        }
+        tmem_st8(t_acc + s8, acc);
+        if (more) {
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            pk[e] = pkn[e];
+            acc[e] = accn[e];
+          }
+        }
+      }
     }
     cur.next(P, D1);
     if (++q == kStages) {
@@ -379,58 +464,103 @@ __global__ void __launch_bounds__(kThreads, 1)
         first = part_block_of(u * P.J, B, P);
         last = part_block_of(u * P.J + P.J - 1, B, P);
       }
-      if (first == last) {
+      const int64_t nseg = last - first + 1;
+      const int64_t seg = bid - first;
+      const int nsl = SLOTS > 0 ? SLOTS : slots;
+      if constexpr (SLOTS > 0) {
+        if (nseg == 1) {
 #pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-          const int32_t k = plan_k[((size_t)kg * SLOTS + s) * kThreads + tid];
-          if (k < 0) continue;
-          const float val = poisoned ? __int_as_float(0x7fc00000) : scale * acc[s];
-          if (col < d)
-            SA[(int64_t)col * ldsa + k] = val;
-          else
-            SB[(int64_t)(col - d) * ldsb + k] = val;
+          for (int e = 0; e < RS; ++e) {
+            const int32_t k = plan_k[((size_t)kg * SLOTS + e) * kThreads + tid];
+            if (k < 0) continue;
+            const float val = poisoned ? __int_as_float(0x7fc00000) : scale * acc_r[e];
+            if (col < d)
+              SA[(int64_t)col * ldsa + k] = val;
+            else
+              SB[(int64_t)(col - d) * ldsb + k] = val;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < RS; ++e) {
+            const int32_t k = plan_k[((size_t)kg * SLOTS + e) * kThreads + tid];
+            if (k < 0) continue;
+            part[((size_t)seg * P.U + u) * rpg + (size_t)e * kThreads + tid] =
+                poisoned ? __int_as_float(0x7fc00000) : acc_r[e];
+          }
         }
+#pragma unroll
+        for (int e = 0; e < RS; ++e) acc_r[e] = 0.0f;
       } else {
-        const int64_t nseg = last - first + 1;
-        const int64_t seg = bid - first;
+        tmem_wait_st();
+        for (int s8 = 0; s8 < slots; s8 += 8) {
+          uint32_t acc[8];
+          tmem_ld8(t_acc + s8, acc);
+          tmem_wait_ld();
 #pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-          const int32_t k = plan_k[((size_t)kg * SLOTS + s) * kThreads + tid];
-          if (k < 0) continue;
-          part[((size_t)seg * P.U + u) * rpg + (size_t)s * kThreads + tid] = poisoned ? __int_as_float(0x7fc00000) : acc[s];
+          for (int e = 0; e < 8; ++e) {
+            const int32_t k = plan_k[((size_t)kg * slots + s8 + e) * kThreads + tid];
+            if (k < 0) continue;
+            const float a = poisoned ? __int_as_float(0x7fc00000) : __uint_as_float(acc[e]);
+            if (nseg == 1) {
+              if (col < d)
+                SA[(int64_t)col * ldsa + k] = scale * a;
+              else
+                SB[(int64_t)(col - d) * ldsb + k] = scale * a;
+            } else {
+              part[((size_t)seg * P.U + u) * rpg + (size_t)(s8 + e) * kThreads + tid] = a;
+            }
+          }
+          tmem_st8(t_acc + s8, zero8);
         }
+      }
+      if (nseg > 1) {
         __threadfence();
         __syncthreads();
         if (tid == 0) last_flag = (atomicAdd(&counters[u], 1u) == (unsigned int)(nseg - 1)) ? 1u : 0u;
         __syncthreads();
         if (last_flag) {
           __threadfence();
-          int32_t kk[SLOTS];
-          float sum[SLOTS];
+          // every row's segment loads in flight together (register variants),
+          // or 32 rows at a time (TMEM variant)
+          constexpr int RB = SLOTS > 0 ? SLOTS : 32;
+          for (int s0b = 0; s0b < nsl; s0b += RB) {
+            int32_t kk[RB];
+            float sum[RB];
 #pragma unroll
-          for (int s = 0; s < SLOTS; ++s) {
-            kk[s] = plan_k[((size_t)kg * SLOTS + s) * kThreads + tid];
-            sum[s] = 0.0f;
-          }
-          for (int64_t g = 0; g < nseg; ++g) {
-            const float *pg = part + ((size_t)g * P.U + u) * rpg + tid;
+            for (int e = 0; e < RB; ++e) {
+              kk[e] = (s0b + e < nsl) ? plan_k[((size_t)kg * slots + s0b + e) * kThreads + tid] : -1;
+              sum[e] = 0.0f;
+            }
+            for (int64_t g = 0; g < nseg; ++g) {
+              const float *pg = part + ((size_t)g * P.U + u) * rpg + (size_t)s0b * kThreads + tid;
+              float t[RB];
 #pragma unroll
-            for (int s = 0; s < SLOTS; ++s) sum[s] += (kk[s] >= 0) ? __ldcg(pg + (size_t)s * kThreads) : 0.0f;
-          }
+              for (int e = 0; e < RB; ++e) t[e] = (kk[e] >= 0) ? __ldcg(pg + (size_t)e * kThreads) : 0.0f;
 #pragma unroll
-          for (int s = 0; s < SLOTS; ++s) {
-            if (kk[s] < 0) continue;
-            if (col < d)
-              SA[(int64_t)col * ldsa + kk[s]] = scale * sum[s];
-            else
-              SB[(int64_t)(col - d) * ldsb + kk[s]] = scale * sum[s];
+              for (int e = 0; e < RB; ++e) sum[e] += t[e];
+            }
+#pragma unroll
+            for (int e = 0; e < RB; ++e) {
+              if (kk[e] < 0) continue;
+              if (col < d)
+                SA[(int64_t)col * ldsa + kk[e]] = scale * sum[e];
+              else
+                SB[(int64_t)(col - d) * ldsb + kk[e]] = scale * sum[e];
+            }
           }
           if (tid == 0) counters[u] = 0u;
         }
       }
-#pragma unroll
-      for (int s = 0; s < SLOTS; ++s) acc[s] = 0.0f;
     }
+  }
+  if constexpr (SLOTS == 0) {
+    tmem_wait_st();
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (tid < 32)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(kTmemCols)
+                   : "memory");
   }
 }
 
@@ -536,14 +666,12 @@ __global__ void combine_f64(const double *__restrict__ Z, int d, int64_t n, cons
   }
 }
 
-// rows of the plan per sketch thread: the smallest instantiated count that
-// holds r rows in one plan group (at most kMaxSlots, then several groups)
+// rows of the plan per sketch thread: enough for r rows in one plan group,
+// a multiple of 8 (TMEM moves eight at a time), at most kMaxSlots (then
+// several groups, each a pass over the data)
 int pick_slots(int64_t rows) {
   const int64_t need = (rows + kThreads - 1) / kThreads;
-  static const int opts[] = {1, 2, 4, 8, 16, 24, 32, kMaxSlots};
-  for (int s : opts)
-    if (need <= s) return s;
-  return kMaxSlots;
+  return (int)std::min<int64_t>(kMaxSlots, std::max<int64_t>(8, (need + 7) / 8 * 8));
 }
 
 typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -582,14 +710,14 @@ int column_map(CUtensorMap *m, const float *base, int64_t n_raw, int64_t cols, i
   return r == CUDA_SUCCESS ? RNNLS_OK : RNNLS_ECUDA;
 }
 
-template <int SLOTS>
 int launch_srht(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, const srht_part &P, int blocks, int vec,
                 const uint64_t *signs, float *part, unsigned int *counters) {
   static bool ready = false;
   if (!ready) {
-    if (cudaFuncSetAttribute(sketch_srht_f32<SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSketchSmem) !=
-        cudaSuccess)
-      return RNNLS_ECUDA;
+    for (auto kern : {sketch_srht_f32<0>, sketch_srht_f32<8>, sketch_srht_f32<16>, sketch_srht_f32<24>,
+                      sketch_srht_f32<32>, sketch_srht_f32<40>})
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSketchSmem) != cudaSuccess)
+        return RNNLS_ECUDA;
     ready = true;
   }
   CUtensorMap tmA, tmB;
@@ -600,24 +728,17 @@ int launch_srht(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, co
     if (!st) st = column_map(&tmB, a.b, a.n_raw, a.nb, a.ldb);
     if (st) return st;
   }
-  sketch_srht_f32<SLOTS><<<(unsigned)blocks, kThreads, kSketchSmem, s>>>(
+  // up to 40 rows per thread in registers, beyond that in TMEM
+  auto kern = plan.slots == 8    ? sketch_srht_f32<8>
+              : plan.slots == 16 ? sketch_srht_f32<16>
+              : plan.slots == 24 ? sketch_srht_f32<24>
+              : plan.slots == 32 ? sketch_srht_f32<32>
+              : plan.slots == 40 ? sketch_srht_f32<40>
+                                 : sketch_srht_f32<0>;
+  kern<<<(unsigned)blocks, kThreads, kSketchSmem, s>>>(
       tmA, tmB, a.A, a.lda, a.b, a.ldb, a.n_raw, a.d, a.nb, a.chunk0 / 4, P, vec, a.seed, a.inst, signs, plan.pk, plan.k,
-      plan.rows_per_group, part, a.scale, a.SA, a.ldsa, a.Sb, a.ldsb, counters);
+      plan.slots, plan.rows_per_group, part, a.scale, a.SA, a.ldsa, a.Sb, a.ldsb, counters);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
-}
-
-int launch_srht_slots(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, const srht_part &P, int blocks,
-                      int vec, const uint64_t *signs, float *part, unsigned int *counters) {
-  switch (plan.slots) {
-    case 1: return launch_srht<1>(s, a, plan, P, blocks, vec, signs, part, counters);
-    case 2: return launch_srht<2>(s, a, plan, P, blocks, vec, signs, part, counters);
-    case 4: return launch_srht<4>(s, a, plan, P, blocks, vec, signs, part, counters);
-    case 8: return launch_srht<8>(s, a, plan, P, blocks, vec, signs, part, counters);
-    case 16: return launch_srht<16>(s, a, plan, P, blocks, vec, signs, part, counters);
-    case 24: return launch_srht<24>(s, a, plan, P, blocks, vec, signs, part, counters);
-    case 32: return launch_srht<32>(s, a, plan, P, blocks, vec, signs, part, counters);
-    default: return launch_srht<kMaxSlots>(s, a, plan, P, blocks, vec, signs, part, counters);
-  }
 }
 
 // Launch geometry of the large-n sketch for `sms` usable SMs.
@@ -699,7 +820,7 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
   }
   if (st) return st;
   prof_scope ps_main(ctx, K_SKETCH);
-  return launch_srht_slots(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
+  return launch_srht(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
 }
 
 int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, void *scratch, size_t bytes) {
@@ -730,7 +851,7 @@ int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, vo
   int st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, a.gen_iid ? &gen : nullptr, signs, g.sign_words,
                              16 * a.chunk0, a.seed, a.inst);
   if (st) return st;
-  return launch_srht_slots(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
+  return launch_srht(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
 }
 
 int sketch_f64(rnnls_ctx *ctx, const sketch_args_f64 &a) {

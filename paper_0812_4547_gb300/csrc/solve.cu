@@ -52,51 +52,6 @@ __device__ __forceinline__ const float *gram_col_nb(const float *S, int64_t lds,
   return (g < d) ? S + (int64_t)g * lds : (g < d + nb ? s + (int64_t)(g - d) * ldt : nullptr);
 }
 
-__global__ void __launch_bounds__(256) gram_f32_kernel(const float *__restrict__ S, int64_t lds,
-                                                       const float *__restrict__ s, int64_t m, int d, int T,
-                                                       int64_t rows_per_split, double *__restrict__ part) {
-  __shared__ float Xi[kGT][kGT + 1];
-  __shared__ float Xj[kGT][kGT + 1];
-  int ti, tj;
-  tile_coords(blockIdx.x, T, ti, tj);
-  const int ntiles = T * (T + 1) / 2;
-  const int64_t k0 = (int64_t)blockIdx.y * rows_per_split;
-  const int64_t k1 = min(m, k0 + rows_per_split);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  dot2 acc[2][2];
-  for (int64_t kb = k0; kb < k1; kb += kGT) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + 256 * q;
-      const int kk = e & 31, cc = e >> 5;
-      const int64_t k = kb + kk;
-      const float *ci = gram_col(S, lds, s, d, ti * kGT + cc);
-      const float *cj = gram_col(S, lds, s, d, tj * kGT + cc);
-      Xi[kk][cc] = (ci && k < k1) ? ci[k] : 0.0f;
-      Xj[kk][cc] = (cj && k < k1) ? cj[k] : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < kGT; ++kk) {
-      const float a0 = Xi[kk][2 * ty], a1 = Xi[kk][2 * ty + 1];
-      const float b0 = Xj[kk][2 * tx], b1 = Xj[kk][2 * tx + 1];
-      acc[0][0].add_prod(a0, b0);
-      acc[0][1].add_prod(a0, b1);
-      acc[1][0].add_prod(a1, b0);
-      acc[1][1].add_prod(a1, b1);
-    }
-    __syncthreads();
-  }
-  double *out = part + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (kGT * kGT);
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const ff v = acc[a][c].value();
-      out[(2 * ty + a) * kGT + 2 * tx + c] = (double)v.hi + (double)v.lo;
-    }
-}
-
 __global__ void __launch_bounds__(256) gram_f64_kernel(const double *__restrict__ S, int64_t lds,
                                                        const double *__restrict__ s, int64_t m, int d, int T,
                                                        int64_t rows_per_split, double *__restrict__ part) {
@@ -169,9 +124,9 @@ __global__ void gram_reduce_kernel(const double *__restrict__ part, int splits, 
 // |.|-sums of its columns); the last block to finish a tile (counter per
 // tile, reset by that block) adds the splits in order 0..splits-1 and writes
 // Q as FP64 and as float pairs, plus the column 1-norms.
-__global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__restrict__ S, int64_t lds,
-                                                             const float *__restrict__ s, int64_t ldt, int nb,
-                                                             int64_t m, int d, int T,
+__device__ __forceinline__ void gram_fused_block(int tile, int split, int splits, const float *__restrict__ S,
+                                                 int64_t lds, const float *__restrict__ s, int64_t ldt, int nb,
+                                                 int64_t m, int d, int T,
                                                              int64_t rows_per_split, double *__restrict__ part,
                                                              double *__restrict__ part_abs,
                                                              unsigned int *__restrict__ counters,
@@ -180,13 +135,13 @@ __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__rest
   __shared__ float Xi[kGT][kGT + 1];
   __shared__ float Xj[kGT][kGT + 1];
   __shared__ unsigned int last_flag;
+  (void)splits;
   int ti, tj;
-  tile_coords(blockIdx.x, T, ti, tj);
+  tile_coords(tile, T, ti, tj);
   // target-by-target products are needed on the diagonal only
   if (ti != tj && ti * kGT >= d) return;
   const int ntiles = T * (T + 1) / 2;
-  const int splits = gridDim.y;
-  const int64_t k0 = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t k0 = (int64_t)split * rows_per_split;
   const int64_t k1 = min(m, k0 + rows_per_split);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool diag = (ti == tj);
@@ -217,7 +172,7 @@ __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__rest
     }
     __syncthreads();
   }
-  double *out = part + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (kGT * kGT);
+  double *out = part + ((int64_t)split * ntiles + tile) * (kGT * kGT);
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -232,13 +187,13 @@ __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__rest
       const ff v = absacc[q].value();
       double t = (double)v.hi + (double)v.lo;
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if ((threadIdx.x & 31) == 0) part_abs[(int64_t)blockIdx.y * (T * kGT) + ti * kGT + (threadIdx.x >> 5) + 8 * q] = t;
+      if ((threadIdx.x & 31) == 0) part_abs[(int64_t)split * (T * kGT) + ti * kGT + (threadIdx.x >> 5) + 8 * q] = t;
     }
   }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int done = atomicAdd(&counters[blockIdx.x], 1u);
+    const unsigned int done = atomicAdd(&counters[tile], 1u);
     last_flag = (done == (unsigned int)(splits - 1)) ? 1u : 0u;
   }
   __syncthreads();
@@ -248,7 +203,7 @@ __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__rest
   // fixed order sp = 0..splits-1; the thread's four positions in flight per sp
   double v4[4] = {0.0, 0.0, 0.0, 0.0};
   for (int sp = 0; sp < splits; ++sp) {
-    const double *src = part + ((int64_t)sp * ntiles + blockIdx.x) * (kGT * kGT);
+    const double *src = part + ((int64_t)sp * ntiles + tile) * (kGT * kGT);
     double t4[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) t4[u] = __ldcg(src + threadIdx.x + 256 * u);
@@ -279,7 +234,47 @@ __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__rest
       colabs[col] = v;
     }
   }
-  if (threadIdx.x == 0) counters[blockIdx.x] = 0u;
+  if (threadIdx.x == 0) counters[tile] = 0u;
+}
+
+__global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__restrict__ S, int64_t lds,
+                                                             const float *__restrict__ s, int64_t ldt, int nb,
+                                                             int64_t m, int d, int T, int64_t rows_per_split,
+                                                             double *__restrict__ part, double *__restrict__ part_abs,
+                                                             unsigned int *__restrict__ counters,
+                                                             double *__restrict__ Qd, float *__restrict__ Qhi,
+                                                             float *__restrict__ Qlo, double *__restrict__ colabs) {
+  gram_fused_block((int)blockIdx.x, (int)blockIdx.y, (int)gridDim.y, S, lds, s, ldt, nb, m, d, T, rows_per_split, part,
+                   part_abs, counters, Qd, Qhi, Qlo, colabs);
+}
+
+// Many problems' Grams in one launch: block b belongs to the problem p with
+// first[p] <= b < first[p + 1] (tiles x splits blocks each).
+struct gram_job {
+  const float *S;
+  const float *s;
+  int64_t lds, m, rows_per_split;
+  int d, T, ntiles, splits;
+  double *part, *part_abs, *Qd, *colabs;
+  float *Qhi, *Qlo;
+  unsigned int *counters;
+};
+
+__global__ void __launch_bounds__(256) gram_batched_f32_kernel(const gram_job *__restrict__ jobs,
+                                                               const int64_t *__restrict__ first, int count) {
+  int lo = 0, hi = count - 1;
+  const int64_t bid = blockIdx.x;
+  while (lo < hi) {  // last p with first[p] <= bid
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= bid)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const gram_job jb = jobs[lo];
+  const int64_t local = bid - first[lo];
+  gram_fused_block((int)(local % jb.ntiles), (int)(local / jb.ntiles), jb.splits, jb.S, jb.lds, jb.s, jb.m, 1, jb.m,
+                   jb.d, jb.T, jb.rows_per_split, jb.part, jb.part_abs, jb.counters, jb.Qd, jb.Qhi, jb.Qlo, jb.colabs);
 }
 
 // ||S||_1 = max_j sum_k |S_kj| (compensated), one warp per column.
@@ -1260,66 +1255,88 @@ int solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, 
 }
 
 int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
-  // Gram per problem (tile kernels), then one Lawson-Hanson launch over all
-  int dmax = 1;
-  int64_t rmax = 1;
-  for (int64_t i = 0; i < count; ++i) {
-    dmax = std::max<int>(dmax, (int)probs[i].d);
-    rmax = std::max<int64_t>(rmax, probs[i].r);
-  }
+  // one launch for every problem's Gram, then one Lawson-Hanson launch over all
   std::vector<gram_plan> plans((size_t)count);
-  size_t bytes = align_up((size_t)count * sizeof(lh_job), 256) + 256;
+  const size_t tbytes = align_up((size_t)count * sizeof(gram_job), 256) +
+                        align_up((size_t)(count + 1) * sizeof(int64_t), 256) +
+                        align_up((size_t)count * sizeof(lh_job), 256);
+  size_t bytes = tbytes + 256;
   size_t smem = 0;
+  int64_t tiles = 0;
   for (int64_t i = 0; i < count; ++i) {
     const int di = (int)probs[i].d;
     plans[(size_t)i] = plan_gram(probs[i].r, di, std::max(1, ctx->num_sms / 8));
     bytes += solve_ws_bytes(plans[(size_t)i], di, 0);
     smem = std::max(smem, lh_smem_for(ctx, di));
+    tiles += plans[(size_t)i].ntiles;
   }
   int st = ensure_workspace(ctx, bytes);
   if (st) return st;
+  unsigned int *counters = nullptr;
+  st = ensure_counters(ctx, (size_t)tiles, &counters);
+  if (st) return st;
+  st = ensure_pinned(ctx, tbytes);
+  if (st) return st;
   ws_carver wc(ctx->ws);
-  lh_job *d_jobs = wc.take<lh_job>((size_t)count);
-  std::vector<lh_job> jobs((size_t)count);
-  cudaStream_t s = ctx->stream;
+  char *d_tables = wc.take<char>(tbytes);
+  char *h_tables = (char *)ctx->pinned;
+  gram_job *gj = (gram_job *)h_tables;
+  int64_t *first = (int64_t *)(h_tables + align_up((size_t)count * sizeof(gram_job), 256));
+  lh_job *jobs = (lh_job *)(h_tables + align_up((size_t)count * sizeof(gram_job), 256) +
+                            align_up((size_t)(count + 1) * sizeof(int64_t), 256));
+  int64_t blocks = 0;
   for (int64_t i = 0; i < count; ++i) {
     const rnnls_problem &pb = probs[i];
     const gram_plan &g = plans[(size_t)i];
     const size_t D1 = pb.d + 1;
-    double *part = wc.take<double>((size_t)g.splits * g.ntiles * kGT * kGT);
-    double *Qd = wc.take<double>(D1 * D1);
-    float *Qhi = wc.take<float>(D1 * D1);
-    float *Qlo = wc.take<float>(D1 * D1);
-    double *colabs = wc.take<double>((size_t)pb.d);
-    dim3 grid((unsigned)g.ntiles, (unsigned)g.splits);
-    gram_f32_kernel<<<grid, 256, 0, s>>>(pb.SA, pb.ldsa, pb.Sb, pb.r, (int)pb.d, g.T, g.rows_per_split, part);
-    gram_reduce_kernel<<<(unsigned)std::min<int64_t>((D1 * D1 + 255) / 256, 1024), 256, 0, s>>>(part, g.splits,
-                                                                                               (int)pb.d, g.T, Qd,
-                                                                                               Qhi, Qlo);
-    colabs_kernel<float><<<(unsigned)((pb.d * 32 + 255) / 256), 256, 0, s>>>(pb.SA, pb.ldsa, pb.r, (int)pb.d, colabs);
-    lh_job &jb = jobs[(size_t)i];
-    jb.Qd = Qd;
-    jb.Qhi = Qhi;
-    jb.Qlo = Qlo;
-    jb.ldq = (int)pb.d + 1;
+    gram_job &q = gj[i];
+    q.S = pb.SA;
+    q.s = pb.Sb;
+    q.lds = pb.ldsa;
+    q.m = pb.r;
+    q.rows_per_split = g.rows_per_split;
+    q.d = (int)pb.d;
+    q.T = g.T;
+    q.ntiles = g.ntiles;
+    q.splits = g.splits;
+    q.part = wc.take<double>((size_t)g.splits * g.ntiles * kGT * kGT);
+    q.part_abs = wc.take<double>((size_t)g.splits * g.T * kGT);
+    q.Qd = wc.take<double>(D1 * D1);
+    q.Qhi = wc.take<float>(D1 * D1);
+    q.Qlo = wc.take<float>(D1 * D1);
+    q.colabs = wc.take<double>((size_t)pb.d);
+    q.counters = counters;
+    counters += g.ntiles;
+    first[i] = blocks;
+    blocks += (int64_t)g.ntiles * g.splits;
+    lh_job &jb = jobs[i];
+    jb.Qd = q.Qd;
+    jb.Qhi = q.Qhi;
+    jb.Qlo = q.Qlo;
+    jb.ldq = (int)D1;
     jb.qcol = (int)pb.d;
-    jb.colabs = colabs;
+    jb.colabs = q.colabs;
     jb.r = pb.r;
     jb.d = (int)pb.d;
     jb.x = pb.x;
     jb.info = pb.info;
     jb.q_smem = lh_q_fits(ctx, (int)pb.d) ? 1 : 0;
   }
-  if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
-  // job table: staged through the context's pinned buffer (the previous
-  // batched call's copy must have finished before it is overwritten)
-  const size_t jbytes = (size_t)count * sizeof(lh_job);
-  st = ensure_pinned(ctx, jbytes);
-  if (st) return st;
-  memcpy(ctx->pinned, jobs.data(), jbytes);
-  RNNLS_CUDA_TRY(cudaMemcpyAsync(d_jobs, ctx->pinned, jbytes, cudaMemcpyHostToDevice, s));
+  first[count] = blocks;
+  cudaStream_t s = ctx->stream;
+  // tables staged through the context's pinned buffer (ensure_pinned waited
+  // for the previous call's copy out of it)
+  RNNLS_CUDA_TRY(cudaMemcpyAsync(d_tables, h_tables, tbytes, cudaMemcpyHostToDevice, s));
   RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
-  (void)dmax;
+  const gram_job *d_gj = (const gram_job *)d_tables;
+  const int64_t *d_first = (const int64_t *)(d_tables + align_up((size_t)count * sizeof(gram_job), 256));
+  const lh_job *d_jobs = (const lh_job *)(d_tables + align_up((size_t)count * sizeof(gram_job), 256) +
+                                          align_up((size_t)(count + 1) * sizeof(int64_t), 256));
+  {
+    prof_scope ps(ctx, K_GRAM);
+    gram_batched_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_gj, d_first, (int)count);
+  }
+  if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
   return lh_launch(ctx, d_jobs, count, smem);
 }
 
