@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-pipeline", action="store_true",
                     help="run each step's sketch and solve back to back on one stream")
+    ap.add_argument("--copy-streams", type=int, default=1,
+                    help="end-to-end leg: streams the host-to-device copy of A is split over")
     ap.add_argument("--solve-streams", type=int, default=2,
                     help="solve streams when pipelined (each solve runs in one block)")
     return ap.parse_args()
@@ -300,16 +302,23 @@ def main():
     SA, Sb, idx, x, info = SAs[0], Sbs[0], idxs[0], xs[0], infos[0]
     x_host = torch.empty(p.d, dtype=torch.float64).pin_memory()
 
-    def step(i: int):
+    def step(i: int, A_=None, b_=None, after_sketch=None, x_out=None):
+        A_ = A if A_ is None else A_
+        b_ = b if b_ is None else b_
         k = i % nbuf
         if pipeline and used[k]:
             s_sketch.wait_event(solved[k])  # the buffer's previous solve has read it
-        ctx.sketch(A, b, r, seed=i, instance=rank, SA=SAs[k], Sb=Sbs[k], idx=idxs[k], want_count=False)
+        ctx.sketch(A_, b_, r, seed=i, instance=rank, SA=SAs[k], Sb=Sbs[k], idx=idxs[k], want_count=False)
+        if after_sketch is not None:
+            after_sketch.record(s_sketch)
         cv = ctx_vs[i % nsolve]
         if pipeline:
             sketched[k].record(s_sketch)
             s_solves[i % nsolve].wait_event(sketched[k])
         cv.solve(SAs[k], Sbs[k], r=r, x=xs[k], info=infos[k])
+        if x_out is not None:
+            with torch.cuda.stream(s_solves[i % nsolve]):
+                x_out.copy_(xs[k], non_blocking=True)
         if pipeline:
             solved[k].record(s_solves[i % nsolve])
             used[k] = True
@@ -358,27 +367,65 @@ def main():
     ms_per_step = ms / args.steps
     value = ws * args.steps / (ms / 1e3)
 
-    # e2e: pinned host inputs copied in and the solution read back every step
-    # (through the same public calls, one stream, no overlap between steps)
+    # e2e: pinned host inputs copied in and the solution read back every step,
+    # through the same public calls (pipelined: copies overlap the previous step)
     def seq_step(i: int):
         ctx.sketch(A, b, r, seed=i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
         ctx.solve(SA, Sb, r=r, x=x, info=info)
 
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, min(args.steps, 200))
-    for i in range(2):
-        A.copy_(A_host.t(), non_blocking=True)
-        b.copy_(b_host, non_blocking=True)
-        seq_step(i)
-        x_host.copy_(x, non_blocking=True)
-        stream.synchronize()
-    e0 = time.perf_counter()
-    for i in range(e2e_steps):
-        A.copy_(A_host.t(), non_blocking=True)
-        b.copy_(b_host, non_blocking=True)
-        seq_step(i)
-        x_host.copy_(x, non_blocking=True)
-        stream.synchronize()
-    e_dt = max_over_ranks(time.perf_counter() - e0, dev)
+    if pipeline:
+        # the inputs of step i+1 are copied (own stream, two device buffers)
+        # while step i is sketched and solved; x of every step comes back
+        # the copy of A is split over a few streams (column ranges) so that
+        # several copy engines share it
+        ncs = max(1, args.copy_streams)
+        copy_ss = [torch.cuda.Stream(dev) for _ in range(ncs)]
+        Ad = [A, torch.empty((p.d, p.n), dtype=tdt, device=dev).t()]
+        bd = [b, torch.empty_like(b)]
+        copied = [[torch.cuda.Event() for _ in range(ncs)] for _ in range(2)]
+        freed = [torch.cuda.Event() for _ in range(2)]
+        x_hosts = [torch.empty(p.d, dtype=torch.float64).pin_memory() for _ in range(nbuf)]
+        cuts = [round(c * p.d / ncs) for c in range(ncs + 1)]
+        At_host = A_host.t()
+
+        def e2e_run(nsteps: int):
+            for i in range(nsteps):
+                k = i % 2
+                for c, cs in enumerate(copy_ss):
+                    if i >= 2:
+                        cs.wait_event(freed[k])  # the sketch two steps back has read this buffer
+                    with torch.cuda.stream(cs):
+                        Ad[k][:, cuts[c]:cuts[c + 1]].copy_(At_host[:, cuts[c]:cuts[c + 1]], non_blocking=True)
+                        if c == 0:
+                            bd[k].copy_(b_host, non_blocking=True)
+                    copied[k][c].record(cs)
+                    s_sketch.wait_event(copied[k][c])
+                step(i, Ad[k], bd[k], after_sketch=freed[k], x_out=x_hosts[i % nbuf])
+            drain()
+            torch.cuda.synchronize()
+
+        e2e_run(2)
+        e0 = time.perf_counter()
+        e2e_run(e2e_steps)
+        e_dt = max_over_ranks(time.perf_counter() - e0, dev)
+        A.copy_(A_host.t())
+        b.copy_(b_host)
+    else:
+        for i in range(2):
+            A.copy_(A_host.t(), non_blocking=True)
+            b.copy_(b_host, non_blocking=True)
+            seq_step(i)
+            x_host.copy_(x, non_blocking=True)
+            stream.synchronize()
+        e0 = time.perf_counter()
+        for i in range(e2e_steps):
+            A.copy_(A_host.t(), non_blocking=True)
+            b.copy_(b_host, non_blocking=True)
+            seq_step(i)
+            x_host.copy_(x, non_blocking=True)
+            stream.synchronize()
+        e_dt = max_over_ranks(time.perf_counter() - e0, dev)
     e2e = {"value": ws * e2e_steps / e_dt, "unit": "solves/s",
            "h2d_bytes_per_step": int(A_host.numel() * elt + b_host.numel() * elt),
            "d2h_bytes_per_step": int(x_host.numel() * 8)}
