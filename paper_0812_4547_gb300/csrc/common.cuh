@@ -232,15 +232,17 @@ const char *kernel_name(int kid);
 struct prof_scope {
   rnnls_ctx *c;
   int slot;
-  prof_scope(rnnls_ctx *ctx, int kid) : c(ctx), slot(-1) {
+  cudaStream_t st;
+  prof_scope(rnnls_ctx *ctx, int kid) : prof_scope(ctx, kid, ctx ? ctx->stream : nullptr) {}
+  prof_scope(rnnls_ctx *ctx, int kid, cudaStream_t s) : c(ctx), slot(-1), st(s) {
     if (c && c->prof_on && c->prof_n < c->prof_cap) {
       slot = c->prof_n++;
       c->prof_kid[slot] = kid;
-      cudaEventRecord(c->prof_ev[2 * slot], c->stream);
+      cudaEventRecord(c->prof_ev[2 * slot], st);
     }
   }
   ~prof_scope() {
-    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], c->stream);
+    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], st);
   }
 };
 

@@ -34,15 +34,10 @@ struct plan_t {
   int64_t rows_per_group;
 };
 size_t plan_ws_bytes(int slots, int kgroups);
-// When `gen` is set the plan kernel also draws the iid rows into idx; with
-// a sign table it also writes the first sign_words sign words of D.
-struct iid_gen {
-  uint64_t seed, inst;
-  int L;
-};
-int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
-                      const iid_gen *gen, uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed,
-                      uint64_t inst);
+// The plan of the rows in idx (drawn before); with a sign table the same
+// launch also writes the first sign_words sign words of D.
+int launch_build_plan(cudaStream_t s, const int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
+                      uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed, uint64_t inst);
 
 // ---- sketch (sketch.cu) ------------------------------------------------------
 // Columns of X = [A | B]: d columns of A, then nb columns of B (nb = 1: the

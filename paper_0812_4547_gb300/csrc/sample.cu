@@ -152,32 +152,55 @@ int launch_sample_bernoulli(cudaStream_t s, uint64_t seed, uint64_t inst, int L,
 // k = row index in the sketch (-1: empty).  n <= 2^28 keeps h >> 2 below
 // 2^14.
 // ---------------------------------------------------------------------------
-constexpr int kPlanThreads = 512;  // half an SM's registers: plans run beside other work
+constexpr int kPlanThreads = 1024;
 
-__global__ void __launch_bounds__(kPlanThreads, 2) build_plan_kernel(int32_t *__restrict__ idx, int64_t r,
+__device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// One block per (plan group g, bank q), plus the sign-table blocks.  Every
+// plan block reads the rows of its group (drawn before), counts all 32
+// banks itself and writes only what belongs to bank q: its rows with rank
+// below 8 * slots (lane q), the spilled ones (into other lanes' free
+// positions, in bank order) and lane q's free positions no spilled row
+// takes.  No block reads another block's output.
+__global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(const int32_t *__restrict__ idx, int64_t r,
                                                                   const int64_t *__restrict__ d_count,
                                                                   uint32_t *__restrict__ plan_pk,
                                                                   int32_t *__restrict__ plan_k, int slots,
-                                                                  int64_t rows_per_group, int gen_iid, uint64_t seed,
-                                                                  uint64_t inst, int L, uint64_t *__restrict__ sign_table,
+                                                                  int64_t rows_per_group, int kgroups, uint64_t seed,
+                                                                  uint64_t inst, uint64_t *__restrict__ sign_table,
                                                                   int64_t sign_words, int64_t sign_block0) {
-  extern __shared__ uint16_t rank_of[];  // rows_per_group entries
-  __shared__ uint32_t wcnt[kPlanThreads / 32][33];
   __shared__ uint32_t cnt[32], ov_start[32], free_start[32];
-  const int g = blockIdx.x;
+  __shared__ uint32_t wsum[kPlanThreads / 32];
+  __shared__ uint32_t whist[kPlanThreads / 32][32];  // per-warp bank counts (no contention)
+  __shared__ uint32_t round_total, total_ov;
+  // this bank's spilled rows, kept from the first scan (a second scan only
+  // if more than kSpillKeep spill)
+  constexpr uint32_t kSpillKeep = 768;
+  __shared__ uint32_t spill_row[kSpillKeep];
+  __shared__ int32_t spill_k[kSpillKeep];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (g >= (int)gridDim.x - (int)((sign_words / 4 + kPlanThreads - 1) / kPlanThreads)) {
+  const int nplan = 32 * kgroups;
+  if ((int)blockIdx.x >= nplan) {
     // sign words of D: word W (counted from the table's first chunk) is word
     // W % 4 of Philox block sign_block0 + W / 4 of stream 0
-    const int64_t first = (int64_t)(g - ((int)gridDim.x - (int)((sign_words / 4 + kPlanThreads - 1) / kPlanThreads)));
-    const int64_t blk = first * kPlanThreads + tid;
+    const int64_t blk = (int64_t)(blockIdx.x - nplan) * kPlanThreads + tid;
     if (4 * blk < sign_words) {
       const u64x4 u = philox4x64_10((uint64_t)(sign_block0 + blk), kStreamSigns, seed, inst);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sign_table[4 * blk + q] = u.w[q];
+      for (int e = 0; e < 4; ++e) sign_table[4 * blk + e] = u.w[e];
     }
     return;
   }
+  const int g = blockIdx.x >> 5;
+  const uint32_t q = blockIdx.x & 31;
   int64_t rr = r;
   if (d_count) rr = min(r, *d_count);
   const int64_t k0 = (int64_t)g * rows_per_group;
@@ -185,84 +208,113 @@ __global__ void __launch_bounds__(kPlanThreads, 2) build_plan_kernel(int32_t *__
   uint32_t *pk_out = plan_pk + (size_t)g * slots * kThreads;
   int32_t *k_out = plan_k + (size_t)g * slots * kThreads;
   const uint32_t cap = 8u * (uint32_t)slots;  // rows per bank without spilling
-
-  for (int e = tid; e < slots * kThreads; e += kPlanThreads) {
-    pk_out[e] = (uint32_t)(e & 31) << 2;
-    k_out[e] = -1;
-  }
-  if (gen_iid) {
-    // the iid rows of this group: draw k is word k of stream 2 (k0 is a multiple of 4)
-    for (int64_t j = k0 / 4 + tid; 4 * j < k1; j += kPlanThreads) {
-      const u64x4 u = philox4x64_10((uint64_t)j, kStreamIid, seed, inst);
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const int64_t k = 4 * j + w;
-        if (k < k1) idx[k] = (L == 0) ? 0 : (int32_t)(u.w[w] >> (64 - L));
-      }
-    }
-  }
+  whist[warp][lane] = 0;
   __syncthreads();
-  // 1. rank of each row within its bank, in row order (stable)
-  uint32_t seen = 0;  // thread q < 32: rows of bank q in earlier tiles
-  for (int64_t t0 = k0; t0 < k1; t0 += kPlanThreads) {
-    const int64_t k = t0 + tid;
-    const bool valid = k < k1;
-    const uint32_t bank = valid ? (swz128((uint32_t)idx[k] & (kM - 1)) & 31u) : 32u;
-    const uint32_t same = __match_any_sync(0xffffffffu, bank);
-    const uint32_t below = __popc(same & ((1u << lane) - 1u));
-    wcnt[warp][lane] = 0;
-    __syncwarp();
-    if (valid && below == 0) wcnt[warp][bank] = __popc(same);
-    __syncthreads();
-    if (tid < 32) {
-      uint32_t run = seen;
-      for (int q = 0; q < kPlanThreads / 32; ++q) {
-        const uint32_t c = wcnt[q][tid];
-        wcnt[q][tid] = run;
-        run += c;
+
+  auto place = [&](uint32_t pos, uint32_t ln, uint32_t row, int64_t k) {
+    const uint32_t l = row & (kM - 1), h = row >> kLogM;
+    const size_t e = (size_t)(pos >> 3) * kThreads + (pos & 7u) * 32u + ln;
+    pk_out[e] = (swz128(l) << 2) | ((h >> 2) << 14) | ((h & 1u) << 31) | (((h >> 1) & 1u) << 30);
+    k_out[e] = (int32_t)k;
+  };
+  // rows k = t0 + 4 tid .. + 3 of this round, in draw order (thread, then e)
+  auto scan = [&](bool count_all, bool place_spilled) {
+    uint32_t qbase = 0;
+    for (int64_t t0 = k0; t0 < k1; t0 += 4 * kPlanThreads) {
+      const int64_t kb = t0 + 4 * tid;
+      uint32_t rows[4], bank[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) rows[e] = (kb + e < k1) ? (uint32_t)idx[kb + e] : 0u;
+      uint32_t mine = 0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool valid = kb + e < k1;
+        bank[e] = valid ? (swz128(rows[e] & (kM - 1)) & 31u) : 32u;
+        mine += (bank[e] == q) ? 1u : 0u;
+        if (count_all) {
+          const uint32_t same = __match_any_sync(0xffffffffu, bank[e]);
+          if (valid && (same & ((1u << lane) - 1u)) == 0) whist[warp][bank[e]] += __popc(same);
+        }
       }
-      seen = run;
+      // ranks of bank-q rows: exclusive scan of `mine` over the block
+      const uint32_t incl = warp_inclusive_sum(mine);
+      if (lane == 31) wsum[warp] = incl;
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t v = (lane < kPlanThreads / 32) ? wsum[lane] : 0u;
+        const uint32_t vi = warp_inclusive_sum(v);
+        if (lane < kPlanThreads / 32) wsum[lane] = vi - v;
+        if (lane == 31) round_total = vi;
+      }
+      __syncthreads();
+      uint32_t rank = qbase + wsum[warp] + incl - mine;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (bank[e] != q) continue;
+        if (rank < cap) {
+          if (!place_spilled) place(rank, q, rows[e], kb + e);
+        } else if (!place_spilled) {
+          if (rank - cap < kSpillKeep) {
+            spill_row[rank - cap] = rows[e];
+            spill_k[rank - cap] = (int32_t)(kb + e);
+          }
+        } else {
+          // spilled row: the e-th overall spilled row takes the e-th free position (bank order)
+          const uint32_t ev = ov_start[q] + (rank - cap);
+          for (uint32_t b2 = 0; b2 < 32; ++b2) {
+            const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
+            if (ev >= free_start[b2] && ev < free_start[b2] + f) place(cnt[b2] + (ev - free_start[b2]), b2, rows[e], kb + e);
+          }
+        }
+        ++rank;
+      }
+      qbase += round_total;
+      __syncthreads();  // wsum and round_total are reused
     }
-    __syncthreads();
-    if (valid) rank_of[k - k0] = (uint16_t)(wcnt[warp][bank] + below);
-    __syncthreads();
+  };
+  scan(true, false);
+  if (tid < 32) {
+    uint32_t c = 0;
+    for (int w = 0; w < kPlanThreads / 32; ++w) c += whist[w][tid];
+    cnt[tid] = c;
   }
-  if (tid < 32) cnt[tid] = seen;
   __syncthreads();
   if (tid == 0) {
     uint32_t ov = 0, fr = 0;
-    for (int q = 0; q < 32; ++q) {
-      ov_start[q] = ov;
-      free_start[q] = fr;
-      ov += cnt[q] > cap ? cnt[q] - cap : 0u;
-      fr += cnt[q] < cap ? cap - cnt[q] : 0u;
+    for (int b2 = 0; b2 < 32; ++b2) {
+      ov_start[b2] = ov;
+      free_start[b2] = fr;
+      ov += cnt[b2] > cap ? cnt[b2] - cap : 0u;
+      fr += cnt[b2] < cap ? cap - cnt[b2] : 0u;
     }
+    total_ov = ov;
   }
   __syncthreads();
-  // 2. place: rank t of bank q -> lane q of (warp t % 8, slot t / 8); spilled
-  //    rows fill the free positions of the banks in bank order
-  for (int64_t k = k0 + tid; k < k1; k += kPlanThreads) {
-    const uint32_t i = (uint32_t)idx[k];
-    const uint32_t l = i & (kM - 1), h = i >> kLogM;
-    const uint32_t wd = swz128(l);
-    const uint32_t bank = wd & 31u;
-    const uint32_t rank = rank_of[k - k0];
-    uint32_t q = bank, pos = rank;
-    if (rank >= cap) {
-      const uint32_t e = ov_start[bank] + (rank - cap);
-      for (uint32_t b2 = 0; b2 < 32; ++b2) {
-        const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
-        if (e >= free_start[b2] && e < free_start[b2] + f) {
-          q = b2;
-          pos = cnt[b2] + (e - free_start[b2]);
+  // lane q's free positions that no spilled row takes: empty entries (read a
+  // word of bank q, write nothing)
+  if (cnt[q] < cap) {
+    const uint32_t nfree = cap - cnt[q];
+    for (uint32_t f = tid; f < nfree; f += kPlanThreads) {
+      if (free_start[q] + f < total_ov) continue;
+      const uint32_t pos = cnt[q] + f;
+      const size_t e = (size_t)(pos >> 3) * kThreads + (pos & 7u) * 32u + q;
+      pk_out[e] = q << 2;
+      k_out[e] = -1;
+    }
+  }
+  if (cnt[q] > cap) {
+    const uint32_t nsp = cnt[q] - cap;
+    if (nsp <= kSpillKeep) {
+      for (uint32_t t = tid; t < nsp; t += kPlanThreads) {
+        const uint32_t ev = ov_start[q] + t;
+        for (uint32_t b2 = 0; b2 < 32; ++b2) {
+          const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
+          if (ev >= free_start[b2] && ev < free_start[b2] + f) place(cnt[b2] + (ev - free_start[b2]), b2, spill_row[t], spill_k[t]);
         }
       }
+    } else {
+      scan(false, true);
     }
-    if (pos >= cap) continue;  // unreachable: the free positions outnumber the spilled rows
-    const uint32_t thread = (pos & 7u) * 32u + q;
-    const uint32_t slot = pos >> 3;
-    pk_out[(size_t)slot * kThreads + thread] = (wd << 2) | ((h >> 2) << 14) | ((h & 1u) << 31) | (((h >> 1) & 1u) << 30);
-    k_out[(size_t)slot * kThreads + thread] = (int32_t)k;
   }
 }
 
@@ -271,24 +323,15 @@ size_t plan_ws_bytes(int slots, int kgroups) {
   return align_up(e * sizeof(uint32_t), 256) + align_up(e * sizeof(int32_t), 256);
 }
 
-int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
-                      const iid_gen *gen, uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed,
-                      uint64_t inst) {
+int launch_build_plan(cudaStream_t s, const int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
+                      uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed, uint64_t inst) {
   if (plan.rows_per_group > kPlanMaxRows || plan.rows_per_group > (int64_t)plan.slots * kThreads)
     return RNNLS_EUNSUPPORTED;
   if (!sign_table) sign_words = 0;
   const int64_t sign_blocks = (sign_words / 4 + kPlanThreads - 1) / kPlanThreads;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(build_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kPlanMaxRows * sizeof(uint16_t))) != cudaSuccess)
-      return RNNLS_ECUDA;
-    attr_set = true;
-  }
-  const size_t smem = (size_t)plan.rows_per_group * sizeof(uint16_t);
-  build_plan_kernel<<<(unsigned)(plan.kgroups + sign_blocks), kPlanThreads, smem, s>>>(
-      idx, r, d_count, plan.pk, plan.k, plan.slots, plan.rows_per_group, gen ? 1 : 0, seed, inst, gen ? gen->L : 0,
-      sign_table, sign_words, sign_block0);
+  build_plan_kernel<<<(unsigned)(32 * plan.kgroups + sign_blocks), kPlanThreads, 0, s>>>(
+      idx, r, d_count, plan.pk, plan.k, plan.slots, plan.rows_per_group, plan.kgroups, seed, inst, sign_table,
+      sign_words, sign_block0);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 

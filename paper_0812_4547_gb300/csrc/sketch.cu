@@ -801,22 +801,23 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
   }
   const int sms = (ctx->sketch_sms > 0) ? std::min(ctx->sketch_sms, num_sms) : num_sms;
   srht_geom g = plan_geometry(a, sms, false);
-  int st = ensure_workspace(ctx, g.plan_bytes + g.sign_bytes + g.part_bytes + 768);
+  int st = ensure_workspace(ctx, g.part_bytes + g.plan_bytes + g.sign_bytes + 1024);
   if (st) return st;
   ws_carver wc(ctx->ws);
+  float *part = g.maxseg ? wc.take<float>((size_t)g.maxseg * g.P.U * g.plan.rows_per_group) : nullptr;
   carve_plan(wc, g.plan);
   uint64_t *signs = wc.take<uint64_t>((size_t)g.sign_words);
-  float *part = g.maxseg ? wc.take<float>((size_t)g.maxseg * g.P.U * g.plan.rows_per_group) : nullptr;
   unsigned int *counters = nullptr;
   if (g.maxseg) {
     st = ensure_counters(ctx, (size_t)g.P.U, &counters);
     if (st) return st;
   }
   {
+    // the iid rows are drawn once by many blocks, then every plan block reads them
     prof_scope ps(ctx, K_PLAN);
-    iid_gen gen{a.seed, a.inst, a.L};
-    st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, a.gen_iid ? &gen : nullptr, signs, g.sign_words,
-                           16 * a.chunk0, a.seed, a.inst);
+    if (a.gen_iid) st = launch_sample_iid(s, a.seed, a.inst, a.L, a.r, a.idx);
+    if (!st)
+      st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, signs, g.sign_words, 16 * a.chunk0, a.seed, a.inst);
   }
   if (st) return st;
   prof_scope ps_main(ctx, K_SKETCH);
@@ -847,9 +848,8 @@ int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, vo
   float *part = g.maxseg ? wc.take<float>((size_t)g.maxseg * g.P.U * g.plan.rows_per_group) : nullptr;
   if (g.maxseg && cudaMemsetAsync(counters, 0, (size_t)g.P.U * sizeof(unsigned int), s) != cudaSuccess)
     return RNNLS_ECUDA;
-  iid_gen gen{a.seed, a.inst, a.L};
-  int st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, a.gen_iid ? &gen : nullptr, signs, g.sign_words,
-                             16 * a.chunk0, a.seed, a.inst);
+  int st = a.gen_iid ? launch_sample_iid(s, a.seed, a.inst, a.L, a.r, a.idx) : RNNLS_OK;
+  if (!st) st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, signs, g.sign_words, 16 * a.chunk0, a.seed, a.inst);
   if (st) return st;
   return launch_srht(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
 }
