@@ -610,14 +610,17 @@ def device_batch(shapes, seed: int, dev):
         g = torch.Generator(device=dev)
         g.manual_seed(seed * 100003 + i)
         colw = torch.arange(1, d + 1, device=dev, dtype=torch.float32).pow(-1.1)[:, None]
-        At = torch.where(torch.rand((d, n_raw), generator=g, device=dev) < 0.02,
-                         torch.randn((d, n_raw), generator=g, device=dev).exp_() * colw,
-                         torch.zeros((), device=dev))
+        # leading dimension rounded up to 4 floats (16-byte aligned columns, as a caller would allocate)
+        ld = (n_raw + 3) // 4 * 4
+        At = torch.zeros((d, ld), device=dev)
+        At[:, :n_raw] = torch.where(torch.rand((d, n_raw), generator=g, device=dev) < 0.02,
+                                    torch.randn((d, n_raw), generator=g, device=dev).exp_() * colw,
+                                    torch.zeros((), device=dev))
         x = workloads.planted_x(d, int(round(0.5 * d)), hrng)
-        y = At.t().double() @ torch.from_numpy(x).to(dev)
+        y = At[:, :n_raw].t().double() @ torch.from_numpy(x).to(dev)
         sigma = 0.05 * float(torch.linalg.vector_norm(y)) / math.sqrt(n_raw)
         b = (y + sigma * torch.randn(n_raw, generator=g, device=dev, dtype=torch.float64)).float()
-        out.append((At.t(), b, r))
+        out.append((At.t()[:n_raw], b, r))
     return out
 
 
@@ -647,6 +650,9 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
     fork = torch.cuda.Event()
     joins = [torch.cuda.Event() for _ in range(S)]
 
+    # the batched calls stage their job tables through their context's pinned
+    # buffer, which a captured graph reads again at every replay: one context each
+    ctx_sketch = P.Context(local, main_s)
     ctx_solve = P.Context(local, main_s)
     problems = [(bufs[i][0], bufs[i][1], bufs[i][3], bufs[i][4]) for i in range(count)]
 
@@ -655,10 +661,9 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
         for st in streams:
             st.wait_event(fork)
         if spread:
-            # phase 1: sketch of instance i on stream i % S; phase 2: every solve in one batched call
-            for i, (A, b, r) in enumerate(insts):
-                SA, Sb, idx, x, info = bufs[i]
-                ctxs[i % S].sketch(A, b, r, seed=seed0 + i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
+            # every sketch in one batched call, then every solve in one batched call
+            ctx_sketch.sketch_batched([(A, b, r, seed0 + i, rank, bufs[i][0], bufs[i][1], bufs[i][2])
+                                       for i, (A, b, r) in enumerate(insts)])
         else:
             # the plain per-instance form: sketch and solve each instance in turn on one stream
             for i, (A, b, r) in enumerate(insts):
@@ -676,12 +681,12 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
             enqueue(0)
         torch.cuda.synchronize()
         # per-kernel times of one step (profiled, not in the graph)
-        for c in ctxs + [ctx_solve]:
+        for c in ctxs + [ctx_sketch, ctx_solve]:
             B.rnnls_profile_begin(c.handle, 8 * count + 64)
         enqueue(0)
         torch.cuda.synchronize()
         prof = {}
-        for c in ctxs + [ctx_solve]:
+        for c in ctxs + [ctx_sketch, ctx_solve]:
             for k, v in B.rnnls_profile_end(c.handle).items():
                 a = prof.get(k, (0, 0.0))
                 prof[k] = (a[0] + v[0], a[1] + v[1])
@@ -728,8 +733,8 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
     wl = {"workload": f"c5: {count} uneven instances, n 2^U[14,20], d U{{16..200}}, r pow2 of 8(d+1)ln n",
           "instances": count, "total_input_gb": total_bytes / 1e9, "sampling": "iid",
           "l2": "inputs larger than L2 (no flush)", "parallelism": "independent instances per GPU",
-          "pipeline": f"one CUDA graph per step: the sketch of instance i on stream i % {S} (one library context "
-                      "per stream), then one rnnls_solve_batched over all instances; every replay redoes every "
+          "pipeline": "one CUDA graph per step: one rnnls_sketch_batched over all instances (rows, plans and "
+                      "sketches in one launch each), then one rnnls_solve_batched; every replay redoes every "
                       "kernel with the same seeds"}
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -740,7 +745,7 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
                      "frac": achieved / peak if achieved else None, "traffic": None, "kernel": kname,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                      "algorithmic_bytes_per_step": sketch_bytes, "kernel_ms_per_step": kms,
-                     "note": "sum over the step's sketch launches, timed by CUDA events in a profiled (non-graph) step"},
+                     "note": "the step's batched sketch launch, timed by CUDA events in a profiled (non-graph) step"},
         "plain_per_instance": {"value": ws * count / (plain_ms / 1e3), "unit": "solves/s",
                                "ms_per_step": plain_ms, "form": "one stream, no graph"},
         "kernel_ms_per_step": {k: v[1] for k, v in prof.items()},
@@ -749,7 +754,7 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
         "solve_status_nonzero": int(sum(1 for x in stat if x != 0)),
         "cpu_baseline": None,
     }
-    for c in ctxs + [ctx_solve]:
+    for c in ctxs + [ctx_sketch, ctx_solve]:
         c.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -160,6 +160,34 @@ int rnnls_sketch_shard(rnnls_ctx *ctx, const float *A, int64_t lda, const float 
                        int64_t rows, int64_t d, int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa,
                        float *Sb, int32_t *idx);
 
+/* One instance of a batched sketch (rnnls_sketch_batched): the arguments
+ * of rnnls_sketch in iid mode with cap = r (all device pointers; idx must not
+ * be null). */
+typedef struct rnnls_sketch_job {
+  const float *A;
+  int64_t lda;
+  const float *b;
+  int64_t n_raw;
+  int64_t d;
+  int64_t r;
+  uint64_t seed;
+  uint64_t instance;
+  float *SA;
+  int64_t ldsa;
+  float *Sb;
+  int32_t *idx;
+} rnnls_sketch_job;
+
+/* The sketches of `count` independent instances of Alg. 1 (uneven sizes),
+ * each exactly as rnnls_sketch in iid mode would give it (up to the FP32
+ * summation order), computed together: one launch draws every instance's
+ * rows, one makes every plan, and one persistent kernel walks all the
+ * instances' chunk groups.  `jobs` is a HOST array; each job's pointers are
+ * device pointers with the layouts of rnnls_sketch (ldsa >= r, lda >= n_raw).
+ * Errors: EINVAL (a null pointer or a bad size in any job; nothing is
+ * enqueued then), EUNSUPPORTED (n_raw > 2^28), ENOMEM, ECUDA. */
+int rnnls_sketch_batched(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count);
+
 /* The same sketch in FP64 throughout (for FP64 inputs). */
 int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double *b, int64_t n_raw, int64_t d,
                      int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, double *SA, int64_t ldsa,

@@ -131,6 +131,15 @@ class Context:
                               instance, SA.data_ptr(), _ld(SA), SB.data_ptr(), _ld(SB), idx.data_ptr())
         return SA, SB, idx
 
+    def sketch_batched(self, items):
+        """Sketch many FP32 instances together; items: (A, b, r, seed, instance, SA, Sb, idx), outputs preallocated."""
+        jobs = []
+        for A, b, r, seed, instance, SA, Sb, idx in items:
+            A = colmajor(A)
+            jobs.append(B.rnnls_sketch_job(A.data_ptr(), _ld(A), b.data_ptr(), A.shape[0], A.shape[1], r, seed, instance,
+                                           SA.data_ptr(), _ld(SA), Sb.data_ptr(), idx.data_ptr()))
+        B.rnnls_sketch_batched(self.handle, jobs)
+
     def sketch_shard(self, A_rows, b_rows, n_raw: int, row0: int, r: int, seed: int, instance: int = 0, SA=None,
                      Sb=None, idx=None):
         """This row block's additive part of the full sketch (FP32, iid); A_rows holds rows row0.. only."""

@@ -31,7 +31,7 @@ EXPORTS = (
     "rnnls_create", "rnnls_destroy", "rnnls_set_stream", "rnnls_sketch", "rnnls_sketch_f64", "rnnls_solve",
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
-    "rnnls_solve_multi",
+    "rnnls_solve_multi", "rnnls_sketch_batched",
 )
 
 
@@ -52,6 +52,23 @@ class rnnls_kernel_time(ctypes.Structure):
         ("name", ctypes.c_char * 32),
         ("launches", ctypes.c_int64),
         ("total_ms", ctypes.c_double),
+    ]
+
+
+class rnnls_sketch_job(ctypes.Structure):
+    _fields_ = [
+        ("A", ctypes.c_void_p),
+        ("lda", ctypes.c_int64),
+        ("b", ctypes.c_void_p),
+        ("n_raw", ctypes.c_int64),
+        ("d", ctypes.c_int64),
+        ("r", ctypes.c_int64),
+        ("seed", ctypes.c_uint64),
+        ("instance", ctypes.c_uint64),
+        ("SA", ctypes.c_void_p),
+        ("ldsa", ctypes.c_int64),
+        ("Sb", ctypes.c_void_p),
+        ("idx", ctypes.c_void_p),
     ]
 
 
@@ -98,6 +115,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_solve_f64.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_batched.argtypes = [P, ctypes.POINTER(rnnls_problem), I64, U32]
         L.rnnls_solve_multi.argtypes = [P, P, I64, P, I64, I64, I64, I64, P, I64, P]
+        L.rnnls_sketch_batched.argtypes = [P, ctypes.POINTER(rnnls_sketch_job), I64]
         L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_profile_begin.argtypes = [P, I32]
         L.rnnls_profile_end.argtypes = [P, ctypes.POINTER(rnnls_kernel_time), I32, ctypes.POINTER(I32)]
@@ -184,6 +202,11 @@ def rnnls_solve(ctx, SA, ldsa, Sb, r, d, x, info) -> None:
 def rnnls_solve_f64(ctx, SA, ldsa, Sb, r, d, x, info) -> None:
     check(lib().rnnls_solve_f64(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
                                 ctypes.c_void_p(x), ctypes.c_void_p(info)), "rnnls_solve_f64")
+
+
+def rnnls_sketch_batched(ctx, jobs) -> None:
+    arr = (rnnls_sketch_job * len(jobs))(*jobs)
+    check(lib().rnnls_sketch_batched(ctypes.c_void_p(ctx), arr, len(jobs)), "rnnls_sketch_batched")
 
 
 def rnnls_solve_multi(ctx, SA, ldsa, SB, ldsb, r, d, nrhs, X, ldx, infos) -> None:

@@ -409,6 +409,19 @@ int rnnls_sketch_shard(rnnls_ctx *ctx, const float *A, int64_t lda, const float 
   return sketch_f32(ctx, a, ctx->num_sms);
 }
 
+int rnnls_sketch_batched(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count) {
+  if (!ctx || (!jobs && count > 0) || count < 0) return RNNLS_EINVAL;
+  for (int64_t i = 0; i < count; ++i) {
+    const rnnls_sketch_job &j = jobs[i];
+    if (!j.A || !j.b || !j.SA || !j.Sb || !j.idx) return RNNLS_EINVAL;
+    if (j.n_raw < 1 || j.d < 1 || j.r < 1 || j.lda < j.n_raw || j.ldsa < j.r) return RNNLS_EINVAL;
+    if (j.n_raw > kMaxRows || j.d > (1 << 20) || j.r > ((int64_t)1 << 30)) return RNNLS_EUNSUPPORTED;
+  }
+  if (count == 0) return RNNLS_OK;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  return sketch_batched_f32(ctx, jobs, count);
+}
+
 int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double *b, int64_t n_raw, int64_t d,
                      int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, double *SA, int64_t ldsa, double *Sb,
                      int32_t *idx, int64_t cap, int64_t *r_out) {

@@ -39,6 +39,24 @@ size_t plan_ws_bytes(int slots, int kgroups);
 int launch_build_plan(cudaStream_t s, const int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
                       uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed, uint64_t inst);
 
+// Many instances' rows and plans in one launch each (iid rows; a sign table
+// per instance, its words counted from the instance's first chunk).
+struct plan_job {
+  int32_t *idx;
+  int64_t r;
+  uint32_t *pk;
+  int32_t *k;
+  int slots, kgroups, L;
+  int64_t rows_per_group;
+  uint64_t seed, inst;
+  uint64_t *signs;
+  int64_t sign_words;
+};
+int64_t sample_blocks(int64_t r);
+int64_t plan_blocks(const plan_job &j);
+int launch_plan_batched(cudaStream_t s, const plan_job *d_jobs, const int64_t *d_first_sample,
+                        const int64_t *d_first_plan, int count, int64_t sample_total, int64_t plan_total);
+
 // ---- sketch (sketch.cu) ------------------------------------------------------
 // Columns of X = [A | B]: d columns of A, then nb columns of B (nb = 1: the
 // target b).  A row shard (rows chunk0 * 2^12 ... of the full problem, A and
@@ -65,6 +83,8 @@ struct sketch_args_f32 {
   int gen_iid;  // 1: the sketch draws the iid rows itself (idx is output only)
 };
 int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms);
+// many instances (iid rows, FP32): rows, plans and sketches of all in one launch each
+int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count);
 // sketch_f32 with caller-provided scratch (no allocation; see noalloc.cu)
 int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, void *scratch, size_t bytes);
 

@@ -170,13 +170,12 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v) {
 // below 8 * slots (lane q), the spilled ones (into other lanes' free
 // positions, in bank order) and lane q's free positions no spilled row
 // takes.  No block reads another block's output.
-__global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(const int32_t *__restrict__ idx, int64_t r,
-                                                                  const int64_t *__restrict__ d_count,
-                                                                  uint32_t *__restrict__ plan_pk,
-                                                                  int32_t *__restrict__ plan_k, int slots,
-                                                                  int64_t rows_per_group, int kgroups, uint64_t seed,
-                                                                  uint64_t inst, uint64_t *__restrict__ sign_table,
-                                                                  int64_t sign_words, int64_t sign_block0) {
+__device__ __forceinline__ void plan_block(int blk, const int32_t *__restrict__ idx, int64_t r,
+                                           const int64_t *__restrict__ d_count, uint32_t *__restrict__ plan_pk,
+                                           int32_t *__restrict__ plan_k, int slots, int64_t rows_per_group,
+                                           int kgroups, uint64_t seed, uint64_t inst,
+                                           uint64_t *__restrict__ sign_table, int64_t sign_words,
+                                           int64_t sign_block0) {
   __shared__ uint32_t cnt[32], ov_start[32], free_start[32];
   __shared__ uint32_t wsum[kPlanThreads / 32];
   __shared__ uint32_t whist[kPlanThreads / 32][32];  // per-warp bank counts (no contention)
@@ -188,19 +187,19 @@ __global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(const int32_t 
   __shared__ int32_t spill_k[kSpillKeep];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nplan = 32 * kgroups;
-  if ((int)blockIdx.x >= nplan) {
+  if (blk >= nplan) {
     // sign words of D: word W (counted from the table's first chunk) is word
     // W % 4 of Philox block sign_block0 + W / 4 of stream 0
-    const int64_t blk = (int64_t)(blockIdx.x - nplan) * kPlanThreads + tid;
-    if (4 * blk < sign_words) {
-      const u64x4 u = philox4x64_10((uint64_t)(sign_block0 + blk), kStreamSigns, seed, inst);
+    const int64_t pb = (int64_t)(blk - nplan) * kPlanThreads + tid;
+    if (4 * pb < sign_words) {
+      const u64x4 u = philox4x64_10((uint64_t)(sign_block0 + pb), kStreamSigns, seed, inst);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) sign_table[4 * blk + e] = u.w[e];
+      for (int e = 0; e < 4; ++e) sign_table[4 * pb + e] = u.w[e];
     }
     return;
   }
-  const int g = blockIdx.x >> 5;
-  const uint32_t q = blockIdx.x & 31;
+  const int g = blk >> 5;
+  const uint32_t q = blk & 31;
   int64_t rr = r;
   if (d_count) rr = min(r, *d_count);
   const int64_t k0 = (int64_t)g * rows_per_group;
@@ -316,6 +315,66 @@ __global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(const int32_t 
       scan(false, true);
     }
   }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(const int32_t *__restrict__ idx, int64_t r,
+                                                                  const int64_t *__restrict__ d_count,
+                                                                  uint32_t *__restrict__ plan_pk,
+                                                                  int32_t *__restrict__ plan_k, int slots,
+                                                                  int64_t rows_per_group, int kgroups, uint64_t seed,
+                                                                  uint64_t inst, uint64_t *__restrict__ sign_table,
+                                                                  int64_t sign_words, int64_t sign_block0) {
+  plan_block((int)blockIdx.x, idx, r, d_count, plan_pk, plan_k, slots, rows_per_group, kgroups, seed, inst,
+             sign_table, sign_words, sign_block0);
+}
+
+// ---- many instances in one launch -----------------------------------------------
+// Block b belongs to the instance p with first[p] <= b < first[p + 1].
+__device__ __forceinline__ int batch_owner(const int64_t *__restrict__ first, int count, int64_t b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void sample_iid_batched_kernel(const plan_job *__restrict__ jobs, const int64_t *__restrict__ first,
+                                          int count) {
+  const int p = batch_owner(first, count, blockIdx.x);
+  const plan_job jb = jobs[p];
+  const int64_t j = (int64_t)(blockIdx.x - first[p]) * blockDim.x + threadIdx.x;
+  if (4 * j >= jb.r) return;
+  const u64x4 u = philox4x64_10((uint64_t)j, kStreamIid, jb.seed, jb.inst);
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const int64_t k = 4 * j + w;
+    if (k < jb.r) jb.idx[k] = (jb.L == 0) ? 0 : (int32_t)(u.w[w] >> (64 - jb.L));
+  }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) build_plan_batched_kernel(const plan_job *__restrict__ jobs,
+                                                                          const int64_t *__restrict__ first,
+                                                                          int count) {
+  const int p = batch_owner(first, count, blockIdx.x);
+  const plan_job jb = jobs[p];
+  plan_block((int)(blockIdx.x - first[p]), jb.idx, jb.r, nullptr, jb.pk, jb.k, jb.slots, jb.rows_per_group,
+             jb.kgroups, jb.seed, jb.inst, jb.signs, jb.sign_words, 0);
+}
+
+int64_t sample_blocks(int64_t r) { return ((r + 3) / 4 + 255) / 256; }
+int64_t plan_blocks(const plan_job &j) {
+  return 32 * (int64_t)j.kgroups + (j.sign_words / 4 + kPlanThreads - 1) / kPlanThreads;
+}
+
+int launch_plan_batched(cudaStream_t s, const plan_job *d_jobs, const int64_t *d_first_sample,
+                        const int64_t *d_first_plan, int count, int64_t sample_total, int64_t plan_total) {
+  sample_iid_batched_kernel<<<(unsigned)sample_total, 256, 0, s>>>(d_jobs, d_first_sample, count);
+  build_plan_batched_kernel<<<(unsigned)plan_total, kPlanThreads, 0, s>>>(d_jobs, d_first_plan, count);
+  return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 
 size_t plan_ws_bytes(int slots, int kgroups) {

@@ -29,6 +29,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "kernels.h"
 
@@ -349,17 +350,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (uint32_t it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, phase);
       if (!ok) *(volatile int *)&stalled = 1;
     }
-    // lines of this thread's two rows that the tensor copy does not cover
-    // (all of them without tensor copies, else the partial last line)
     {
       const float *x = (col < d) ? A + (int64_t)col * lda : Bm + (int64_t)(col - d) * ldb;
+      if (!vec) {
+        // no tensor copies: the worker loads its chunk with coalesced plain loads
+        const int64_t row0 = (4 * j + w) * (int64_t)kM;
+#pragma unroll 16
+        for (int i = wt; i < kM; i += 64) {
+          const int64_t row = row0 + i;
+          zw[swz128((uint32_t)i)] = (row < n_raw) ? x[row] : 0.0f;
+        }
+        bar_worker(w);
+      } else {
+        // the partial last line of a column (the copy filled it with zeros)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t line = (4 * j + w) * (int64_t)(kM / 32) + 64 * h + wt;
-        if (!vec || line == nrow32) {
-          for (int e = 0; e < 32; ++e) {
-            const int64_t row = 32 * line + e;
-            zw[swz128((uint32_t)((h << 11) | (wt << 5) | e))] = (row < n_raw) ? x[row] : 0.0f;
+        for (int h = 0; h < 2; ++h) {
+          const int64_t line = (4 * j + w) * (int64_t)(kM / 32) + 64 * h + wt;
+          if (line == nrow32) {
+            for (int e = 0; e < 32; ++e) {
+              const int64_t row = 32 * line + e;
+              zw[swz128((uint32_t)((h << 11) | (wt << 5) | e))] = (row < n_raw) ? x[row] : 0.0f;
+            }
           }
         }
       }
@@ -562,6 +573,374 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(kTmemCols)
                    : "memory");
   }
+}
+
+// ---------------------------------------------------------------------------
+// Many instances in one launch (iid rows, one target each).  The step list
+// is the concatenation of the instances' step lists (instance i owns global
+// steps step0 .. step0 + T - 1, its units ordered as in the one-instance
+// kernel); blocks take balanced stretches of it.  Plan words and row sums
+// live in TMEM (a runtime number of rows per thread, the instance's).  A
+// unit split between blocks is finished through the partial-sum slots of
+// the block where it starts (at most one such unit per block boundary).
+// Tensor maps are read from the job table in global memory, after a
+// tensormap acquire fence per instance.
+// ---------------------------------------------------------------------------
+struct srht_job {  // 64-byte aligned through its tensor maps
+  CUtensorMap tmA, tmB;
+  const float *A, *B;
+  const uint64_t *signs;
+  const uint32_t *pk;
+  const int32_t *pkk;
+  float *SA, *SB;
+  int64_t lda, ldb, ldsa, ldsb, n_raw, J, U, step0, rpg;
+  float scale;
+  int d, slots, vec, pad;
+};
+
+__device__ __forceinline__ void fence_tensormap_acquire(const void *map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
+
+// instance holding global step s
+__device__ __forceinline__ int job_of_step(const srht_job *__restrict__ jobs, int njobs, int64_t s) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].step0 <= s)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// position (instance, unit u, group j, column, plan group) of a global step
+struct batch_cursor {
+  int ji;
+  int64_t u, j, kg;
+  int col;
+  __device__ void init(const srht_job *__restrict__ jobs, int njobs, int64_t s) {
+    ji = job_of_step(jobs, njobs, s);
+    const srht_job &J0 = jobs[ji];
+    const int64_t ls = s - J0.step0;
+    u = ls / J0.J;
+    j = ls - u * J0.J;
+    kg = u / (J0.d + 1);
+    col = (int)(u - kg * (J0.d + 1));
+  }
+  __device__ void next(const srht_job *__restrict__ jobs, int njobs) {
+    const srht_job &J0 = jobs[ji];
+    if (++j < J0.J) return;
+    j = 0;
+    if (++u < J0.U) {
+      if (++col == J0.d + 1) {
+        col = 0;
+        ++kg;
+      }
+      return;
+    }
+    if (ji + 1 < njobs) ++ji;
+    u = 0;
+    kg = 0;
+    col = 0;
+  }
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    sketch_srht_batch_f32(const srht_job *__restrict__ jobs, int njobs, int64_t Ttot, float *__restrict__ part,
+                          int maxseg, int64_t rpg_max, unsigned int *__restrict__ counters) {
+  extern __shared__ __align__(1024) float dyn_smem[];
+  __shared__ __align__(16) uint32_t sgn[kStages][kWorkers][kM / 32];
+  __shared__ __align__(8) uint64_t mbar[kStages];
+  __shared__ unsigned int last_flag;
+  __shared__ int stalled;
+  __shared__ uint32_t tmem_base_s;
+
+  const int tid = threadIdx.x;
+  const int w = tid >> 6;
+  const int wt = tid & 63;
+  const int64_t B = gridDim.x;
+  const int64_t bid = blockIdx.x;
+  const int64_t s0 = (Ttot * bid) / B;
+  const int64_t nsteps = (Ttot * (bid + 1)) / B - s0;
+  if (nsteps <= 0) return;
+  const uint32_t raw_u32 = smem_u32(dyn_smem);
+  const uint32_t stage_u32 = (raw_u32 + 16383u) & ~16383u;
+  float *stage = dyn_smem + (stage_u32 - raw_u32) / 4;
+
+  if (tid == 0) {
+    for (int q = 0; q < kStages; ++q) mbar_init(smem_u32(&mbar[q]), 1);
+    fence_mbar_init();
+    stalled = 0;
+  }
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t t_pk = tmem_base_s + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * 2 * kMaxSlots);
+  const uint32_t t_acc = t_pk + kMaxSlots;
+  const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+
+  // thread 0: copies of a step (four chunks and their sign words)
+  batch_cursor ic;
+  ic.init(jobs, njobs, s0);
+  int iq = 0;
+  int fenced = -1;
+  auto issue = [&]() {
+    const srht_job &J0 = jobs[ic.ji];
+    const uint32_t bar = smem_u32(&mbar[iq]);
+    if (!J0.vec) {
+      mbar_arrive_expect_tx(bar, 0u);
+    } else {
+      if (fenced != ic.ji) {
+        fence_tensormap_acquire(&J0.tmA);
+        fence_tensormap_acquire(&J0.tmB);
+        fenced = ic.ji;
+      }
+      mbar_arrive_expect_tx(bar, (uint32_t)(kWorkers * kM * sizeof(float)) + 2048u);
+      bulk_g2s(smem_u32(&sgn[iq][0][0]), J0.signs + 4 * ic.j * (kM / 64), 2048u, bar);
+      const CUtensorMap *map = (ic.col < J0.d) ? &J0.tmA : &J0.tmB;
+      const int z = (ic.col < J0.d) ? ic.col : 0;
+#pragma unroll
+      for (int c = 0; c < kWorkers; ++c)
+        tma_load_chunk(stage_u32 + (uint32_t)(iq * kStageFloats + c * kM) * 4u, map,
+                       (int)((4 * ic.j + c) * (kM / 32)), z, bar);
+    }
+    ic.next(jobs, njobs);
+    iq = (iq + 1 == kStages) ? 0 : iq + 1;
+  };
+  if (tid == 0) {
+    issue();
+    if (nsteps > 1) issue();
+  }
+
+  batch_cursor cur;
+  cur.init(jobs, njobs, s0);
+  int loaded_ji = -1;
+  int64_t loaded_kg = -1;
+  int q = 0;
+  uint32_t phase = 0;
+  for (int64_t ls = 0; ls < nsteps; ++ls) {
+    const int ji = cur.ji;
+    const int64_t j = cur.j, u = cur.u, kg = cur.kg;
+    const int col = cur.col;
+    const srht_job &J0 = jobs[ji];
+    const int d = J0.d;
+    const int slots = J0.slots;
+    float *__restrict__ zw = stage + q * kStageFloats + w * kM;
+    const uint32_t step_u32 = stage_u32 + (uint32_t)(q * kStageFloats) * 4u;
+    if (ji != loaded_ji || kg != loaded_kg) {  // this instance's plan group into TMEM, sums cleared
+      tmem_wait_st();
+      for (int s8 = 0; s8 < slots; s8 += 8) {
+        uint32_t r8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r8[e] = J0.pk[((size_t)kg * slots + s8 + e) * kThreads + tid];
+        tmem_st8(t_pk + s8, r8);
+        tmem_st8(t_acc + s8, zero8);
+      }
+      loaded_ji = ji;
+      loaded_kg = kg;
+    }
+    __syncthreads();  // step ls-1 is done with its buffer
+    if (tid == 0 && ls + 2 < nsteps) {
+      fence_proxy_async();
+      issue();
+    }
+    {
+      const uint32_t bar = smem_u32(&mbar[q]);
+      const uint32_t limit = *(volatile int *)&stalled ? 64u : kSpinLimit;
+      bool ok = false;
+      for (uint32_t it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, phase);
+      if (!ok) *(volatile int *)&stalled = 1;
+    }
+    const int vec = J0.vec;
+    const int64_t n_raw = J0.n_raw;
+    const int64_t nrow32 = n_raw >> 5;
+    {
+      const float *x = (col < d) ? J0.A + (int64_t)col * J0.lda : J0.B;
+      if (!vec) {
+        const int64_t row0 = (4 * j + w) * (int64_t)kM;
+#pragma unroll 16
+        for (int i = wt; i < kM; i += 64) {
+          const int64_t row = row0 + i;
+          zw[swz128((uint32_t)i)] = (row < n_raw) ? x[row] : 0.0f;
+        }
+        bar_worker(w);
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t line = (4 * j + w) * (int64_t)(kM / 32) + 64 * h + wt;
+          if (line == nrow32) {
+            for (int e = 0; e < 32; ++e) {
+              const int64_t row = 32 * line + e;
+              zw[swz128((uint32_t)((h << 11) | (wt << 5) | e))] = (row < n_raw) ? x[row] : 0.0f;
+            }
+          }
+        }
+      }
+    }
+    uint32_t swv[2];
+    if (vec) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) swv[h] = sgn[q][w][2 * ((h << 5) | (wt >> 1)) + (wt & 1)];
+    } else {
+      const uint32_t *t32 = reinterpret_cast<const uint32_t *>(J0.signs + (4 * j + w) * (kM / 64));
+#pragma unroll
+      for (int h = 0; h < 2; ++h) swv[h] = t32[2 * ((h << 5) | (wt >> 1)) + (wt & 1)];
+    }
+    float v[64];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t sw = swv[h];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const float4 t =
+            *reinterpret_cast<const float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2)));
+        v[32 * h + 4 * g + 0] = xor_sign(t.x, (sw << (31 - (4 * g + 0))) & 0x80000000u);
+        v[32 * h + 4 * g + 1] = xor_sign(t.y, (sw << (31 - (4 * g + 1))) & 0x80000000u);
+        v[32 * h + 4 * g + 2] = xor_sign(t.z, (sw << (31 - (4 * g + 2))) & 0x80000000u);
+        v[32 * h + 4 * g + 3] = xor_sign(t.w, (sw << (31 - (4 * g + 3))) & 0x80000000u);
+      }
+    }
+    fwht64(v);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        *reinterpret_cast<float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2))) =
+            make_float4(v[32 * h + 4 * g], v[32 * h + 4 * g + 1], v[32 * h + 4 * g + 2], v[32 * h + 4 * g + 3]);
+    bar_worker(w);
+    {
+      const uint32_t lane = (uint32_t)(wt & 31), hi = (uint32_t)(wt >> 5) << 11;
+#pragma unroll
+      for (int s = 0; s < 64; ++s) v[s] = zw[hi | ((uint32_t)s << 5) | (lane ^ (((uint32_t)s & 7u) << 2))];
+      fwht64(v);
+#pragma unroll
+      for (int s = 0; s < 64; ++s) zw[hi | ((uint32_t)s << 5) | (lane ^ (((uint32_t)s & 7u) << 2))] = v[s];
+    }
+    __syncthreads();
+
+    const uint32_t jm = (uint32_t)j << 14;
+    {
+      uint32_t pk[8], acc[8], pkn[8], accn[8];
+      tmem_wait_st();
+      tmem_ld8(t_pk, pk);
+      tmem_ld8(t_acc, acc);
+      tmem_wait_ld();
+      for (int s8 = 0; s8 < slots; s8 += 8) {
+        const bool more = s8 + 8 < slots;
+        if (more) {
+          tmem_ld8(t_pk + s8 + 8, pkn);
+          tmem_ld8(t_acc + s8 + 8, accn);
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const uint32_t p = pk[e];
+          float z0, z1, z2, z3;
+          lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+          const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
+          const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
+          const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
+          acc[e] = __float_as_uint(__uint_as_float(acc[e]) + xor_sign(t, (uint32_t)__popc(p & jm) << 31));
+        }
+        tmem_st8(t_acc + s8, acc);
+        if (more) {
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            pk[e] = pkn[e];
+            acc[e] = accn[e];
+          }
+        }
+      }
+    }
+    cur.next(jobs, njobs);
+    if (++q == kStages) {
+      q = 0;
+      phase ^= 1u;
+    }
+
+    // end of this block's part of (instance ji, unit u)
+    if (j == J0.J - 1 || ls == nsteps - 1) {
+      const bool poisoned = *(volatile int *)&stalled != 0;
+      const int64_t g0 = J0.step0 + u * J0.J;  // the unit's first global step
+      const int64_t first = ((g0 + 1) * B - 1) / Ttot;
+      const int64_t last = ((g0 + J0.J) * B - 1) / Ttot;
+      const int64_t nseg = last - first + 1;
+      const int64_t seg = bid - first;
+      float *pslot = part + (size_t)first * maxseg * rpg_max;  // the unit starting in block `first`
+      tmem_wait_st();
+      for (int s8 = 0; s8 < slots; s8 += 8) {
+        uint32_t acc[8];
+        tmem_ld8(t_acc + s8, acc);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int32_t k = J0.pkk[((size_t)kg * slots + s8 + e) * kThreads + tid];
+          if (k < 0) continue;
+          const float a = poisoned ? __int_as_float(0x7fc00000) : __uint_as_float(acc[e]);
+          if (nseg == 1) {
+            if (col < d)
+              J0.SA[(int64_t)col * J0.ldsa + k] = J0.scale * a;
+            else
+              J0.SB[k] = J0.scale * a;
+          } else {
+            pslot[(size_t)seg * rpg_max + (size_t)(s8 + e) * kThreads + tid] = a;
+          }
+        }
+        tmem_st8(t_acc + s8, zero8);
+      }
+      if (nseg > 1) {
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) last_flag = (atomicAdd(&counters[first], 1u) == (unsigned int)(nseg - 1)) ? 1u : 0u;
+        __syncthreads();
+        if (last_flag) {
+          __threadfence();
+          for (int s0b = 0; s0b < slots; s0b += 32) {
+            int32_t kk[32];
+            float sum[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              kk[e] = (s0b + e < slots) ? J0.pkk[((size_t)kg * slots + s0b + e) * kThreads + tid] : -1;
+              sum[e] = 0.0f;
+            }
+            for (int64_t g = 0; g < nseg; ++g) {
+              const float *pg = pslot + (size_t)g * rpg_max + (size_t)s0b * kThreads + tid;
+              float t[32];
+#pragma unroll
+              for (int e = 0; e < 32; ++e) t[e] = (kk[e] >= 0) ? __ldcg(pg + (size_t)e * kThreads) : 0.0f;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) sum[e] += t[e];
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              if (kk[e] < 0) continue;
+              if (col < d)
+                J0.SA[(int64_t)col * J0.ldsa + kk[e]] = J0.scale * sum[e];
+              else
+                J0.SB[kk[e]] = J0.scale * sum[e];
+            }
+          }
+          if (tid == 0) counters[first] = 0u;
+        }
+      }
+    }
+  }
+  tmem_wait_st();
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (tid < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(kTmemCols)
+                 : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -822,6 +1201,143 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
   if (st) return st;
   prof_scope ps_main(ctx, K_SKETCH);
   return launch_srht(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
+}
+
+int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count) {
+  cudaStream_t s = ctx->stream;
+  const int num_sms = ctx->num_sms;
+  // instances too small for the chunked path go one by one
+  std::vector<int64_t> big;
+  for (int64_t i = 0; i < count; ++i) {
+    const rnnls_sketch_job &jb = jobs[i];
+    if (((int64_t)1 << log2_ceil64(jb.n_raw)) > 8192) {
+      big.push_back(i);
+      continue;
+    }
+    sketch_args_f32 a{};
+    a.A = jb.A; a.lda = jb.lda; a.b = jb.b; a.ldb = jb.n_raw; a.nb = 1; a.n_raw = jb.n_raw; a.d = (int)jb.d;
+    a.L = log2_ceil64(jb.n_raw); a.chunk0 = 0; a.r = jb.r; a.d_count = nullptr; a.seed = jb.seed;
+    a.inst = jb.instance; a.scale = (float)(1.0 / sqrt((double)jb.r)); a.SA = jb.SA; a.ldsa = jb.ldsa; a.Sb = jb.Sb;
+    a.ldsb = jb.ldsa; a.idx = jb.idx; a.gen_iid = 0;
+    int st = launch_sample_iid(s, jb.seed, jb.instance, a.L, jb.r, jb.idx);
+    if (!st) st = sketch_f32(ctx, a, num_sms);
+    if (st) return st;
+  }
+  const int nb = (int)big.size();
+  if (nb == 0) return RNNLS_OK;
+  // per-instance geometry; global step offsets
+  std::vector<srht_job> sj((size_t)nb);
+  std::vector<plan_job> pj((size_t)nb);
+  std::vector<int64_t> first_s((size_t)nb + 1), first_p((size_t)nb + 1);
+  int64_t Ttot = 0, rpg_max = 0, samp_tot = 0, plan_tot = 0;
+  size_t plan_bytes = 0;
+  for (int t = 0; t < nb; ++t) {
+    const rnnls_sketch_job &jb = jobs[big[(size_t)t]];
+    srht_job &J = sj[(size_t)t];
+    memset(&J, 0, sizeof(J));
+    const int slots = pick_slots(jb.r);
+    const int64_t rpg = (int64_t)kThreads * slots;
+    const int kgroups = (int)((jb.r + rpg - 1) / rpg);
+    J.A = jb.A; J.B = jb.b; J.lda = jb.lda; J.ldb = jb.n_raw; J.ldsa = jb.ldsa; J.ldsb = jb.ldsa;
+    J.n_raw = jb.n_raw; J.J = (jb.n_raw + 4 * (int64_t)kM - 1) / (4 * (int64_t)kM);
+    J.U = (int64_t)kgroups * (jb.d + 1); J.step0 = Ttot; J.rpg = rpg; J.scale = (float)(1.0 / sqrt((double)jb.r));
+    J.d = (int)jb.d; J.slots = slots; J.SA = jb.SA; J.SB = jb.Sb;
+    J.vec = (((uintptr_t)jb.A % 16 == 0) && (jb.lda % 4 == 0) && ((uintptr_t)jb.b % 16 == 0)) ? 1 : 0;
+    Ttot += J.U * J.J;
+    rpg_max = std::max(rpg_max, rpg);
+    plan_job &P = pj[(size_t)t];
+    P.idx = jb.idx; P.r = jb.r; P.slots = slots; P.kgroups = kgroups; P.L = log2_ceil64(jb.n_raw);
+    P.rows_per_group = rpg; P.seed = jb.seed; P.inst = jb.instance; P.sign_words = 4 * J.J * (kM / 64);
+    plan_bytes += plan_ws_bytes(slots, kgroups) + align_up((size_t)P.sign_words * 8, 256) + 512;
+    first_s[(size_t)t] = samp_tot;
+    first_p[(size_t)t] = plan_tot;
+    samp_tot += sample_blocks(jb.r);
+    plan_tot += plan_blocks(P);
+  }
+  first_s[(size_t)nb] = samp_tot;
+  first_p[(size_t)nb] = plan_tot;
+  const int sms = (ctx->sketch_sms > 0) ? std::min(ctx->sketch_sms, num_sms) : num_sms;
+  const int64_t B = std::max<int64_t>(1, std::min<int64_t>(sms, Ttot));
+  // a unit split between blocks uses the slots of the block where it starts
+  int maxseg = 1;
+  for (int64_t b = 0; b + 1 < B; ++b) {
+    const int64_t s_last = (Ttot * (b + 1)) / B - 1;
+    if (s_last < 0) continue;
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sj[(size_t)mid].step0 <= s_last)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const srht_job &J = sj[(size_t)lo];
+    const int64_t g0 = J.step0 + ((s_last - J.step0) / J.J) * J.J;
+    const int64_t f = ((g0 + 1) * B - 1) / Ttot, l = ((g0 + J.J) * B - 1) / Ttot;
+    maxseg = std::max<int>(maxseg, (int)(l - f + 1));
+  }
+  const size_t tables = align_up((size_t)nb * sizeof(srht_job), 256) + align_up((size_t)nb * sizeof(plan_job), 256) +
+                        2 * align_up((size_t)(nb + 1) * sizeof(int64_t), 256);
+  const size_t part_bytes = align_up((size_t)B * maxseg * rpg_max * sizeof(float), 256);
+  int st = ensure_workspace(ctx, tables + plan_bytes + part_bytes + 4096);
+  if (st) return st;
+  unsigned int *counters = nullptr;
+  st = ensure_counters(ctx, (size_t)B, &counters);
+  if (st) return st;
+  st = ensure_pinned(ctx, tables);
+  if (st) return st;
+  ws_carver wc(ctx->ws);
+  char *d_tables = wc.take<char>(tables);
+  float *part = wc.take<float>((size_t)B * maxseg * rpg_max);
+  for (int t = 0; t < nb; ++t) {
+    plan_job &P = pj[(size_t)t];
+    srht_job &J = sj[(size_t)t];
+    plan_t pl;
+    pl.slots = P.slots;
+    pl.kgroups = P.kgroups;
+    pl.rows_per_group = P.rows_per_group;
+    carve_plan(wc, pl);
+    P.pk = pl.pk;
+    P.k = pl.k;
+    P.signs = wc.take<uint64_t>((size_t)P.sign_words);
+    J.pk = P.pk;
+    J.pkk = P.k;
+    J.signs = P.signs;
+    if (J.vec) {
+      st = column_map(&J.tmA, J.A, J.n_raw, J.d, J.lda);
+      if (!st) st = column_map(&J.tmB, J.B, J.n_raw, 1, J.n_raw);
+      if (st) return st;
+    }
+  }
+  char *h = (char *)ctx->pinned;
+  memcpy(h, sj.data(), (size_t)nb * sizeof(srht_job));
+  size_t off = align_up((size_t)nb * sizeof(srht_job), 256);
+  memcpy(h + off, pj.data(), (size_t)nb * sizeof(plan_job));
+  const size_t off_p = off;
+  off += align_up((size_t)nb * sizeof(plan_job), 256);
+  memcpy(h + off, first_s.data(), (size_t)(nb + 1) * sizeof(int64_t));
+  const size_t off_fs = off;
+  off += align_up((size_t)(nb + 1) * sizeof(int64_t), 256);
+  memcpy(h + off, first_p.data(), (size_t)(nb + 1) * sizeof(int64_t));
+  const size_t off_fp = off;
+  RNNLS_CUDA_TRY(cudaMemcpyAsync(d_tables, h, tables, cudaMemcpyHostToDevice, s));
+  RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
+  {
+    prof_scope ps(ctx, K_PLAN);
+    st = launch_plan_batched(s, (const plan_job *)(d_tables + off_p), (const int64_t *)(d_tables + off_fs),
+                             (const int64_t *)(d_tables + off_fp), nb, samp_tot, plan_tot);
+  }
+  if (st) return st;
+  static bool ready = false;
+  if (!ready) {
+    RNNLS_CUDA_TRY(cudaFuncSetAttribute(sketch_srht_batch_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kSketchSmem));
+    ready = true;
+  }
+  prof_scope ps_main(ctx, K_SKETCH);
+  sketch_srht_batch_f32<<<(unsigned)B, kThreads, kSketchSmem, s>>>((const srht_job *)d_tables, nb, Ttot, part, maxseg,
+                                                                    rpg_max, counters);
+  return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 
 int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, void *scratch, size_t bytes) {

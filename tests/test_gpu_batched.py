@@ -1,0 +1,85 @@
+"""GPU parity of the batched sketch (rnnls_sketch_batched) on uneven instances.
+
+Every instance of a batch must get the sketch rnnls_sketch gives it alone:
+the same rows bit for bit, SA and Sb within FP32 summation-order noise
+(1e-6 relative), and within the oracle tolerance of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_util import dev_colmajor, dev_vec, host, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_SAME = 1e-6
+
+# (n_raw, d, r): chunked sizes with few and many rows per thread (TMEM), a
+# ragged tail, one below the chunked size, one with a leading dimension not a
+# multiple of 4 (plain loads)
+SHAPES = [((1 << 14) + 7, 3, 300), (1 << 16, 17, 4096), (70001, 9, 20000), (5000, 4, 700), (1 << 17, 40, 9000),
+          (40000, 2, 33000)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_0812_4547_gb300 as P
+
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+def _make(rng, n, d, r, pad=0):
+    import torch
+
+    A = rng.standard_normal((n, d)).astype(np.float32)
+    b = rng.standard_normal(n).astype(np.float32)
+    if pad:
+        buf = torch.zeros((d, n + pad), dtype=torch.float32, device="cuda")
+        buf[:, :n] = torch.from_numpy(np.ascontiguousarray(A.T)).cuda()
+        A_d = buf.t()[:n]
+    else:
+        A_d = dev_colmajor(A)
+    return A, b, A_d, dev_vec(b)
+
+
+def test_batched_equals_one_by_one(ctx, orc):
+    import torch
+
+    rng = np.random.default_rng(5)
+    items, data = [], []
+    for t, (n, d, r) in enumerate(SHAPES):
+        A, b, A_d, b_d = _make(rng, n, d, r, pad=3 if t == 2 else 0)
+        SA = torch.full((d, r), float("nan"), device="cuda").t()
+        Sb = torch.full((r,), float("nan"), device="cuda")
+        idx = torch.full((r,), -1, dtype=torch.int32, device="cuda")
+        items.append((A_d, b_d, r, 100 + t, t, SA, Sb, idx))
+        data.append((A, b, A_d, b_d, r, 100 + t, t))
+    for rep in range(2):  # twice: the partial-sum counters must be left at zero
+        ctx.sketch_batched(items)
+        torch.cuda.synchronize()
+        for (A, b, A_d, b_d, r, seed, inst), it in zip(data, items):
+            SA1, Sb1, idx1, _ = ctx.sketch(A_d, b_d, r, seed=seed, instance=inst)
+            assert np.array_equal(host(it[7]), host(idx1))
+            assert rel_fro(host(it[5]), host(SA1).astype(np.float64)) <= TOL_SAME
+            assert rel_fro(host(it[6]), host(Sb1).astype(np.float64)) <= TOL_SAME
+    for (A, b, A_d, b_d, r, seed, inst), it in list(zip(data, items))[:3]:
+        SA_o, Sb_o, idx_o = orc.sketch(A.astype(np.float64), b.astype(np.float64), r, seed, inst)
+        assert np.array_equal(host(it[7]), idx_o)
+        assert rel_fro(host(it[5]), SA_o) <= TOL_F32
+        assert rel_fro(host(it[6]), Sb_o) <= TOL_F32
+
+
+def test_batched_rejects_bad_job(ctx):
+    import torch
+
+    import paper_0812_4547_gb300 as P
+
+    A = torch.zeros((2, 20000), device="cuda").t()
+    b = torch.zeros(20000, device="cuda")
+    SA = torch.zeros((2, 100), device="cuda").t()
+    Sb = torch.zeros(100, device="cuda")
+    idx = torch.zeros(100, dtype=torch.int32, device="cuda")
+    with pytest.raises(P.RNNLSError):
+        ctx.sketch_batched([(A, b, 100, 1, 0, SA, Sb, idx), (A, b, 0, 1, 0, SA, Sb, idx)])
