@@ -146,9 +146,11 @@ int launch_sample_bernoulli(cudaStream_t s, uint64_t seed, uint64_t inst, int L,
 // into free positions of other lanes (one extra shared-memory wavefront
 // each); empty positions read a word of their own bank and write nothing.
 //
-// Entry encoding: pk = 4 * (smem word of l) | ((h >> 2) << 14) | ((h & 1) << 31)
-// | (((h >> 1) & 1) << 30), so bits 2-13 are the byte offset of l in a
-// chunk, bit 31 the sign of chunk 4j + 1 and bit 30 that of chunk 4j + 2;
+// Entry encoding: pk = 4 * (smem word of l) | ((h & 3) << 14) | ((h >> 2) << 16)
+// | ((h & 1) << 31) | (((h >> 1) & 1) << 30), so bits 2-13 are the byte
+// offset of l in a chunk, bits 2-15 its byte offset in the step's chunk
+// (h & 3) (used once the step's four chunks have been transformed into one
+// another), bit 31 the sign of chunk 4j + 1 and bit 30 that of chunk 4j + 2;
 // k = row index in the sketch (-1: empty).  n <= 2^28 keeps h >> 2 below
 // 2^14.
 // ---------------------------------------------------------------------------
@@ -213,7 +215,7 @@ __device__ __forceinline__ void plan_block(int blk, const int32_t *__restrict__ 
   auto place = [&](uint32_t pos, uint32_t ln, uint32_t row, int64_t k) {
     const uint32_t l = row & (kM - 1), h = row >> kLogM;
     const size_t e = (size_t)(pos >> 3) * kThreads + (pos & 7u) * 32u + ln;
-    pk_out[e] = (swz128(l) << 2) | ((h >> 2) << 14) | ((h & 1u) << 31) | (((h >> 1) & 1u) << 30);
+    pk_out[e] = (swz128(l) << 2) | ((h & 3u) << 14) | ((h >> 2) << 16) | ((h & 1u) << 31) | (((h >> 1) & 1u) << 30);
     k_out[e] = (int32_t)k;
   };
   // rows k = t0 + 4 tid .. + 3 of this round, in draw order (thread, then e)

@@ -42,6 +42,13 @@ constexpr int kStageFloats = kWorkers * kM;                  // one step: four c
 // stage buffers plus slack to place them at a 16 KiB boundary
 constexpr size_t kSketchSmem = (size_t)kStages * kStageFloats * sizeof(float) + 16384;  // 208 KiB
 constexpr uint32_t kSpinLimit = 1u << 22;                    // bounded wait on a bulk copy
+// From this many plan rows per thread on, a step's four chunks are first
+// transformed into one another (a 16384-point transform per step), so that
+// each row reads one word instead of four.
+#ifndef RNNLS_FULL_MIN_SLOTS
+#define RNNLS_FULL_MIN_SLOTS 48
+#endif
+constexpr int kFullMinSlots = RNNLS_FULL_MIN_SLOTS;
 
 __device__ __forceinline__ void bar_worker(int w) {
   asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
@@ -129,6 +136,51 @@ __device__ __forceinline__ void lds_x4(uint32_t a, float &z0, float &z1, float &
       "[%4+49152];"
       : "=f"(z0), "=f"(z1), "=f"(z2), "=f"(z3)
       : "r"(a));
+}
+
+// one word at byte address `a` of shared memory
+__device__ __forceinline__ float lds_1(uint32_t a) {
+  float z;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(z) : "r"(a));
+  return z;
+}
+
+// (a, b) <- (a + b, a - b) on four lanes, as two packed f32x2 pairs
+__device__ __forceinline__ void bfly4(float4 &a, float4 &b) {
+  const unsigned long long a0 = pack2(a.x, a.y), a1 = pack2(a.z, a.w);
+  const unsigned long long b0 = pack2(b.x, b.y), b1 = pack2(b.z, b.w);
+  unsigned long long s0, s1, d0, d1;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s0) : "l"(a0), "l"(b0));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s1) : "l"(a1), "l"(b1));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(a0), "l"(b0));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(a1), "l"(b1));
+  unpack2(s0, a.x, a.y);
+  unpack2(s1, a.z, a.w);
+  unpack2(d0, b.x, b.y);
+  unpack2(d1, b.z, b.w);
+}
+
+// The 4-point transform across a step's four transformed chunks, word by
+// word: chunk slot c <- sum_c' (-1)^popcount(c & c') z_c' (the H_4 factor of
+// H_16384 = H_4 (x) H_4096; the same word of every chunk holds the same
+// position l).  Thread t takes the 16-byte units t, t + 256, ...
+__device__ __forceinline__ void cross_chunk_h4(float *__restrict__ st, int tid) {
+#pragma unroll
+  for (int k = 0; k < kM / (4 * kThreads); ++k) {
+    const int o = 4 * (tid + kThreads * k);
+    float4 z0 = *reinterpret_cast<const float4 *>(st + o);
+    float4 z1 = *reinterpret_cast<const float4 *>(st + kM + o);
+    float4 z2 = *reinterpret_cast<const float4 *>(st + 2 * kM + o);
+    float4 z3 = *reinterpret_cast<const float4 *>(st + 3 * kM + o);
+    bfly4(z0, z1);
+    bfly4(z2, z3);
+    bfly4(z0, z2);
+    bfly4(z1, z3);
+    *reinterpret_cast<float4 *>(st + o) = z0;
+    *reinterpret_cast<float4 *>(st + kM + o) = z1;
+    *reinterpret_cast<float4 *>(st + 2 * kM + o) = z2;
+    *reinterpret_cast<float4 *>(st + 3 * kM + o) = z3;
+  }
 }
 
 // ---- tensor memory (TMEM) ----------------------------------------------------
@@ -241,6 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t stage_u32 = (raw_u32 + 16383u) & ~16383u;
   float *stage = dyn_smem + (stage_u32 - raw_u32) / 4;
   const int64_t nrow32 = n_raw >> 5;  // whole 32-row lines of a column
+  const bool full = SLOTS > 0 ? (SLOTS >= kFullMinSlots) : (slots >= kFullMinSlots);
 
   if (tid == 0) {
     for (int q = 0; q < kStages; ++q) mbar_init(smem_u32(&mbar[q]), 1);
@@ -367,6 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int h = 0; h < 2; ++h) {
           const int64_t line = (4 * j + w) * (int64_t)(kM / 32) + 64 * h + wt;
           if (line == nrow32) {
+#pragma unroll
             for (int e = 0; e < 32; ++e) {
               const int64_t row = 32 * line + e;
               zw[swz128((uint32_t)((h << 11) | (wt << 5) | e))] = (row < n_raw) ? x[row] : 0.0f;
@@ -409,20 +463,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < 64; ++s) zw[hi | ((uint32_t)s << 5) | (lane ^ (((uint32_t)s & 7u) << 2))] = v[s];
     }
     __syncthreads();  // the four transformed chunks are ready
+    if (full) {       // ... and transformed into one another
+      cross_chunk_h4(stage + q * kStageFloats, tid);
+      __syncthreads();
+    }
 
-    // combine: row (hq, c1, c2) adds (-1)^popcount(hq & j) (z0 + s1 z1 + s2 (z2 + s1 z3))[l],
-    // eight rows at a time (plan words and sums move between TMEM and registers)
-    const uint32_t jm = (uint32_t)(j + jg0) << 14;
+    // combine: row (hq, c1, c2) adds (-1)^popcount(hq & j) (z0 + s1 z1 + s2 (z2 + s1 z3))[l]
+    // (full: the word of l in chunk slot h & 3), eight rows at a time (plan words and sums
+    // move between TMEM and registers)
+    const uint32_t jm = (uint32_t)(j + jg0) << 16;
     if constexpr (SLOTS > 0) {
+      if constexpr (SLOTS >= kFullMinSlots) {
 #pragma unroll
-      for (int e = 0; e < SLOTS; ++e) {
-        const uint32_t p = pk_r[e];
-        float z0, z1, z2, z3;
-        lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
-        const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
-        const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
-        const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
-        acc_r[e] += xor_sign(t, (uint32_t)__popc(p & jm) << 31);
+        for (int e = 0; e < SLOTS; ++e) {
+          const uint32_t p = pk_r[e];
+          acc_r[e] += xor_sign(lds_1(step_u32 + (p & 0xfffcu)), (uint32_t)__popc(p & jm) << 31);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < SLOTS; ++e) {
+          const uint32_t p = pk_r[e];
+          float z0, z1, z2, z3;
+          lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+          const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
+          const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
+          const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
+          acc_r[e] += xor_sign(t, (uint32_t)__popc(p & jm) << 31);
+        }
       }
     } else {
       // batch k+1 is loaded from TMEM while batch k is combined
@@ -437,15 +504,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld8(t_pk + s8 + 8, pkn);
           tmem_ld8(t_acc + s8 + 8, accn);
         }
+        if (full) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const uint32_t p = pk[e];
-          float z0, z1, z2, z3;
-          lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
-          const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
-          const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
-          const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
-          acc[e] = __float_as_uint(__uint_as_float(acc[e]) + xor_sign(t, (uint32_t)__popc(p & jm) << 31));
+          for (int e = 0; e < 8; ++e) {
+            const uint32_t p = pk[e];
+            const float y = lds_1(step_u32 + (p & 0xfffcu));
+            acc[e] = __float_as_uint(__uint_as_float(acc[e]) + xor_sign(y, (uint32_t)__popc(p & jm) << 31));
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const uint32_t p = pk[e];
+            float z0, z1, z2, z3;
+            lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+            const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
+            const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
+            const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
+            acc[e] = __float_as_uint(__uint_as_float(acc[e]) + xor_sign(t, (uint32_t)__popc(p & jm) << 31));
+          }
         }
         tmem_st8(t_acc + s8, acc);
         if (more) {
@@ -503,25 +579,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int e = 0; e < RS; ++e) acc_r[e] = 0.0f;
       } else {
         tmem_wait_st();
-        for (int s8 = 0; s8 < slots; s8 += 8) {
-          uint32_t acc[8];
-          tmem_ld8(t_acc + s8, acc);
+        // 32 rows at a time: their indices and sums are fetched together
+        for (int s32 = 0; s32 < slots; s32 += 32) {
+          const int n8 = min(4, (slots - s32) >> 3);
+          int32_t kk[32];
+          uint32_t acc[32];
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            kk[e] = (e < 8 * n8) ? plan_k[((size_t)kg * slots + s32 + e) * kThreads + tid] : -1;
+#pragma unroll
+          for (int b8 = 0; b8 < 4; ++b8)
+            if (b8 < n8) tmem_ld8(t_acc + s32 + 8 * b8, acc + 8 * b8);
           tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int32_t k = plan_k[((size_t)kg * slots + s8 + e) * kThreads + tid];
-            if (k < 0) continue;
+          for (int e = 0; e < 32; ++e) {
+            if (kk[e] < 0) continue;
             const float a = poisoned ? __int_as_float(0x7fc00000) : __uint_as_float(acc[e]);
             if (nseg == 1) {
               if (col < d)
-                SA[(int64_t)col * ldsa + k] = scale * a;
+                SA[(int64_t)col * ldsa + kk[e]] = scale * a;
               else
-                SB[(int64_t)(col - d) * ldsb + k] = scale * a;
+                SB[(int64_t)(col - d) * ldsb + kk[e]] = scale * a;
             } else {
-              part[((size_t)seg * P.U + u) * rpg + (size_t)(s8 + e) * kThreads + tid] = a;
+              part[((size_t)seg * P.U + u) * rpg + (size_t)(s32 + e) * kThreads + tid] = a;
             }
           }
-          tmem_st8(t_acc + s8, zero8);
+#pragma unroll
+          for (int b8 = 0; b8 < 4; ++b8)
+            if (b8 < n8) tmem_st8(t_acc + s32 + 8 * b8, zero8);
         }
       }
       if (nseg > 1) {
@@ -595,7 +680,7 @@ struct srht_job {  // 64-byte aligned through its tensor maps
   float *SA, *SB;
   int64_t lda, ldb, ldsa, ldsb, n_raw, J, U, step0, rpg;
   float scale;
-  int d, slots, vec, pad;
+  int d, slots, vec, r;
 };
 
 __device__ __forceinline__ void fence_tensormap_acquire(const void *map) {
@@ -609,6 +694,19 @@ __device__ __forceinline__ int job_of_step(const srht_job *__restrict__ jobs, in
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (jobs[mid].step0 <= s)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// block whose step range [starts[b], starts[b+1]) holds step s (empty ranges skipped)
+__host__ __device__ __forceinline__ int64_t block_of_step(const int64_t *starts, int64_t B, int64_t s) {
+  int64_t lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= s)
       lo = mid;
     else
       hi = mid - 1;
@@ -649,8 +747,8 @@ struct batch_cursor {
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-    sketch_srht_batch_f32(const srht_job *__restrict__ jobs, int njobs, int64_t Ttot, float *__restrict__ part,
-                          int maxseg, int64_t rpg_max, unsigned int *__restrict__ counters) {
+    sketch_srht_batch_f32(const srht_job *__restrict__ jobs, int njobs, const int64_t *__restrict__ starts,
+                          float *__restrict__ part, int maxseg, int64_t rpg_max, unsigned int *__restrict__ counters) {
   extern __shared__ __align__(1024) float dyn_smem[];
   __shared__ __align__(16) uint32_t sgn[kStages][kWorkers][kM / 32];
   __shared__ __align__(8) uint64_t mbar[kStages];
@@ -663,8 +761,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int wt = tid & 63;
   const int64_t B = gridDim.x;
   const int64_t bid = blockIdx.x;
-  const int64_t s0 = (Ttot * bid) / B;
-  const int64_t nsteps = (Ttot * (bid + 1)) / B - s0;
+  const int64_t s0 = starts[bid];
+  const int64_t nsteps = starts[bid + 1] - s0;
   if (nsteps <= 0) return;
   const uint32_t raw_u32 = smem_u32(dyn_smem);
   const uint32_t stage_u32 = (raw_u32 + 16383u) & ~16383u;
@@ -778,6 +876,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int h = 0; h < 2; ++h) {
           const int64_t line = (4 * j + w) * (int64_t)(kM / 32) + 64 * h + wt;
           if (line == nrow32) {
+#pragma unroll
             for (int e = 0; e < 32; ++e) {
               const int64_t row = 32 * line + e;
               zw[swz128((uint32_t)((h << 11) | (wt << 5) | e))] = (row < n_raw) ? x[row] : 0.0f;
@@ -826,8 +925,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < 64; ++s) zw[hi | ((uint32_t)s << 5) | (lane ^ (((uint32_t)s & 7u) << 2))] = v[s];
     }
     __syncthreads();
+    const bool full = slots >= kFullMinSlots;
+    if (full) {
+      cross_chunk_h4(stage + q * kStageFloats, tid);
+      __syncthreads();
+    }
 
-    const uint32_t jm = (uint32_t)j << 14;
+    const uint32_t jm = (uint32_t)j << 16;
     {
       uint32_t pk[8], acc[8], pkn[8], accn[8];
       tmem_wait_st();
@@ -840,15 +944,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld8(t_pk + s8 + 8, pkn);
           tmem_ld8(t_acc + s8 + 8, accn);
         }
+        if (full) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const uint32_t p = pk[e];
-          float z0, z1, z2, z3;
-          lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
-          const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
-          const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
-          const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
-          acc[e] = __float_as_uint(__uint_as_float(acc[e]) + xor_sign(t, (uint32_t)__popc(p & jm) << 31));
+          for (int e = 0; e < 8; ++e) {
+            const uint32_t p = pk[e];
+            const float y = lds_1(step_u32 + (p & 0xfffcu));
+            acc[e] = __float_as_uint(__uint_as_float(acc[e]) + xor_sign(y, (uint32_t)__popc(p & jm) << 31));
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const uint32_t p = pk[e];
+            float z0, z1, z2, z3;
+            lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+            const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
+            const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
+            const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
+            acc[e] = __float_as_uint(__uint_as_float(acc[e]) + xor_sign(t, (uint32_t)__popc(p & jm) << 31));
+          }
         }
         tmem_st8(t_acc + s8, acc);
         if (more) {
@@ -862,6 +975,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     cur.next(jobs, njobs);
+    const int qs = q;  // this step's buffer
     if (++q == kStages) {
       q = 0;
       phase ^= 1u;
@@ -871,31 +985,76 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (j == J0.J - 1 || ls == nsteps - 1) {
       const bool poisoned = *(volatile int *)&stalled != 0;
       const int64_t g0 = J0.step0 + u * J0.J;  // the unit's first global step
-      const int64_t first = ((g0 + 1) * B - 1) / Ttot;
-      const int64_t last = ((g0 + J0.J) * B - 1) / Ttot;
+      const int64_t first = block_of_step(starts, B, g0);
+      const int64_t last = block_of_step(starts, B, g0 + J0.J - 1);
       const int64_t nseg = last - first + 1;
       const int64_t seg = bid - first;
       float *pslot = part + (size_t)first * maxseg * rpg_max;  // the unit starting in block `first`
       tmem_wait_st();
-      for (int s8 = 0; s8 < slots; s8 += 8) {
-        uint32_t acc[8];
-        tmem_ld8(t_acc + s8, acc);
+      if (nseg == 1) {
+        // Whole unit in this block: its rows k0 .. k0 + nk - 1 (a plan group
+        // holds consecutive rows) go through this step's buffer, 16384 at a
+        // time, so that the sketch column is written with coalesced stores.
+        // The buffer is refilled only after the next step's first barrier.
+        float *ost = stage + qs * kStageFloats;
+        const int64_t k0 = kg * J0.rpg;
+        const int64_t nk = min(J0.rpg, (int64_t)J0.r - k0);
+        float *dst = ((col < d) ? J0.SA + (int64_t)col * J0.ldsa : J0.SB) + k0;
+        for (int64_t h0 = 0; h0 < nk; h0 += kStageFloats) {
+          __syncthreads();  // the combine (or the previous copy) is done with the buffer
+          for (int s32 = 0; s32 < slots; s32 += 32) {
+            const int n8 = min(4, (slots - s32) >> 3);
+            int32_t kk[32];
+            uint32_t acc[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+              kk[e] = (e < 8 * n8) ? J0.pkk[((size_t)kg * slots + s32 + e) * kThreads + tid] : -1;
+#pragma unroll
+            for (int b8 = 0; b8 < 4; ++b8)
+              if (b8 < n8) tmem_ld8(t_acc + s32 + 8 * b8, acc + 8 * b8);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const int64_t o = (int64_t)kk[e] - k0 - h0;
+              if (kk[e] < 0 || o < 0 || o >= kStageFloats) continue;
+              ost[o] = poisoned ? __int_as_float(0x7fc00000) : J0.scale * __uint_as_float(acc[e]);
+            }
+          }
+          __syncthreads();
+          const int64_t cnt = min((int64_t)kStageFloats, nk - h0);
+          for (int64_t i = tid; i < cnt; i += kThreads) dst[h0 + i] = ost[i];
+        }
+        for (int s8 = 0; s8 < slots; s8 += 8) tmem_st8(t_acc + s8, zero8);
+      } else {
+      // 32 rows at a time: their indices and sums are fetched together
+      for (int s32 = 0; s32 < slots; s32 += 32) {
+        const int n8 = min(4, (slots - s32) >> 3);
+        int32_t kk[32];
+        uint32_t acc[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+          kk[e] = (e < 8 * n8) ? J0.pkk[((size_t)kg * slots + s32 + e) * kThreads + tid] : -1;
+#pragma unroll
+        for (int b8 = 0; b8 < 4; ++b8)
+          if (b8 < n8) tmem_ld8(t_acc + s32 + 8 * b8, acc + 8 * b8);
         tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int32_t k = J0.pkk[((size_t)kg * slots + s8 + e) * kThreads + tid];
-          if (k < 0) continue;
+        for (int e = 0; e < 32; ++e) {
+          if (kk[e] < 0) continue;
           const float a = poisoned ? __int_as_float(0x7fc00000) : __uint_as_float(acc[e]);
           if (nseg == 1) {
             if (col < d)
-              J0.SA[(int64_t)col * J0.ldsa + k] = J0.scale * a;
+              J0.SA[(int64_t)col * J0.ldsa + kk[e]] = J0.scale * a;
             else
-              J0.SB[k] = J0.scale * a;
+              J0.SB[kk[e]] = J0.scale * a;
           } else {
-            pslot[(size_t)seg * rpg_max + (size_t)(s8 + e) * kThreads + tid] = a;
+            pslot[(size_t)seg * rpg_max + (size_t)(s32 + e) * kThreads + tid] = a;
           }
         }
-        tmem_st8(t_acc + s8, zero8);
+#pragma unroll
+        for (int b8 = 0; b8 < 4; ++b8)
+          if (b8 < n8) tmem_st8(t_acc + s32 + 8 * b8, zero8);
+      }
       }
       if (nseg > 1) {
         __threadfence();
@@ -1241,7 +1400,7 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
     J.A = jb.A; J.B = jb.b; J.lda = jb.lda; J.ldb = jb.n_raw; J.ldsa = jb.ldsa; J.ldsb = jb.ldsa;
     J.n_raw = jb.n_raw; J.J = (jb.n_raw + 4 * (int64_t)kM - 1) / (4 * (int64_t)kM);
     J.U = (int64_t)kgroups * (jb.d + 1); J.step0 = Ttot; J.rpg = rpg; J.scale = (float)(1.0 / sqrt((double)jb.r));
-    J.d = (int)jb.d; J.slots = slots; J.SA = jb.SA; J.SB = jb.Sb;
+    J.d = (int)jb.d; J.slots = slots; J.r = (int)jb.r; J.SA = jb.SA; J.SB = jb.Sb;
     J.vec = (((uintptr_t)jb.A % 16 == 0) && (jb.lda % 4 == 0) && ((uintptr_t)jb.b % 16 == 0)) ? 1 : 0;
     Ttot += J.U * J.J;
     rpg_max = std::max(rpg_max, rpg);
@@ -1258,10 +1417,35 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
   first_p[(size_t)nb] = plan_tot;
   const int sms = (ctx->sketch_sms > 0) ? std::min(ctx->sketch_sms, num_sms) : num_sms;
   const int64_t B = std::max<int64_t>(1, std::min<int64_t>(sms, Ttot));
+  // Block ranges of equal estimated cost: a step costs about 104 + slots
+  // (the transform, then one word per plan row), plus the unit's write-out
+  // (slots) spread over its J steps.
+  std::vector<int64_t> starts((size_t)B + 1);
+  {
+    std::vector<double> wt((size_t)nb), cum((size_t)nb + 1, 0.0);
+    for (int t = 0; t < nb; ++t) {
+      const srht_job &J = sj[(size_t)t];
+      wt[(size_t)t] = 104.0 + J.slots + (double)J.slots / (double)J.J;
+      cum[(size_t)t + 1] = cum[(size_t)t] + wt[(size_t)t] * (double)(J.U * J.J);
+    }
+    int t = 0;
+    starts[0] = 0;
+    for (int64_t b = 1; b < B; ++b) {
+      const double target = cum[(size_t)nb] * (double)b / (double)B;
+      while (t + 1 < nb && cum[(size_t)t + 1] <= target) ++t;
+      const srht_job &J = sj[(size_t)t];
+      int64_t st_b = J.step0 + (int64_t)((target - cum[(size_t)t]) / wt[(size_t)t]);
+      // every block keeps at least one step (a split unit then has a segment in
+      // every block of its span)
+      st_b = std::max(st_b, starts[(size_t)b - 1] + 1);
+      starts[(size_t)b] = std::min(st_b, Ttot - (B - b));
+    }
+    starts[(size_t)B] = Ttot;
+  }
   // a unit split between blocks uses the slots of the block where it starts
   int maxseg = 1;
-  for (int64_t b = 0; b + 1 < B; ++b) {
-    const int64_t s_last = (Ttot * (b + 1)) / B - 1;
+  for (int64_t b = 1; b < B; ++b) {
+    const int64_t s_last = starts[(size_t)b] - 1;
     if (s_last < 0) continue;
     int lo = 0, hi = nb - 1;
     while (lo < hi) {
@@ -1273,11 +1457,12 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
     }
     const srht_job &J = sj[(size_t)lo];
     const int64_t g0 = J.step0 + ((s_last - J.step0) / J.J) * J.J;
-    const int64_t f = ((g0 + 1) * B - 1) / Ttot, l = ((g0 + J.J) * B - 1) / Ttot;
+    const int64_t f = block_of_step(starts.data(), B, g0), l = block_of_step(starts.data(), B, g0 + J.J - 1);
     maxseg = std::max<int>(maxseg, (int)(l - f + 1));
   }
   const size_t tables = align_up((size_t)nb * sizeof(srht_job), 256) + align_up((size_t)nb * sizeof(plan_job), 256) +
-                        2 * align_up((size_t)(nb + 1) * sizeof(int64_t), 256);
+                        2 * align_up((size_t)(nb + 1) * sizeof(int64_t), 256) +
+                        align_up((size_t)(B + 1) * sizeof(int64_t), 256);
   const size_t part_bytes = align_up((size_t)B * maxseg * rpg_max * sizeof(float), 256);
   int st = ensure_workspace(ctx, tables + plan_bytes + part_bytes + 4096);
   if (st) return st;
@@ -1320,6 +1505,9 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
   off += align_up((size_t)(nb + 1) * sizeof(int64_t), 256);
   memcpy(h + off, first_p.data(), (size_t)(nb + 1) * sizeof(int64_t));
   const size_t off_fp = off;
+  off += align_up((size_t)(nb + 1) * sizeof(int64_t), 256);
+  memcpy(h + off, starts.data(), (size_t)(B + 1) * sizeof(int64_t));
+  const size_t off_st = off;
   RNNLS_CUDA_TRY(cudaMemcpyAsync(d_tables, h, tables, cudaMemcpyHostToDevice, s));
   RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
   {
@@ -1335,8 +1523,8 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
     ready = true;
   }
   prof_scope ps_main(ctx, K_SKETCH);
-  sketch_srht_batch_f32<<<(unsigned)B, kThreads, kSketchSmem, s>>>((const srht_job *)d_tables, nb, Ttot, part, maxseg,
-                                                                    rpg_max, counters);
+  sketch_srht_batch_f32<<<(unsigned)B, kThreads, kSketchSmem, s>>>(
+      (const srht_job *)d_tables, nb, (const int64_t *)(d_tables + off_st), part, maxseg, rpg_max, counters);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 

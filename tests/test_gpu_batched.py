@@ -19,6 +19,9 @@ TOL_SAME = 1e-6
 # multiple of 4 (plain loads)
 SHAPES = [((1 << 14) + 7, 3, 300), (1 << 16, 17, 4096), (70001, 9, 20000), (5000, 4, 700), (1 << 17, 40, 9000),
           (40000, 2, 33000)]
+# few steps (188) of very different cost for 152 blocks: the cost-weighted
+# block ranges are clamped to one step each and short units are split
+FEW = [(20000, 30, 32768), (16385, 40, 2048), (50000, 10, 8192)]
 
 
 @pytest.fixture(scope="module")
@@ -44,12 +47,13 @@ def _make(rng, n, d, r, pad=0):
     return A, b, A_d, dev_vec(b)
 
 
-def test_batched_equals_one_by_one(ctx, orc):
+@pytest.mark.parametrize("shapes", [SHAPES, FEW], ids=["uneven", "few-steps"])
+def test_batched_equals_one_by_one(ctx, orc, shapes):
     import torch
 
     rng = np.random.default_rng(5)
     items, data = [], []
-    for t, (n, d, r) in enumerate(SHAPES):
+    for t, (n, d, r) in enumerate(shapes):
         A, b, A_d, b_d = _make(rng, n, d, r, pad=3 if t == 2 else 0)
         SA = torch.full((d, r), float("nan"), device="cuda").t()
         Sb = torch.full((r,), float("nan"), device="cuda")
