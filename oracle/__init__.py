@@ -16,6 +16,8 @@ this module compiles it with gcc and exposes numpy-level wrappers:
   Lawson-Hanson solve of Alg. 1 step 5 on the QP form of Sec. 3.4.
 * :func:`residual_sq`, :func:`randomized_nnls`, :func:`exact_nnls` --
   Definition 1's objective and the residual ratio of Theorem 1.
+* :func:`boosted_nnls` -- repetitions of Alg. 1, best full residual kept
+  (the footnote to Theorem 1).
 """
 from __future__ import annotations
 
@@ -295,6 +297,32 @@ def randomized_nnls(A, b, r: int, seed: int, instance: int = 0, mode: int = MODE
     SA, Sb, idx = sketch(A, b, r, seed, instance, mode, nthreads)
     x, info = nnls(SA, Sb)
     return x, info, (SA, Sb, idx)
+
+
+def boosted_nnls(A, b, r: int, seed: int, k: int, instance0: int = 0, mode: int = MODE_IID, nthreads: int = 1):
+    """Repeated RandomizedNNLS (the footnote to Theorem 1 in Sec. 1: a few
+    independent repetitions raise the success probability of the (1 + eps)
+    bound).  Repetition j runs Alg. 1 with randomness (seed, instance0 + j);
+    the answer is the repetition with the smallest full residual
+    ||A x_j - b||^2 among those whose Lawson-Hanson solve ended with status
+    OK (ties to the smallest j; if none did, repetition 0).
+
+    Returns (x, best, residuals, infos): residuals[j] = ||A x_j - b||^2 for
+    every repetition, infos[j] its solve's info."""
+    if k < 1:
+        raise ValueError("k >= 1 repetitions")
+    xs, res, infos = [], [], []
+    for j in range(k):
+        x, info, _ = randomized_nnls(A, b, r, seed, instance0 + j, mode, nthreads)
+        xs.append(x)
+        infos.append(info)
+        res.append(residual_sq(A, b, x))
+    best = -1
+    for j in range(k):
+        if infos[j]["status"] == OK and np.isfinite(res[j]) and (best < 0 or res[j] < res[best]):
+            best = j
+    best = max(best, 0)
+    return xs[best], best, np.array(res, dtype=np.float64), infos
 
 
 def exact_nnls(A, b):
