@@ -230,6 +230,27 @@ int rnnls_solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float
  * HOST array of `count` descriptors whose pointers are device pointers. */
 int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count, uint32_t flags);
 
+/* Repeated RandomizedNNLS (the footnote to Theorem 1 in Sec. 1: a few
+ * independent repetitions raise the success probability of the (1 + eps)
+ * bound from 1/2 to at least 1 - 2^-k).  Run j (j < k) is Alg. 1 exactly as
+ * rnnls_sketch (iid rows, seed, instance instance0 + j) followed by
+ * rnnls_solve; the answer is the run with the smallest full residual
+ * ||A x_j - b||^2 among the runs whose solve ended with status OK (ties to
+ * the smallest j; run 0 when none did).  The residuals are evaluated in one
+ * pass over A: row dot products in FP32 on FP32 copies of x_j, squared row
+ * residuals summed in FP64.
+ * A: n_raw x d FP32 column-major (lda >= n_raw), b: n_raw, device.
+ * Outputs (device, caller-owned): x (FP64, d) the kept run's solution;
+ * resid (FP64, k, nullable) every run's residual; best (int32, 1, nullable)
+ * the kept run's j; info (nullable) the kept run's solve info.
+ * Requires 1 <= k <= 16 and d <= 256 (EUNSUPPORTED otherwise).  Scratch (k
+ * sketches, k solutions) lives in the context and is reused by the next
+ * call.  Errors: EINVAL (null pointer, a size < 1, lda < n_raw),
+ * EUNSUPPORTED, ENOMEM, ECUDA. */
+int rnnls_solve_boosted(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d,
+                        int64_t r, uint64_t seed, uint64_t instance0, int k, double *x, double *resid, int32_t *best,
+                        rnnls_info *info);
+
 /* Objective of Definition 1 on the full data: out[0] = ||A x - b||^2 with
  * A n x d (lda >= n) and b FP32, x FP64 (device), accumulated in FP64.
  * out: device double. */

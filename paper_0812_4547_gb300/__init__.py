@@ -194,6 +194,26 @@ class Context:
                                        info.data_ptr() if info is not None else None))
         B.rnnls_solve_batched(self.handle, descs, 0)
 
+    def solve_boosted(self, A, b, r: int, k: int, seed: int, instance0: int = 0, x=None, resid=None, best=None,
+                      info=None):
+        """k runs of Alg. 1 (instances instance0 .. instance0 + k - 1), the one with the smallest
+        ||A x_j - b||^2 kept; returns (x, resid (k), best (1, int32), info bytes), all on the device."""
+        torch = _torch()
+        A = colmajor(A)
+        n, d = A.shape
+        dev = A.device
+        if x is None:
+            x = torch.empty(d, dtype=torch.float64, device=dev)
+        if resid is None:
+            resid = torch.empty(k, dtype=torch.float64, device=dev)
+        if best is None:
+            best = torch.empty(1, dtype=torch.int32, device=dev)
+        if info is None:
+            info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=dev)
+        B.rnnls_solve_boosted(self.handle, A.data_ptr(), _ld(A), b.data_ptr(), n, d, r, seed, instance0, k,
+                              x.data_ptr(), resid.data_ptr(), best.data_ptr(), info.data_ptr())
+        return x, resid, best, info
+
     def residual(self, A, b, x, out=None):
         """||A x - b||^2 on the full data (FP64 accumulation), a 1-element device tensor."""
         torch = _torch()

@@ -31,7 +31,7 @@ EXPORTS = (
     "rnnls_create", "rnnls_destroy", "rnnls_set_stream", "rnnls_sketch", "rnnls_sketch_f64", "rnnls_solve",
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
-    "rnnls_solve_multi", "rnnls_sketch_batched",
+    "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted",
 )
 
 
@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_solve_multi.argtypes = [P, P, I64, P, I64, I64, I64, I64, P, I64, P]
         L.rnnls_sketch_batched.argtypes = [P, ctypes.POINTER(rnnls_sketch_job), I64]
         L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
+        L.rnnls_solve_boosted.argtypes = [P, P, I64, P, I64, I64, I64, U64, U64, I32, P, P, P, P]
         L.rnnls_profile_begin.argtypes = [P, I32]
         L.rnnls_profile_end.argtypes = [P, ctypes.POINTER(rnnls_kernel_time), I32, ctypes.POINTER(I32)]
         L.rnnls_sketch_noalloc.argtypes = [P, P, I64, P, I64, I64, I64, U64, U64, P, I64, P, P]
@@ -217,6 +218,12 @@ def rnnls_solve_multi(ctx, SA, ldsa, SB, ldsb, r, d, nrhs, X, ldx, infos) -> Non
 def rnnls_solve_batched(ctx, problems, flags: int = 0) -> None:
     arr = (rnnls_problem * len(problems))(*problems)
     check(lib().rnnls_solve_batched(ctypes.c_void_p(ctx), arr, len(problems), flags), "rnnls_solve_batched")
+
+
+def rnnls_solve_boosted(ctx, A, lda, b, n_raw, d, r, seed, instance0, k, x, resid, best, info) -> None:
+    check(lib().rnnls_solve_boosted(ctypes.c_void_p(ctx), ctypes.c_void_p(A), lda, ctypes.c_void_p(b), n_raw, d, r,
+                                    seed, instance0, k, ctypes.c_void_p(x), ctypes.c_void_p(resid),
+                                    ctypes.c_void_p(best), ctypes.c_void_p(info)), "rnnls_solve_boosted")
 
 
 def rnnls_residual(ctx, A, lda, b, n, d, x, out) -> None:

@@ -78,7 +78,7 @@ int ensure_pinned(rnnls_ctx *ctx, size_t bytes) {
 const char *kernel_name(int kid) {
   static const char *names[K_COUNT] = {"sample_rows", "build_plan", "sketch_srht_f32", "sketch_small",
                                        "reduce_partials", "sketch_f64", "gram", "gram_reduce", "colabs",
-                                       "lawson_hanson", "residual"};
+                                       "lawson_hanson", "residual", "boost_residual", "boost_select"};
   return (kid >= 0 && kid < K_COUNT) ? names[kid] : "?";
 }
 
@@ -239,6 +239,7 @@ int rnnls_destroy(rnnls_ctx *ctx) {
   profile_free(ctx);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->aux) cudaFree(ctx->aux);
+  if (ctx->boost) cudaFree(ctx->boost);
   if (ctx->counters) cudaFree(ctx->counters);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   cudaEventDestroy(ctx->pinned_ready);
@@ -508,6 +509,15 @@ int rnnls_residual(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, 
   if (!ctx || !A || !b || !x || !out || n < 1 || d < 1 || lda < n) return RNNLS_EINVAL;
   RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
   return residual_f32(ctx, A, lda, b, n, d, x, out);
+}
+
+int rnnls_solve_boosted(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d,
+                        int64_t r, uint64_t seed, uint64_t instance0, int k, double *x, double *resid, int32_t *best,
+                        rnnls_info *info) {
+  if (!ctx || !A || !b || !x || n_raw < 1 || d < 1 || r < 1 || lda < n_raw || k < 1) return RNNLS_EINVAL;
+  if (k > kBoostMaxK || d > kBoostMaxD || n_raw > kMaxRows || r > ((int64_t)1 << 30)) return RNNLS_EUNSUPPORTED;
+  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  return solve_boosted_f32(ctx, A, lda, b, n_raw, d, r, seed, instance0, k, x, resid, best, info);
 }
 
 const char *rnnls_strerror(int status) {

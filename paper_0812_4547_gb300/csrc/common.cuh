@@ -191,6 +191,8 @@ struct rnnls_ctx {
   size_t aux_bytes;
   unsigned int *counters;  // device: zero-initialised completion counters (reset by their users)
   size_t counters_len;
+  void *boost;       // device: the sketches, solutions and partial sums of repeated runs
+  size_t boost_bytes;
   // launch profiling (rnnls_profile_begin / rnnls_profile_end)
   int prof_on;
   int prof_cap;
@@ -223,6 +225,8 @@ enum kernel_id {
   K_COLABS,
   K_LH,
   K_RESIDUAL,
+  K_BOOST_RES,
+  K_BOOST_SEL,
   K_COUNT
 };
 const char *kernel_name(int kid);

@@ -115,6 +115,12 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count);
 // nrhs targets sharing one sketch SA: X (d x nrhs, leading dimension ldx), infos nrhs (nullable)
 int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, int64_t ldsb, int64_t r, int64_t d,
                 int64_t nrhs, double *X, int64_t ldx, rnnls_info *infos);
+// repeated runs (rnnls_solve_boosted); k <= kBoostMaxK, d <= kBoostMaxD
+constexpr int kBoostMaxK = 16;
+constexpr int kBoostMaxD = 256;
+int solve_boosted_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d,
+                      int64_t r, uint64_t seed, uint64_t instance0, int k, double *x, double *resid, int32_t *best,
+                      rnnls_info *info);
 int residual_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
                  const double *x, double *out);
 
