@@ -47,6 +47,46 @@ __device__ __forceinline__ const T *gram_col(const T *S, int64_t lds, const T *s
   return (g < d) ? S + (int64_t)g * lds : (g == d ? s : nullptr);
 }
 // column g of [S | s_0 .. s_{nb-1}] (targets with leading dimension ldt)
+// ---- packed f32x2 Dot2 step (two lanes per instruction) ----------------------
+__device__ __forceinline__ void unpack_f2(unsigned long long r, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// (s, c) += a * b on two lanes with the roundings of dot2::add_prod:
+// aa = (a, a), b = (b0, b1), nb = (-b0, -b1).  pn = -fl(a b) exactly, so
+// fma(a, b, pn) is TwoProduct's error, s - pn is s + p, and
+// -(pn + bb) is p - bb (negation commutes with round-to-nearest).
+__device__ __forceinline__ void dot2_add_prod_x2(unsigned long long &s, unsigned long long &c, unsigned long long aa,
+                                                 unsigned long long b, unsigned long long nb) {
+  const unsigned long long pn = f2_mul(aa, nb);
+  const unsigned long long e = f2_fma(aa, b, pn);
+  const unsigned long long s1 = f2_sub(s, pn);
+  const unsigned long long bb = f2_sub(s1, s);
+  const unsigned long long err = f2_sub(f2_sub(s, f2_sub(s1, bb)), f2_add(pn, bb));
+  s = s1;
+  c = f2_add(c, f2_add(err, e));
+}
+
 __device__ __forceinline__ const float *gram_col_nb(const float *S, int64_t lds, const float *s, int64_t ldt, int d,
                                                     int nb, int g) {
   return (g < d) ? S + (int64_t)g * lds : (g < d + nb ? s + (int64_t)(g - d) * ldt : nullptr);
@@ -132,8 +172,11 @@ __device__ __forceinline__ void gram_fused_block(int tile, int split, int splits
                                                              unsigned int *__restrict__ counters,
                                                              double *__restrict__ Qd, float *__restrict__ Qhi,
                                                              float *__restrict__ Qlo, double *__restrict__ colabs) {
-  __shared__ float Xi[kGT][kGT + 1];
-  __shared__ float Xj[kGT][kGT + 1];
+  // Xi as duplicated pairs (a, a); Xj and its negation as pairs of
+  // neighbouring columns (rows padded to an even length for 8-byte loads)
+  __shared__ float2 Xi2[kGT][kGT + 1];
+  __shared__ __align__(8) float Xj[kGT][kGT + 2];
+  __shared__ __align__(8) float Xn[kGT][kGT + 2];
   __shared__ unsigned int last_flag;
   (void)splits;
   int ti, tj;
@@ -145,7 +188,9 @@ __device__ __forceinline__ void gram_fused_block(int tile, int split, int splits
   const int64_t k1 = min(m, k0 + rows_per_split);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool diag = (ti == tj);
-  dot2 acc[2][2];
+  // Dot2 sums of the thread's 2 x 2 outputs, row a's two columns as one
+  // packed pair: s[a] = (s_a0, s_a1), c[a] likewise
+  unsigned long long sp[2] = {0ull, 0ull}, cp[2] = {0ull, 0ull};
   dot2 absacc[4];
   for (int64_t kb = k0; kb < k1; kb += kGT) {
 #pragma unroll
@@ -156,30 +201,35 @@ __device__ __forceinline__ void gram_fused_block(int tile, int split, int splits
       const float *ci = gram_col_nb(S, lds, s, ldt, d, nb, ti * kGT + cc);
       const float *cj = gram_col_nb(S, lds, s, ldt, d, nb, tj * kGT + cc);
       const float vi = (ci && k < k1) ? ci[k] : 0.0f;
-      Xi[kk][cc] = vi;
-      Xj[kk][cc] = (cj && k < k1) ? cj[k] : 0.0f;
+      const float vj = (cj && k < k1) ? cj[k] : 0.0f;
+      Xi2[kk][cc] = make_float2(vi, vi);
+      Xj[kk][cc] = vj;
+      Xn[kk][cc] = -vj;
       if (diag) absacc[q].add(fabsf(vi));
     }
     __syncthreads();
 #pragma unroll 8
     for (int kk = 0; kk < kGT; ++kk) {
-      const float a0 = Xi[kk][2 * ty], a1 = Xi[kk][2 * ty + 1];
-      const float b0 = Xj[kk][2 * tx], b1 = Xj[kk][2 * tx + 1];
-      acc[0][0].add_prod(a0, b0);
-      acc[0][1].add_prod(a0, b1);
-      acc[1][0].add_prod(a1, b0);
-      acc[1][1].add_prod(a1, b1);
+      const unsigned long long b = *reinterpret_cast<const unsigned long long *>(&Xj[kk][2 * tx]);
+      const unsigned long long nbv = *reinterpret_cast<const unsigned long long *>(&Xn[kk][2 * tx]);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const unsigned long long aa = *reinterpret_cast<const unsigned long long *>(&Xi2[kk][2 * ty + a]);
+        dot2_add_prod_x2(sp[a], cp[a], aa, b, nbv);
+      }
     }
     __syncthreads();
   }
   double *out = part + ((int64_t)split * ntiles + tile) * (kGT * kGT);
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const ff v = acc[a][c].value();
-      out[(2 * ty + a) * kGT + 2 * tx + c] = (double)v.hi + (double)v.lo;
-    }
+  for (int a = 0; a < 2; ++a) {
+    float s0, s1, c0, c1;
+    unpack_f2(sp[a], s0, s1);
+    unpack_f2(cp[a], c0, c1);
+    const ff v0 = fast_two_sum(s0, c0), v1 = fast_two_sum(s1, c1);
+    out[(2 * ty + a) * kGT + 2 * tx] = (double)v0.hi + (double)v0.lo;
+    out[(2 * ty + a) * kGT + 2 * tx + 1] = (double)v1.hi + (double)v1.lo;
+  }
   if (diag) {
     // column ti*32 + (warp + 8q): the 32 lanes of a warp hold 32 rows of it
 #pragma unroll
