@@ -192,22 +192,38 @@ __device__ __forceinline__ void gram_fused_block(int tile, int split, int splits
   // packed pair: s[a] = (s_a0, s_a1), c[a] likewise
   unsigned long long sp[2] = {0ull, 0ull}, cp[2] = {0ull, 0ull};
   dot2 absacc[4];
+  // this thread's four (row, column) positions of a stage; the next stage's
+  // values are loaded while the current one is multiplied
+  const float *ci[4], *cj[4];
+  int kq[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    kq[q] = e & 31;
+    ci[q] = gram_col_nb(S, lds, s, ldt, d, nb, ti * kGT + (e >> 5));
+    cj[q] = gram_col_nb(S, lds, s, ldt, d, nb, tj * kGT + (e >> 5));
+  }
+  float vi[4], vj[4];
+  auto fetch = [&](int64_t kb) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t k = kb + kq[q];
+      vi[q] = (ci[q] && k < k1) ? ci[q][k] : 0.0f;
+      vj[q] = (cj[q] && k < k1) ? cj[q][k] : 0.0f;
+    }
+  };
+  if (k0 < k1) fetch(k0);
   for (int64_t kb = k0; kb < k1; kb += kGT) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + 256 * q;
-      const int kk = e & 31, cc = e >> 5;
-      const int64_t k = kb + kk;
-      const float *ci = gram_col_nb(S, lds, s, ldt, d, nb, ti * kGT + cc);
-      const float *cj = gram_col_nb(S, lds, s, ldt, d, nb, tj * kGT + cc);
-      const float vi = (ci && k < k1) ? ci[k] : 0.0f;
-      const float vj = (cj && k < k1) ? cj[k] : 0.0f;
-      Xi2[kk][cc] = make_float2(vi, vi);
-      Xj[kk][cc] = vj;
-      Xn[kk][cc] = -vj;
-      if (diag) absacc[q].add(fabsf(vi));
+      const int kk = kq[q], cc = (threadIdx.x + 256 * q) >> 5;
+      Xi2[kk][cc] = make_float2(vi[q], vi[q]);
+      Xj[kk][cc] = vj[q];
+      Xn[kk][cc] = -vj[q];
+      if (diag) absacc[q].add(fabsf(vi[q]));
     }
     __syncthreads();
+    if (kb + kGT < k1) fetch(kb + kGT);
 #pragma unroll 8
     for (int kk = 0; kk < kGT; ++kk) {
       const unsigned long long b = *reinterpret_cast<const unsigned long long *>(&Xj[kk][2 * tx]);
