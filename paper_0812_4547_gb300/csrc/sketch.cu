@@ -1417,15 +1417,15 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
   first_p[(size_t)nb] = plan_tot;
   const int sms = (ctx->sketch_sms > 0) ? std::min(ctx->sketch_sms, num_sms) : num_sms;
   const int64_t B = std::max<int64_t>(1, std::min<int64_t>(sms, Ttot));
-  // Block ranges of equal estimated cost: a step costs about 104 + slots
-  // (the transform, then one word per plan row), plus the unit's write-out
-  // (slots) spread over its J steps.
+  // Block ranges of equal estimated cost, in units of about 22 ns: a step
+  // costs about 114 + slots (the transform, then the plan rows), plus the
+  // unit's write-out (about 6 slots) spread over its J steps.
   std::vector<int64_t> starts((size_t)B + 1);
   {
     std::vector<double> wt((size_t)nb), cum((size_t)nb + 1, 0.0);
     for (int t = 0; t < nb; ++t) {
       const srht_job &J = sj[(size_t)t];
-      wt[(size_t)t] = 104.0 + J.slots + (double)J.slots / (double)J.J;
+      wt[(size_t)t] = 114.0 + J.slots + 6.0 * (double)J.slots / (double)J.J;
       cum[(size_t)t + 1] = cum[(size_t)t] + wt[(size_t)t] * (double)(J.U * J.J);
     }
     int t = 0;

@@ -1331,7 +1331,7 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   int64_t tiles = 0;
   for (int64_t i = 0; i < count; ++i) {
     const int di = (int)probs[i].d;
-    plans[(size_t)i] = plan_gram(probs[i].r, di, std::max(1, ctx->num_sms / 8));
+    plans[(size_t)i] = plan_gram(probs[i].r, di, std::max(1, ctx->num_sms / 2));
     bytes += solve_ws_bytes(plans[(size_t)i], di, 0);
     smem = std::max(smem, lh_smem_for(ctx, di));
     tiles += plans[(size_t)i].ntiles;
