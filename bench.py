@@ -858,7 +858,8 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (term-document-like, generated on the device)",
         "config": wl,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None, "kernel": kname,
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": recorded_traffic(kname, wl["workload"]), "kernel": kname,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                      "algorithmic_bytes_per_step": sketch_bytes, "kernel_ms_per_step": kms,
                      "note": "the step's batched sketch launch, timed by CUDA events in a profiled (non-graph) step"},
