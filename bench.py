@@ -57,6 +57,8 @@ def parse():
                     help="end-to-end leg: streams the host-to-device copy of A is split over")
     ap.add_argument("--boost", type=int, default=0,
                     help="k > 0: time repeated RandomizedNNLS (k runs, best full residual kept) on workload 2 or 3")
+    ap.add_argument("--no-sketch-priority", dest="sketch_priority", action="store_false",
+                    help="pipelined mode: give the sketch stream the default priority")
     ap.add_argument("--solve-streams", type=int, default=2,
                     help="solve streams when pipelined (each solve runs in one block)")
     return ap.parse_args()
@@ -287,8 +289,15 @@ def main():
     # the sketch of step i+1 overlaps the solves of earlier steps: one sketch
     # stream, `nsolve` solve streams (each solve is one block on one SM),
     # sketch outputs in nsolve + 1 rotating buffers, ordered by events
-    s_sketch = torch.cuda.current_stream(dev)
+    # the sketch stream (the step's critical path) gets the higher stream
+    # priority, so that blocks of the concurrent solves yield SMs to its launches
     nsolve = max(1, args.solve_streams) if pipeline else 1
+    if pipeline and args.sketch_priority:
+        torch.cuda.synchronize(dev)
+        s_sketch = torch.cuda.Stream(dev, priority=min(torch.cuda.Stream.priority_range()))
+        torch.cuda.set_stream(s_sketch)  # torch's own work (copies, fills) goes there too
+    else:
+        s_sketch = torch.cuda.current_stream(dev)
     s_solves = [torch.cuda.Stream(dev) for _ in range(nsolve)] if pipeline else [s_sketch]
     ctx = P.Context(local, s_sketch)
     ctx_vs = [P.Context(local, st) for st in s_solves] if pipeline else [ctx]

@@ -39,8 +39,10 @@ namespace {
 
 constexpr int kStages = 3;                                   // stage buffers (steps in flight + 1)
 constexpr int kStageFloats = kWorkers * kM;                  // one step: four chunks
-// stage buffers plus slack to place them at a 16 KiB boundary
-constexpr size_t kSketchSmem = (size_t)kStages * kStageFloats * sizeof(float) + 16384;  // 208 KiB
+// stage buffers plus slack to place them at a 1 KiB boundary (the 128-byte
+// swizzle repeats every 1 KiB); kept small so that a Gram block (17 KiB) of a
+// concurrent solve fits on the same SM
+constexpr size_t kSketchSmem = (size_t)kStages * kStageFloats * sizeof(float) + 1024;  // 193 KiB
 constexpr uint32_t kSpinLimit = 1u << 22;                    // bounded wait on a bulk copy
 // From this many plan rows per thread on, a step's four chunks are first
 // transformed into one another (a 16384-point transform per step), so that
@@ -288,9 +290,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t nsteps = part_start(bid + 1, B, P) - s0;
   if (nsteps <= 0) return;
   const int64_t D1 = (int64_t)d + nb;
-  // stage buffers at a 16 KiB boundary: chunk slots are then addressed by OR
+  // stage buffers at a 1 KiB boundary (the tensor copies' swizzle pattern)
   const uint32_t raw_u32 = smem_u32(dyn_smem);
-  const uint32_t stage_u32 = (raw_u32 + 16383u) & ~16383u;
+  const uint32_t stage_u32 = (raw_u32 + 1023u) & ~1023u;
   float *stage = dyn_smem + (stage_u32 - raw_u32) / 4;
   const int64_t nrow32 = n_raw >> 5;  // whole 32-row lines of a column
   const bool full = SLOTS > 0 ? (SLOTS >= kFullMinSlots) : (slots >= kFullMinSlots);
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int e = 0; e < SLOTS; ++e) {
           const uint32_t p = pk_r[e];
           float z0, z1, z2, z3;
-          lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+          lds_x4(step_u32 + (p & 0x3ffcu), z0, z1, z2, z3);
           const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
           const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
           const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
@@ -516,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int e = 0; e < 8; ++e) {
             const uint32_t p = pk[e];
             float z0, z1, z2, z3;
-            lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+            lds_x4(step_u32 + (p & 0x3ffcu), z0, z1, z2, z3);
             const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
             const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
             const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
@@ -765,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t nsteps = starts[bid + 1] - s0;
   if (nsteps <= 0) return;
   const uint32_t raw_u32 = smem_u32(dyn_smem);
-  const uint32_t stage_u32 = (raw_u32 + 16383u) & ~16383u;
+  const uint32_t stage_u32 = (raw_u32 + 1023u) & ~1023u;
   float *stage = dyn_smem + (stage_u32 - raw_u32) / 4;
 
   if (tid == 0) {
@@ -956,7 +958,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int e = 0; e < 8; ++e) {
             const uint32_t p = pk[e];
             float z0, z1, z2, z3;
-            lds_x4(step_u32 | (p & 0x3ffcu), z0, z1, z2, z3);
+            lds_x4(step_u32 + (p & 0x3ffcu), z0, z1, z2, z3);
             const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
             const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
             const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));

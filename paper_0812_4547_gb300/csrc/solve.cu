@@ -1184,6 +1184,18 @@ __global__ void sum_partials_kernel(const double *__restrict__ partial, int nb, 
   }
 }
 
+// The FP32 Gram kernels ask for the largest shared-memory carveout, so that
+// their blocks can run on SMs that also hold a sketch block (about 200 KiB).
+void gram_carveout_once() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(gram_fused_f32_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(gram_batched_f32_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
+  done = true;
+}
+
 struct gram_plan {
   int T, ntiles, splits;
   int64_t rows_per_split;
@@ -1273,6 +1285,7 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
     st = ensure_counters(ctx, (size_t)g.ntiles, &counters);
     if (st) return st;
     prof_scope ps(ctx, K_GRAM);
+    gram_carveout_once();
     gram_fused_f32_kernel<<<grid, 256, 0, s>>>((const float *)SA, ldsa, (const float *)Sb, r, 1, r, (int)d, g.T,
                                                g.rows_per_split, w.part, w.part_abs, counters, w.Qd, w.Qhi, w.Qlo,
                                                w.colabs);
@@ -1400,6 +1413,7 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
                                           align_up((size_t)(count + 1) * sizeof(int64_t), 256));
   {
     prof_scope ps(ctx, K_GRAM);
+    gram_carveout_once();
     gram_batched_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_gj, d_first, (int)count);
   }
   if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
@@ -1432,6 +1446,7 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
   {
     prof_scope ps(ctx, K_GRAM);
     dim3 grid((unsigned)g.ntiles, (unsigned)g.splits);
+    gram_carveout_once();
     gram_fused_f32_kernel<<<grid, 256, 0, s>>>(SA, ldsa, SB, ldsb, (int)nrhs, r, (int)d, g.T, g.rows_per_split, w.part,
                                                w.part_abs, counters, w.Qd, w.Qhi, w.Qlo, w.colabs);
   }
