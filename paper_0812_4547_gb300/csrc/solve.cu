@@ -303,6 +303,10 @@ __device__ __forceinline__ void gram_fused_block(int tile, int split, int splits
   if (threadIdx.x == 0) counters[tile] = 0u;
 }
 
+// SHARE = 1: the one-problem launch, whose blocks may share SMs with a
+// concurrent sketch (it gets its own carveout attribute); SHARE = 0: the
+// multi-target launch.
+template <int SHARE>
 __global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__restrict__ S, int64_t lds,
                                                              const float *__restrict__ s, int64_t ldt, int nb,
                                                              int64_t m, int d, int T, int64_t rows_per_split,
@@ -1184,14 +1188,16 @@ __global__ void sum_partials_kernel(const double *__restrict__ partial, int nb, 
   }
 }
 
-// The FP32 Gram kernels ask for the largest shared-memory carveout, so that
-// their blocks can run on SMs that also hold a sketch block (about 200 KiB).
+// The one-problem FP32 Gram asks for the largest shared-memory carveout, so
+// that its blocks can run on SMs that also hold a sketch block (about 200 KiB)
+// when solves overlap the next sketch.  (Not the multi-target and batched
+// Grams: a following Lawson-Hanson launch that reads Q from global memory
+// needs the L1 share; a function's carveout is per function, hence the
+// separate instantiation.)
 void gram_carveout_once() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(gram_fused_f32_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       (int)cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(gram_batched_f32_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+  cudaFuncSetAttribute(gram_fused_f32_kernel<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
   done = true;
 }
@@ -1285,10 +1291,12 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
     st = ensure_counters(ctx, (size_t)g.ntiles, &counters);
     if (st) return st;
     prof_scope ps(ctx, K_GRAM);
-    gram_carveout_once();
-    gram_fused_f32_kernel<<<grid, 256, 0, s>>>((const float *)SA, ldsa, (const float *)Sb, r, 1, r, (int)d, g.T,
-                                               g.rows_per_split, w.part, w.part_abs, counters, w.Qd, w.Qhi, w.Qlo,
-                                               w.colabs);
+    // Q held in the Lawson-Hanson block's shared memory: the following solve
+    // does not lean on L1, so the Gram may take the shared-SM carveout
+    auto kern = fits ? gram_fused_f32_kernel<1> : gram_fused_f32_kernel<0>;
+    if (fits) gram_carveout_once();
+    kern<<<grid, 256, 0, s>>>((const float *)SA, ldsa, (const float *)Sb, r, 1, r, (int)d, g.T, g.rows_per_split,
+                              w.part, w.part_abs, counters, w.Qd, w.Qhi, w.Qlo, w.colabs);
   } else {
     {
       prof_scope ps(ctx, K_GRAM);
@@ -1413,7 +1421,6 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
                                           align_up((size_t)(count + 1) * sizeof(int64_t), 256));
   {
     prof_scope ps(ctx, K_GRAM);
-    gram_carveout_once();
     gram_batched_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_gj, d_first, (int)count);
   }
   if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
@@ -1446,8 +1453,7 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
   {
     prof_scope ps(ctx, K_GRAM);
     dim3 grid((unsigned)g.ntiles, (unsigned)g.splits);
-    gram_carveout_once();
-    gram_fused_f32_kernel<<<grid, 256, 0, s>>>(SA, ldsa, SB, ldsb, (int)nrhs, r, (int)d, g.T, g.rows_per_split, w.part,
+    gram_fused_f32_kernel<0><<<grid, 256, 0, s>>>(SA, ldsa, SB, ldsb, (int)nrhs, r, (int)d, g.T, g.rows_per_split, w.part,
                                                w.part_abs, counters, w.Qd, w.Qhi, w.Qlo, w.colabs);
   }
   if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
