@@ -59,7 +59,7 @@ def parse():
                     help="k > 0: time repeated RandomizedNNLS (k runs, best full residual kept) on workload 2 or 3")
     ap.add_argument("--no-sketch-priority", dest="sketch_priority", action="store_false",
                     help="pipelined mode: give the sketch stream the default priority")
-    ap.add_argument("--solve-streams", type=int, default=2,
+    ap.add_argument("--solve-streams", type=int, default=3,
                     help="solve streams when pipelined (each solve runs in one block)")
     return ap.parse_args()
 
