@@ -326,6 +326,9 @@ __global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(const int32_t 
                                                                   int64_t rows_per_group, int kgroups, uint64_t seed,
                                                                   uint64_t inst, uint64_t *__restrict__ sign_table,
                                                                   int64_t sign_words, int64_t sign_block0) {
+  // the sketch launch that follows may be scheduled now (it waits for this
+  // launch's completion before it reads the plan)
+  asm volatile("griddepcontrol.launch_dependents;");
   plan_block((int)blockIdx.x, idx, r, d_count, plan_pk, plan_k, slots, rows_per_group, kgroups, seed, inst,
              sign_table, sign_words, sign_block0);
 }

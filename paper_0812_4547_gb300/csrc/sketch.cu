@@ -328,10 +328,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   step_cursor ic;
   ic.init(s0, P, D1);
   int iq = 0;
-  auto issue = [&]() {
+  auto issue = [&](bool with_signs) {
     const uint32_t bar = smem_u32(&mbar[iq]);
     mbar_arrive_expect_tx(bar, (uint32_t)(kWorkers * kM * sizeof(float)) + (sign_table ? 2048u : 0u));
-    if (sign_table) bulk_g2s(smem_u32(&sgn[iq][0][0]), sign_table + 4 * ic.j * (kM / 64), 2048u, bar);
+    if (sign_table && with_signs) bulk_g2s(smem_u32(&sgn[iq][0][0]), sign_table + 4 * ic.j * (kM / 64), 2048u, bar);
     const CUtensorMap *map = (ic.col < d) ? &tmA : &tmB;
     const int z = (ic.col < d) ? ic.col : ic.col - d;
 #pragma unroll
@@ -359,9 +359,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   };
 
+  // The first two steps' data copies need nothing from the plan launch that
+  // precedes this one in the stream: launched as its programmatic dependent,
+  // this block issues them while that launch finishes, then waits for it
+  // (griddepcontrol.wait: the plan, sign table and rows are complete and
+  // visible) before the sign words and plan entries are read.
+  int64_t j_first[2] = {-1, -1};
   if (vec && tid == 0) {
-    issue();
-    if (nsteps > 1) issue();
+    j_first[0] = ic.j;
+    issue(false);
+    if (nsteps > 1) {
+      j_first[1] = ic.j;
+      issue(false);
+    }
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (vec && tid == 0 && sign_table) {
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+      if (j_first[f] >= 0)
+        bulk_g2s(smem_u32(&sgn[f][0][0]), sign_table + 4 * j_first[f] * (kM / 64), 2048u, smem_u32(&mbar[f]));
   }
   step_cursor cur;
   cur.init(s0, P, D1);
@@ -397,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (vec) {
       if (tid == 0 && ls + 2 < nsteps) {
         fence_proxy_async();
-        issue();
+        issue(true);
       }
       const uint32_t bar = smem_u32(&mbar[q]);
       const uint32_t limit = *(volatile int *)&stalled ? 64u : kSpinLimit;
@@ -1275,10 +1292,23 @@ int launch_srht(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, co
               : plan.slots == 32 ? sketch_srht_f32<32>
               : plan.slots == 40 ? sketch_srht_f32<40>
                                  : sketch_srht_f32<0>;
-  kern<<<(unsigned)blocks, kThreads, kSketchSmem, s>>>(
-      tmA, tmB, a.A, a.lda, a.b, a.ldb, a.n_raw, a.d, a.nb, a.chunk0 / 4, P, vec, a.seed, a.inst, signs, plan.pk, plan.k,
-      plan.slots, plan.rows_per_group, part, a.scale, a.SA, a.ldsa, a.Sb, a.ldsb, counters);
-  return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
+  // programmatic dependent of the plan launch before it (the kernel waits for
+  // that launch before it reads anything the launch writes)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSketchSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e =
+      cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a.A, a.lda, a.b, a.ldb, a.n_raw, a.d, a.nb, a.chunk0 / 4, P, vec, a.seed,
+                         a.inst, signs, plan.pk, plan.k, plan.slots, plan.rows_per_group, part, a.scale, a.SA, a.ldsa,
+                         a.Sb, a.ldsb, counters);
+  return (e == cudaSuccess && cudaGetLastError() == cudaSuccess) ? RNNLS_OK : RNNLS_ECUDA;
 }
 
 // Launch geometry of the large-n sketch for `sms` usable SMs.
