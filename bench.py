@@ -59,6 +59,8 @@ def parse():
                     help="k > 0: time repeated RandomizedNNLS (k runs, best full residual kept) on workload 2 or 3")
     ap.add_argument("--no-sketch-priority", dest="sketch_priority", action="store_false",
                     help="pipelined mode: give the sketch stream the default priority")
+    ap.add_argument("--sketch-streams", type=int, default=1,
+                    help="pipelined mode: steps alternate over this many sketch streams")
     ap.add_argument("--solve-streams", type=int, default=3,
                     help="solve streams when pipelined (each solve runs in one block)")
     return ap.parse_args()
@@ -314,10 +316,17 @@ def main():
     s_solves = [torch.cuda.Stream(dev) for _ in range(nsolve)] if pipeline else [s_sketch]
     ctx = P.Context(local, s_sketch)
     ctx_vs = [P.Context(local, st) for st in s_solves] if pipeline else [ctx]
+    # --sketch-streams k: steps alternate over k sketch streams (one context
+    # each), so that the rows and plan of step i+1 start on the SMs the sketch
+    # of step i releases first
+    nsk = max(1, args.sketch_streams) if pipeline else 1
+    s_sks = [s_sketch] + [torch.cuda.Stream(dev, priority=s_sketch.priority) for _ in range(nsk - 1)]
+    ctx_sks = [ctx] + [P.Context(local, st) for st in s_sks[1:]]
     if pipeline:
         # one SM per concurrent Lawson-Hanson solve stays free of sketch blocks
-        ctx.set_sketch_sms(torch.cuda.get_device_properties(local).multi_processor_count - nsolve)
-    nbuf = nsolve + 1 if pipeline else 1
+        for cs in ctx_sks:
+            cs.set_sketch_sms(torch.cuda.get_device_properties(local).multi_processor_count - nsolve)
+    nbuf = nsolve + nsk if pipeline else 1
     SAs = [torch.empty((p.d, r), dtype=tdt, device=dev).t() for _ in range(nbuf)]
     Sbs = [torch.empty(r, dtype=tdt, device=dev) for _ in range(nbuf)]
     idxs = [torch.empty(r, dtype=torch.int32, device=dev) for _ in range(nbuf)]
@@ -333,14 +342,15 @@ def main():
         A_ = A if A_ is None else A_
         b_ = b if b_ is None else b_
         k = i % nbuf
+        st, cs = s_sks[i % nsk], ctx_sks[i % nsk]
         if pipeline and used[k]:
-            s_sketch.wait_event(solved[k])  # the buffer's previous solve has read it
-        ctx.sketch(A_, b_, r, seed=i, instance=rank, SA=SAs[k], Sb=Sbs[k], idx=idxs[k], want_count=False)
+            st.wait_event(solved[k])  # the buffer's previous solve has read it
+        cs.sketch(A_, b_, r, seed=i, instance=rank, SA=SAs[k], Sb=Sbs[k], idx=idxs[k], want_count=False)
         if after_sketch is not None:
-            after_sketch.record(s_sketch)
+            after_sketch.record(st)
         cv = ctx_vs[i % nsolve]
         if pipeline:
-            sketched[k].record(s_sketch)
+            sketched[k].record(st)
             s_solves[i % nsolve].wait_event(sketched[k])
         cv.solve(SAs[k], Sbs[k], r=r, x=xs[k], info=infos[k])
         if x_out is not None:
@@ -355,6 +365,10 @@ def main():
             for k in range(nbuf):
                 if used[k]:
                     s_sketch.wait_event(solved[k])
+            for st in s_sks[1:]:
+                e = torch.cuda.Event()
+                e.record(st)
+                s_sketch.wait_event(e)
 
     stream = s_sketch
     for i in range(args.warmup):
@@ -366,7 +380,8 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.15)
-    B.rnnls_profile_begin(ctx.handle, 16 * args.steps + 64)
+    for cs in ctx_sks:
+        B.rnnls_profile_begin(cs.handle, 16 * args.steps + 64)
     if pipeline:
         for cv in ctx_vs:
             B.rnnls_profile_begin(cv.handle, 16 * args.steps + 64)
@@ -375,18 +390,19 @@ def main():
     torch.cuda.synchronize()
     w0 = time.time()
     ev0.record(stream)
+    for st in s_sks[1:]:
+        st.wait_event(ev0)
     for i in range(args.steps):
         step(args.warmup + i)
     drain()
     ev1.record(stream)
     torch.cuda.synchronize()
     w1 = time.time()
-    prof = B.rnnls_profile_end(ctx.handle)
-    if pipeline:
-        for cv in ctx_vs:
-            for k, v in B.rnnls_profile_end(cv.handle).items():
-                a = prof.get(k, (0, 0.0))
-                prof[k] = (a[0] + v[0], a[1] + v[1])
+    prof = {}
+    for cx in ctx_sks + (ctx_vs if pipeline else []):
+        for k, v in B.rnnls_profile_end(cx.handle).items():
+            a = prof.get(k, (0, 0.0))
+            prof[k] = (a[0] + v[0], a[1] + v[1])
     clk = clocks.stop(w0, w1)
     ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     if ws > 1:
@@ -427,7 +443,7 @@ def main():
                         if c == 0:
                             bd[k].copy_(b_host, non_blocking=True)
                     copied[k][c].record(cs)
-                    s_sketch.wait_event(copied[k][c])
+                    s_sks[i % nsk].wait_event(copied[k][c])
                 step(i, Ad[k], bd[k], after_sketch=freed[k], x_out=x_hosts[i % nbuf])
             drain()
             torch.cuda.synchronize()
@@ -480,7 +496,7 @@ def main():
     sketch_ms = sum(prof.get(k, (0, 0.0))[1] for k in ("sample_rows", "build_plan", "sketch_srht_f32",
                                                         "reduce_partials", "sketch_small", "sketch_f64"))
     wl = workload_desc(cfg, p)
-    wl["pipeline"] = (f"sketches on one stream overlap solves on {nsolve} streams ({nbuf} sketch buffers)"
+    wl["pipeline"] = (f"sketches on {nsk} stream(s) overlap solves on {nsolve} streams ({nbuf} sketch buffers)"
                       if pipeline else "sketch and solve back to back on one stream")
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -506,6 +522,8 @@ def main():
     if pipeline:
         for cv in ctx_vs:
             cv.close()
+    for cs in ctx_sks[1:]:
+        cs.close()
     ctx.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
