@@ -59,6 +59,10 @@ def parse():
                     help="k > 0: time repeated RandomizedNNLS (k runs, best full residual kept) on workload 2 or 3")
     ap.add_argument("--no-sketch-priority", dest="sketch_priority", action="store_false",
                     help="pipelined mode: give the sketch stream the default priority")
+    ap.add_argument("--solve-after-plan", type=int, default=None, choices=[0, 1],
+                    help="pipelined mode: 1 enqueues each solve after the next step's plan launch, 0 right after "
+                         "its own sketch (default: 1 for workload 3, whose Grams and solves otherwise delay the "
+                         "plan, 0 elsewhere)")
     ap.add_argument("--sketch-streams", type=int, default=1,
                     help="pipelined mode: steps alternate over this many sketch streams")
     ap.add_argument("--solve-streams", type=int, default=3,
@@ -338,6 +342,33 @@ def main():
     SA, Sb, idx, x, info = SAs[0], Sbs[0], idxs[0], xs[0], infos[0]
     x_host = torch.empty(p.d, dtype=torch.float64).pin_memory()
 
+    # --solve-after-plan (pipelined): the solve of step i is enqueued after the
+    # sketch call of step i+1 and waits for that call's plan launch, so that
+    # its Gram does not hold the SMs the plan needs; it then runs beside the
+    # transform (a Gram block fits next to a sketch block)
+    after_plan = pipeline and bool(args.solve_after_plan if args.solve_after_plan is not None else cfg == 3)
+    plan_ev = None
+    if after_plan:
+        plan_ev = torch.cuda.Event()
+        plan_ev.record(s_sketch)  # creates the CUDA event the contexts record
+        for cs in ctx_sks:
+            cs.set_plan_event(plan_ev)
+    pending = []  # (step, buffer, x_out) whose solve is not enqueued yet
+
+    def enqueue_solve(i: int, k: int, x_out, wait_plan: bool):
+        cv, ss = ctx_vs[i % nsolve], s_solves[i % nsolve]
+        if pipeline:
+            ss.wait_event(sketched[k])
+            if wait_plan:
+                ss.wait_event(plan_ev)
+        cv.solve(SAs[k], Sbs[k], r=r, x=xs[k], info=infos[k])
+        if x_out is not None:
+            with torch.cuda.stream(ss):
+                x_out.copy_(xs[k], non_blocking=True)
+        if pipeline:
+            solved[k].record(ss)
+            used[k] = True
+
     def step(i: int, A_=None, b_=None, after_sketch=None, x_out=None):
         A_ = A if A_ is None else A_
         b_ = b if b_ is None else b_
@@ -348,19 +379,18 @@ def main():
         cs.sketch(A_, b_, r, seed=i, instance=rank, SA=SAs[k], Sb=Sbs[k], idx=idxs[k], want_count=False)
         if after_sketch is not None:
             after_sketch.record(st)
-        cv = ctx_vs[i % nsolve]
         if pipeline:
             sketched[k].record(st)
-            s_solves[i % nsolve].wait_event(sketched[k])
-        cv.solve(SAs[k], Sbs[k], r=r, x=xs[k], info=infos[k])
-        if x_out is not None:
-            with torch.cuda.stream(s_solves[i % nsolve]):
-                x_out.copy_(xs[k], non_blocking=True)
-        if pipeline:
-            solved[k].record(s_solves[i % nsolve])
-            used[k] = True
+        if after_plan:
+            if pending:
+                enqueue_solve(*pending.pop(), wait_plan=True)
+            pending.append((i, k, x_out))
+        else:
+            enqueue_solve(i, k, x_out, wait_plan=False)
 
     def drain():
+        if pending:
+            enqueue_solve(*pending.pop(), wait_plan=False)
         if pipeline:
             for k in range(nbuf):
                 if used[k]:

@@ -108,6 +108,15 @@ int rnnls_set_stream(rnnls_ctx *ctx, void *stream);
  * Errors: EINVAL (ctx null or sms < 0). */
 int rnnls_set_sketch_sms(rnnls_ctx *ctx, int sms);
 
+/* Scheduling aid (not part of the method): `event` (a cudaEvent_t, borrowed;
+ * NULL to stop) is recorded on the context stream by every FP32 sketch call
+ * once its row sampling and plan launches are enqueued, before the transform
+ * launch (at the start of the call for n <= 8192, which has no plan).  Work
+ * on other streams that waits on it starts after the plan, so it does not
+ * delay the plan launch, and runs beside the transform.  Errors: EINVAL
+ * (ctx null). */
+int rnnls_set_plan_event(rnnls_ctx *ctx, void *event);
+
 /* Sketch of Alg. 1 steps 1-4 for FP32 data:
  *   SA[k, j] = s * sum_i H_n[idx[k], i] D_ii A[i, j]   (k < r_out, j < d)
  *   Sb[k]    = s * sum_i H_n[idx[k], i] D_ii b[i]

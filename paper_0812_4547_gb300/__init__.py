@@ -87,6 +87,10 @@ class Context:
         """Cap the SMs the large-n sketch occupies (0: all), leaving the rest to other streams."""
         B.rnnls_set_sketch_sms(self.handle, sms)
 
+    def set_plan_event(self, event) -> None:
+        """Record `event` (a torch.cuda.Event, or None) after each sketch's plan launch."""
+        B.rnnls_set_plan_event(self.handle, 0 if event is None else event.cuda_event)
+
     # -- sketch -------------------------------------------------------------------------
     def sketch(self, A, b, r: int, seed: int, instance: int = 0, mode: int = RNNLS_SAMPLE_IID, SA=None, Sb=None,
                idx=None, cap: int | None = None, want_count: bool = True):

@@ -31,7 +31,7 @@ EXPORTS = (
     "rnnls_create", "rnnls_destroy", "rnnls_set_stream", "rnnls_sketch", "rnnls_sketch_f64", "rnnls_solve",
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
-    "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted",
+    "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted", "rnnls_set_plan_event",
 )
 
 
@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_destroy.argtypes = [P]
         L.rnnls_set_stream.argtypes = [P, P]
         L.rnnls_set_sketch_sms.argtypes = [P, I32]
+        L.rnnls_set_plan_event.argtypes = [P, P]
         sk = [P, P, I64, P, I64, I64, I64, U64, U64, U32, P, I64, P, P, I64, ctypes.POINTER(I64)]
         L.rnnls_sketch.argtypes = sk
         L.rnnls_sketch_f64.argtypes = sk
@@ -162,6 +163,10 @@ def rnnls_set_stream(ctx: int, stream: int) -> None:
 
 def rnnls_set_sketch_sms(ctx: int, sms: int) -> None:
     check(lib().rnnls_set_sketch_sms(ctypes.c_void_p(ctx), sms), "rnnls_set_sketch_sms")
+
+
+def rnnls_set_plan_event(ctx: int, event: int) -> None:
+    check(lib().rnnls_set_plan_event(ctypes.c_void_p(ctx), ctypes.c_void_p(event)), "rnnls_set_plan_event")
 
 
 def _sketch(fn, name, ctx, A, lda, b, n_raw, d, r, seed, instance, flags, SA, ldsa, Sb, idx, cap, want_count):

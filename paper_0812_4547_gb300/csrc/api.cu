@@ -253,6 +253,12 @@ int rnnls_set_stream(rnnls_ctx *ctx, void *stream) {
   return RNNLS_OK;
 }
 
+int rnnls_set_plan_event(rnnls_ctx *ctx, void *event) {
+  if (!ctx) return RNNLS_EINVAL;
+  ctx->plan_event = (cudaEvent_t)event;
+  return RNNLS_OK;
+}
+
 int rnnls_set_sketch_sms(rnnls_ctx *ctx, int sms) {
   if (!ctx || sms < 0) return RNNLS_EINVAL;
   ctx->sketch_sms = sms;

@@ -193,6 +193,7 @@ struct rnnls_ctx {
   size_t counters_len;
   void *boost;       // device: the sketches, solutions and partial sums of repeated runs
   size_t boost_bytes;
+  cudaEvent_t plan_event;  // borrowed, nullable: recorded after each FP32 sketch's plan launch
   // launch profiling (rnnls_profile_begin / rnnls_profile_end)
   int prof_on;
   int prof_cap;

@@ -1363,6 +1363,7 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
   cudaStream_t s = ctx->stream;
   if (n <= 8192) {
     const size_t smem = (size_t)n * sizeof(float) + (size_t)std::max<int64_t>(n / 64, 4) * sizeof(uint64_t);
+    if (ctx->plan_event) RNNLS_CUDA_TRY(cudaEventRecord(ctx->plan_event, s));  // no plan at this size
     prof_scope ps(ctx, K_SKETCH_SMALL);
     sketch_small<float><<<(unsigned)(a.d + a.nb), 256, smem, s>>>(a.A, a.lda, a.b, a.ldb, a.n_raw, a.d, a.L, a.seed,
                                                                   a.inst, a.idx, a.r, a.d_count, a.scale, a.SA,
@@ -1390,6 +1391,7 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
       st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, signs, g.sign_words, 16 * a.chunk0, a.seed, a.inst);
   }
   if (st) return st;
+  if (ctx->plan_event) RNNLS_CUDA_TRY(cudaEventRecord(ctx->plan_event, s));
   prof_scope ps_main(ctx, K_SKETCH);
   return launch_srht(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
 }
