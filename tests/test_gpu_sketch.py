@@ -193,3 +193,35 @@ def test_sketch_sm_cap(orc, sms):
             run_case(c, orc, rng.standard_normal((n, d)), rng.standard_normal(n), r, seed=sms, inst=4, mode=0)
     finally:
         c.close()
+
+
+def test_plan_event_is_recorded_and_changes_nothing():
+    """rnnls_set_plan_event: the event is recorded by every FP32 sketch call
+    (with and without a plan) and the sketch is the one without it."""
+    import torch
+
+    import paper_0812_4547_gb300 as P
+
+    c = P.Context(0)
+    try:
+        rng = np.random.default_rng(3)
+        for n, d, r in [((1 << 17) + 9, 5, 700), (3000, 4, 200)]:
+            A = dev_colmajor(rng.standard_normal((n, d)), np.float32)
+            b = dev_vec(rng.standard_normal(n), np.float32)
+            SA0, Sb0, idx0, _ = c.sketch(A, b, r, seed=5, instance=1)
+            ev = torch.cuda.Event()
+            ev.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            c.set_plan_event(ev)
+            side = torch.cuda.Stream()
+            side.wait_event(ev)  # a stream that follows the plan launch
+            SA1, Sb1, idx1, _ = c.sketch(A, b, r, seed=5, instance=1)
+            side.wait_event(ev)
+            c.set_plan_event(None)
+            torch.cuda.synchronize()
+            assert ev.query()
+            assert np.array_equal(host(idx0), host(idx1))
+            assert np.array_equal(host(SA0), host(SA1))
+            assert np.array_equal(host(Sb0), host(Sb1))
+    finally:
+        c.close()
