@@ -1145,7 +1145,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
   }
 }
 
-__global__ void __launch_bounds__(kLHThreads, 1) lh_kernel(const lh_job *__restrict__ jobs, int max_outer_mul,
+__global__ void __launch_bounds__(kLHThreads, 2) lh_kernel(const lh_job *__restrict__ jobs, int max_outer_mul,
                                                            int max_inner_mul) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ lh_shared sh;
@@ -1433,7 +1433,6 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
   // then one Lawson-Hanson block per target, all reading the same Q
   const int64_t D1 = d + nrhs;
   const gram_plan g = plan_gram(r, (int)(D1 - 1), ctx->num_sms);
-  const bool fits = lh_q_fits(ctx, (int)d);
   const size_t bytes = solve_ws_bytes(g, (int)(D1 - 1), nrhs);
   int st = ensure_workspace(ctx, bytes);
   if (st) return st;
@@ -1470,7 +1469,7 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
     jb.d = (int)d;
     jb.x = X + t * ldx;
     jb.info = infos ? infos + t : nullptr;
-    jb.q_smem = fits ? 1 : 0;
+    jb.q_smem = 0;  // every target reads the shared Q from global memory (L1/L2), so two blocks fit per SM
   }
   const size_t jbytes = (size_t)nrhs * sizeof(lh_job);
   st = ensure_pinned(ctx, jbytes);
@@ -1478,7 +1477,7 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
   memcpy(ctx->pinned, jobs.data(), jbytes);
   RNNLS_CUDA_TRY(cudaMemcpyAsync(d_jobs, ctx->pinned, jbytes, cudaMemcpyHostToDevice, s));
   RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
-  return lh_launch(ctx, d_jobs, nrhs, lh_smem_for(ctx, (int)d));
+  return lh_launch(ctx, d_jobs, nrhs, lh_make_layout((int)d, false).bytes);
 }
 
 int residual_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
