@@ -225,3 +225,40 @@ def test_plan_event_is_recorded_and_changes_nothing():
             assert np.array_equal(host(Sb0), host(Sb1))
     finally:
         c.close()
+
+
+def test_largest_supported_n(ctx, orc):
+    """n_raw = 2^28, the largest row count the library takes (one column of A
+    and b, 1 GiB each): rows bit-exact, sampled entries against the
+    definition; one row more is refused before anything runs."""
+    import torch
+
+    import paper_0812_4547_gb300 as P
+    from paper_0812_4547_gb300 import _binding as B
+
+    n, r = 1 << 28, 2048
+    rng = np.random.default_rng(28)
+    a_h = rng.random(n, dtype=np.float32)
+    b_h = rng.random(n, dtype=np.float32) - 0.5
+    A = torch.from_numpy(a_h).cuda().reshape(1, n).t()
+    b = torch.from_numpy(b_h).cuda()
+    SA, Sb, idx, rows = ctx.sketch(A, b, r, seed=3, instance=2)
+    idx_o = orc.sample(3, 2, n, r)
+    assert np.array_equal(host(idx), idx_o)
+    SAh, Sbh = host(SA), host(Sb)
+    sc = 1 / math.sqrt(r)
+    for col_h, got_col in ((a_h, SAh[:, 0]), (b_h, Sbh)):
+        col = col_h.astype(np.float64)
+        tol = 1e-5 * sc * np.linalg.norm(col)
+        for k in (0, 977, r - 1):
+            want = orc.sketch_entry(col, 3, 2, int(idx_o[k]), sc)
+            assert abs(got_col[k] - want) <= tol
+        del col
+    del A, b, SA, Sb
+    torch.cuda.empty_cache()
+    small = torch.zeros(16, device="cuda")
+    out = torch.zeros(16, device="cuda")
+    with pytest.raises(P.RNNLSError) as e:
+        B.rnnls_sketch(ctx.handle, small.data_ptr(), n + 1, small.data_ptr(), n + 1, 1, 8, 0, 0, 0, out.data_ptr(), 8,
+                       out.data_ptr(), 0, 8)
+    assert e.value.status == B.RNNLS_EUNSUPPORTED
