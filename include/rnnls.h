@@ -212,7 +212,9 @@ int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double 
  * caps 3d additions and 30d interpolation solves (EMAXITER).
  * Q = SA'SA and q = SA'Sb are formed with products exact and sums
  * compensated (about 2^-44 relative), the Lawson-Hanson decisions use
- * passive solves refined to that accuracy.  Requires 1 <= d <= 256,
+ * passive solves refined to that accuracy.  Requires 1 <= d <= 1024 (for d
+ * above about 230 the passive-block inverse is kept in the context's
+ * workspace instead of shared memory),
  * r >= 1.  A return of RNNLS_OK means the work was enqueued; the solve's
  * own outcome is info->status. */
 int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
@@ -228,15 +230,16 @@ int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double
  * same rules and tolerance; the Gram of SA is formed once for all targets.
  * SA: r x d (ldsa >= r), SB: r x nrhs (ldsb >= r), FP32, device.  X: device
  * FP64 d x nrhs, column-major, ldx >= d.  infos: device, nrhs entries
- * (nullable).  Requires 1 <= d <= 256 (EUNSUPPORTED otherwise).  Errors:
+ * (nullable).  Requires 1 <= d <= 1024 (EUNSUPPORTED otherwise).  Errors:
  * EINVAL, EUNSUPPORTED, ENOMEM, ECUDA; each target's own outcome is
  * infos[t].status. */
 int rnnls_solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, int64_t ldsb, int64_t r,
                       int64_t d, int64_t nrhs, double *X, int64_t ldx, rnnls_info *infos);
 
 /* Many independent small NNLS problems in one launch sequence (one
- * Lawson-Hanson block per problem, uneven d and r allowed).  `probs` is a
- * HOST array of `count` descriptors whose pointers are device pointers. */
+ * Lawson-Hanson block per problem, uneven d and r allowed, each d <= 1024).
+ * `probs` is a HOST array of `count` descriptors whose pointers are device
+ * pointers. */
 int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count, uint32_t flags);
 
 /* Repeated RandomizedNNLS (the footnote to Theorem 1 in Sec. 1: a few

@@ -89,6 +89,9 @@ using namespace rnnls;
 namespace {
 
 constexpr int64_t kMaxRows = (int64_t)1 << 28;
+// Largest d of the small NNLS (beyond about 230 the passive-block inverse
+// leaves shared memory for the workspace)
+constexpr int64_t kMaxSolveD = 1024;
 
 // Device layout of the auxiliary buffer: [count (int64) | sampled rows (int32)].
 struct aux_view {
@@ -477,7 +480,7 @@ int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double 
 int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
                 rnnls_info *info) {
   if (!ctx || !SA || !Sb || !x || r < 1 || d < 1 || ldsa < r) return RNNLS_EINVAL;
-  if (d > 256) return RNNLS_EUNSUPPORTED;
+  if (d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
   RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
   return solve_f32(ctx, SA, ldsa, Sb, r, d, x, info);
 }
@@ -485,7 +488,7 @@ int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, 
 int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,
                     double *x, rnnls_info *info) {
   if (!ctx || !SA || !Sb || !x || r < 1 || d < 1 || ldsa < r) return RNNLS_EINVAL;
-  if (d > 256) return RNNLS_EUNSUPPORTED;
+  if (d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
   RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
   return solve_f64(ctx, SA, ldsa, Sb, r, d, x, info);
 }
@@ -495,7 +498,7 @@ int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t coun
   for (int64_t i = 0; i < count; ++i) {
     const rnnls_problem &p = probs[i];
     if (!p.SA || !p.Sb || !p.x || p.r < 1 || p.d < 1 || p.ldsa < p.r) return RNNLS_EINVAL;
-    if (p.d > 256) return RNNLS_EUNSUPPORTED;
+    if (p.d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
   }
   RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
   return solve_batched(ctx, probs, count);
@@ -505,7 +508,7 @@ int rnnls_solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float
                       int64_t d, int64_t nrhs, double *X, int64_t ldx, rnnls_info *infos) {
   if (!ctx || !SA || !SB || !X) return RNNLS_EINVAL;
   if (r < 1 || d < 1 || nrhs < 1 || ldsa < r || ldsb < r || ldx < d) return RNNLS_EINVAL;
-  if (d > 256) return RNNLS_EUNSUPPORTED;
+  if (d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
   RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
   return solve_multi(ctx, SA, ldsa, SB, ldsb, r, d, nrhs, X, ldx, infos);
 }

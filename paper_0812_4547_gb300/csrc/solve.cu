@@ -384,6 +384,7 @@ struct lh_job {
   double *x;
   rnnls_info *info;
   int q_smem;  // 1: copy Q into shared memory (it fits); 0: read it from global memory
+  float *Bg;   // non-null: the passive-block inverse lives here (global, odd_ld(d) x d), not in shared memory
 };
 
 // float-float dot accumulator with float-float inputs (Dot2 on the leading
@@ -827,7 +828,7 @@ struct lh_layout {
       off_res, off_f1, off_f2, off_f3;
 };
 
-__host__ __device__ inline lh_layout lh_make_layout(int d, bool q_smem) {
+__host__ __device__ inline lh_layout lh_make_layout(int d, bool q_smem, bool b_smem = true) {
   lh_layout L;
   size_t o = 0;
   auto take = [&](size_t b) {
@@ -836,7 +837,7 @@ __host__ __device__ inline lh_layout lh_make_layout(int d, bool q_smem) {
     return at;
   };
   const int ldB = odd_ld(d), ldQ = odd_ld(d + 1);
-  L.off_B = take((size_t)ldB * d * 4);
+  L.off_B = b_smem ? take((size_t)ldB * d * 4) : 0;
   L.off_Qh = q_smem ? take((size_t)(d + 1) * ldQ * 4) : 0;
   L.off_Ql = q_smem ? take((size_t)(d + 1) * ldQ * 4) : 0;
   L.off_Dsc = take((size_t)d * 4);
@@ -861,10 +862,10 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
   const int D1 = d + 1;
   const int tid = threadIdx.x;
   const bool q_smem = jb.q_smem;
-  const lh_layout L = lh_make_layout(d, q_smem);
+  const lh_layout L = lh_make_layout(d, q_smem, jb.Bg == nullptr);
   lh_vecs V;
   V.ldB = odd_ld(d);
-  V.B = (float *)(smem_raw + L.off_B);
+  V.B = jb.Bg ? jb.Bg : (float *)(smem_raw + L.off_B);
   if (q_smem) {
     float *qh = (float *)(smem_raw + L.off_Qh);
     float *ql = (float *)(smem_raw + L.off_Ql);
@@ -1244,7 +1245,17 @@ constexpr size_t kLHStaticSmem = 2048;
 bool lh_q_fits(rnnls_ctx *ctx, int d) {
   return lh_make_layout(d, true).bytes + kLHStaticSmem <= (size_t)ctx->max_smem_optin;
 }
-size_t lh_smem_for(rnnls_ctx *ctx, int d) { return lh_make_layout(d, lh_q_fits(ctx, d)).bytes; }
+// Whether the passive-block inverse fits in shared memory (Q read from global
+// memory); for larger d it lives in the workspace and is read through L1/L2.
+bool lh_b_fits(rnnls_ctx *ctx, int d) {
+  return lh_make_layout(d, false, true).bytes + kLHStaticSmem <= (size_t)ctx->max_smem_optin;
+}
+size_t lh_smem_for(rnnls_ctx *ctx, int d) {
+  return lh_make_layout(d, lh_q_fits(ctx, d), lh_b_fits(ctx, d)).bytes;
+}
+size_t lh_bg_bytes(rnnls_ctx *ctx, int d) {
+  return lh_b_fits(ctx, d) ? 0 : align_up((size_t)odd_ld(d) * d * sizeof(float), 256);
+}
 
 int lh_launch(rnnls_ctx *ctx, const lh_job *d_jobs, int64_t count, size_t smem) {
   prof_scope ps(ctx, K_LH);
@@ -1256,7 +1267,7 @@ int lh_launch(rnnls_ctx *ctx, const lh_job *d_jobs, int64_t count, size_t smem) 
 
 int lh_launch_one(rnnls_ctx *ctx, const lh_job &jb) {
   prof_scope ps(ctx, K_LH);
-  const size_t smem = lh_make_layout(jb.d, jb.q_smem != 0).bytes;
+  const size_t smem = lh_make_layout(jb.d, jb.q_smem != 0, jb.Bg == nullptr).bytes;
   if (smem + kLHStaticSmem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
   static int attr_bytes = 0;
   if ((int)smem > attr_bytes) {
@@ -1272,7 +1283,7 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
               rnnls_info *info) {
   const gram_plan g = plan_gram(r, (int)d, ctx->num_sms);
   const bool fits = lh_q_fits(ctx, (int)d);
-  const size_t bytes = solve_ws_bytes(g, (int)d, 1);
+  const size_t bytes = solve_ws_bytes(g, (int)d, 1) + lh_bg_bytes(ctx, (int)d);
   int st = ensure_workspace(ctx, bytes);
   if (st) return st;
   ws_carver wc(ctx->ws);
@@ -1284,6 +1295,7 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
   w.Qlo = wc.take<float>(D1 * D1);
   w.colabs = wc.take<double>((size_t)d);
   w.part_abs = wc.take<double>((size_t)g.splits * g.T * kGT);
+  float *Bg = lh_b_fits(ctx, (int)d) ? nullptr : wc.take<float>((size_t)odd_ld((int)d) * d);
   cudaStream_t s = ctx->stream;
   dim3 grid((unsigned)g.ntiles, (unsigned)g.splits);
   if (sizeof(T) == 4) {
@@ -1325,6 +1337,7 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
   jb.x = x;
   jb.info = info;
   jb.q_smem = fits ? 1 : 0;
+  jb.Bg = Bg;
   if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
   return lh_launch_one(ctx, jb);
 }
@@ -1353,7 +1366,7 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   for (int64_t i = 0; i < count; ++i) {
     const int di = (int)probs[i].d;
     plans[(size_t)i] = plan_gram(probs[i].r, di, std::max(1, ctx->num_sms / 2));
-    bytes += solve_ws_bytes(plans[(size_t)i], di, 0);
+    bytes += solve_ws_bytes(plans[(size_t)i], di, 0) + lh_bg_bytes(ctx, di);
     smem = std::max(smem, lh_smem_for(ctx, di));
     tiles += plans[(size_t)i].ntiles;
   }
@@ -1408,6 +1421,7 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
     jb.x = pb.x;
     jb.info = pb.info;
     jb.q_smem = lh_q_fits(ctx, (int)pb.d) ? 1 : 0;
+    jb.Bg = lh_b_fits(ctx, (int)pb.d) ? nullptr : wc.take<float>((size_t)odd_ld((int)pb.d) * pb.d);
   }
   first[count] = blocks;
   cudaStream_t s = ctx->stream;
@@ -1433,7 +1447,8 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
   // then one Lawson-Hanson block per target, all reading the same Q
   const int64_t D1 = d + nrhs;
   const gram_plan g = plan_gram(r, (int)(D1 - 1), ctx->num_sms);
-  const size_t bytes = solve_ws_bytes(g, (int)(D1 - 1), nrhs);
+  const bool bfit = lh_b_fits(ctx, (int)d);
+  const size_t bytes = solve_ws_bytes(g, (int)(D1 - 1), nrhs) + (size_t)nrhs * lh_bg_bytes(ctx, (int)d);
   int st = ensure_workspace(ctx, bytes);
   if (st) return st;
   ws_carver wc(ctx->ws);
@@ -1470,6 +1485,7 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
     jb.x = X + t * ldx;
     jb.info = infos ? infos + t : nullptr;
     jb.q_smem = 0;  // every target reads the shared Q from global memory (L1/L2), so two blocks fit per SM
+    jb.Bg = bfit ? nullptr : wc.take<float>((size_t)odd_ld((int)d) * d);
   }
   const size_t jbytes = (size_t)nrhs * sizeof(lh_job);
   st = ensure_pinned(ctx, jbytes);
@@ -1477,7 +1493,7 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
   memcpy(ctx->pinned, jobs.data(), jbytes);
   RNNLS_CUDA_TRY(cudaMemcpyAsync(d_jobs, ctx->pinned, jbytes, cudaMemcpyHostToDevice, s));
   RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
-  return lh_launch(ctx, d_jobs, nrhs, lh_make_layout((int)d, false).bytes);
+  return lh_launch(ctx, d_jobs, nrhs, lh_make_layout((int)d, false, bfit).bytes);
 }
 
 int residual_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,

@@ -148,3 +148,56 @@ def test_end_to_end_randomized_nnls(ctx, orc):
     assert rg >= 1 - 1e-9
     assert abs(rg - ro) <= 1e-6 * ro
     assert np.linalg.norm(xg - xo) <= 1e-3 * np.linalg.norm(xo)
+
+
+# d above about 230: the passive-block inverse no longer fits in shared
+# memory and is kept in the workspace (one block per solve either way)
+@pytest.mark.parametrize("m,d,seed", [(450, 300, 11), (1200, 600, 12)])
+def test_large_d(ctx, orc, m, d, seed):
+    rng = np.random.default_rng(seed)
+    S = rng.standard_normal((m, d))
+    s = rng.standard_normal(m) + S @ np.maximum(rng.standard_normal(d), 0)
+    check_match(*solve_both(ctx, orc, S, s))
+
+
+def test_large_d_batched_and_multi(ctx, orc):
+    import torch
+
+    import paper_0812_4547_gb300 as P
+
+    rng = np.random.default_rng(21)
+    shapes = [(400, 300), (300, 40), (700, 500)]
+    probs, data = [], []
+    for m, d in shapes:
+        S = rng.standard_normal((m, d)).astype(np.float32)
+        s = (rng.standard_normal(m) + S @ np.maximum(rng.standard_normal(d), 0)).astype(np.float32)
+        x = torch.empty(d, dtype=torch.float64, device="cuda")
+        info = torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device="cuda")
+        probs.append((dev_colmajor(S), dev_vec(s), x, info))
+        data.append((S, s))
+    ctx.solve_batched(probs)
+    torch.cuda.synchronize()
+    for (S, s), (_, _, x, info) in zip(data, probs):
+        xo, io = orc.nnls(S, s)
+        check_match(host(x), P.info_dict(info), xo, io)
+    # three targets sharing one sketch with d = 300
+    m, d, nrhs = 450, 300, 3
+    S = rng.standard_normal((m, d)).astype(np.float32)
+    T = np.stack([rng.standard_normal(m) + S @ np.maximum(rng.standard_normal(d), 0) for _ in range(nrhs)],
+                 axis=1).astype(np.float32)
+    X, infos = ctx.solve_multi(dev_colmajor(S), dev_colmajor(T), r=m)
+    X = host(X)
+    for t in range(nrhs):
+        xo, io = orc.nnls(S, T[:, t])
+        check_match(X[:, t], P.info_dict(infos[t]), xo, io)
+
+
+def test_d_beyond_the_limit_is_refused(ctx):
+    import torch
+
+    import paper_0812_4547_gb300 as P
+
+    S = torch.zeros((1025, 1100), device="cuda").t()
+    s = torch.zeros(1100, device="cuda")
+    with pytest.raises(P.RNNLSError):
+        ctx.solve(S, s)
