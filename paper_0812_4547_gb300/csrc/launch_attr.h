@@ -1,0 +1,57 @@
+// launch_attr.h -- kernel attributes set once per device.
+//
+// A kernel's attributes (the dynamic shared memory it may ask for, its
+// preferred shared-memory carveout) belong to each device's context, so a
+// process that drives several devices must set them on every device it
+// launches on.  These helpers remember, per device, what was set.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+namespace rnnls {
+
+constexpr int kAttrDevices = 64;  // device ordinals beyond this share entries
+
+// Runs `set` the first time it is reached on the current device; later calls
+// on that device return cudaSuccess without running it (a failed `set` is
+// retried on the next call).
+struct once_per_device {
+  std::mutex m;
+  bool done[kAttrDevices] = {};
+
+  template <typename F>
+  cudaError_t run(F &&set) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(m);
+    bool &d = done[dev % kAttrDevices];
+    if (d) return cudaSuccess;
+    e = set();
+    if (e == cudaSuccess) d = true;
+    return e;
+  }
+};
+
+// The largest dynamic shared memory `func` was allowed on each device; grows
+// it on the current device when a launch needs more.
+struct smem_attr {
+  std::mutex m;
+  int bytes[kAttrDevices] = {};
+
+  cudaError_t ensure(const void *func, size_t need) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(m);
+    int &have = bytes[dev % kAttrDevices];
+    if ((int)need <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e == cudaSuccess) have = (int)need;
+    return e;
+  }
+};
+
+}  // namespace rnnls

@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "launch_attr.h"
 
 namespace rnnls {
 
@@ -1269,14 +1270,17 @@ int column_map(CUtensorMap *m, const float *base, int64_t n_raw, int64_t cols, i
 
 int launch_srht(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, const srht_part &P, int blocks, int vec,
                 const uint64_t *signs, float *part, unsigned int *counters) {
-  static bool ready = false;
-  if (!ready) {
-    for (auto kern : {sketch_srht_f32<0>, sketch_srht_f32<8>, sketch_srht_f32<16>, sketch_srht_f32<24>,
-                      sketch_srht_f32<32>, sketch_srht_f32<40>})
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSketchSmem) != cudaSuccess)
-        return RNNLS_ECUDA;
-    ready = true;
-  }
+  static once_per_device attrs;
+  if (attrs.run([] {
+        for (auto kern : {sketch_srht_f32<0>, sketch_srht_f32<8>, sketch_srht_f32<16>, sketch_srht_f32<24>,
+                          sketch_srht_f32<32>, sketch_srht_f32<40>}) {
+          const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)kSketchSmem);
+          if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+      }) != cudaSuccess)
+    return RNNLS_ECUDA;
   CUtensorMap tmA, tmB;
   memset(&tmA, 0, sizeof(tmA));
   memset(&tmB, 0, sizeof(tmB));
@@ -1550,12 +1554,8 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
                              (const int64_t *)(d_tables + off_fp), nb, samp_tot, plan_tot);
   }
   if (st) return st;
-  static bool ready = false;
-  if (!ready) {
-    RNNLS_CUDA_TRY(cudaFuncSetAttribute(sketch_srht_batch_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kSketchSmem));
-    ready = true;
-  }
+  static smem_attr batch_attr;
+  RNNLS_CUDA_TRY(batch_attr.ensure((const void *)sketch_srht_batch_f32, kSketchSmem));
   prof_scope ps_main(ctx, K_SKETCH);
   sketch_srht_batch_f32<<<(unsigned)B, kThreads, kSketchSmem, s>>>(
       (const srht_job *)d_tables, nb, (const int64_t *)(d_tables + off_st), part, maxseg, rpg_max, counters);
@@ -1598,12 +1598,8 @@ int sketch_f64(rnnls_ctx *ctx, const sketch_args_f64 &a) {
   prof_scope ps(ctx, K_SKETCH_F64);
   if (n <= 8192) {
     const size_t smem = (size_t)n * sizeof(double) + (size_t)std::max<int64_t>(n / 64, 4) * sizeof(uint64_t);
-    static bool attr = false;
-    if (!attr) {
-      RNNLS_CUDA_TRY(cudaFuncSetAttribute(sketch_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(8192 * sizeof(double) + 128 * sizeof(uint64_t))));
-      attr = true;
-    }
+    static smem_attr small_attr;
+    RNNLS_CUDA_TRY(small_attr.ensure((const void *)sketch_small<double>, 8192 * sizeof(double) + 128 * sizeof(uint64_t)));
     sketch_small<double><<<(unsigned)(a.d + 1), 256, smem, s>>>(a.A, a.lda, a.b, a.n_raw, a.n_raw, a.d, a.L, a.seed,
                                                                 a.inst, a.idx, a.r, a.d_count, a.scale, a.SA, a.ldsa,
                                                                 a.Sb, a.r);

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "launch_attr.h"
 
 namespace rnnls {
 
@@ -1196,11 +1197,11 @@ __global__ void sum_partials_kernel(const double *__restrict__ partial, int nb, 
 // needs the L1 share; a function's carveout is per function, hence the
 // separate instantiation.)
 void gram_carveout_once() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(gram_fused_f32_kernel<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       (int)cudaSharedmemCarveoutMaxShared);
-  done = true;
+  static once_per_device carve;
+  carve.run([] {
+    return cudaFuncSetAttribute(gram_fused_f32_kernel<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+  });
 }
 
 struct gram_plan {
@@ -1260,7 +1261,8 @@ size_t lh_bg_bytes(rnnls_ctx *ctx, int d) {
 int lh_launch(rnnls_ctx *ctx, const lh_job *d_jobs, int64_t count, size_t smem) {
   prof_scope ps(ctx, K_LH);
   if (smem + kLHStaticSmem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
-  RNNLS_CUDA_TRY(cudaFuncSetAttribute(lh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  static smem_attr lh_attr;
+  RNNLS_CUDA_TRY(lh_attr.ensure((const void *)lh_kernel, smem));
   lh_kernel<<<(unsigned)count, kLHThreads, smem, ctx->stream>>>(d_jobs, 3, 30);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
@@ -1269,11 +1271,8 @@ int lh_launch_one(rnnls_ctx *ctx, const lh_job &jb) {
   prof_scope ps(ctx, K_LH);
   const size_t smem = lh_make_layout(jb.d, jb.q_smem != 0, jb.Bg == nullptr).bytes;
   if (smem + kLHStaticSmem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
-  static int attr_bytes = 0;
-  if ((int)smem > attr_bytes) {
-    RNNLS_CUDA_TRY(cudaFuncSetAttribute(lh_kernel_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_bytes = (int)smem;
-  }
+  static smem_attr one_attr;
+  RNNLS_CUDA_TRY(one_attr.ensure((const void *)lh_kernel_one, smem));
   lh_kernel_one<<<1, kLHThreads, smem, ctx->stream>>>(jb, 3, 30);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
