@@ -26,6 +26,10 @@
  *   - Return value: RNNLS_OK or an error code below.  Argument errors are
  *     detected on the host before anything is enqueued.  Per-solve
  *     outcomes (singular, iteration cap) are reported in rnnls_info.
+ *   - A context is used by one host thread at a time (its workspace and
+ *     staging buffer are reused call after call); use one context per
+ *     thread or stream for concurrent work.  Different contexts may share a
+ *     device and run concurrently.
  *
  * Randomness (the paper leaves the generator unspecified, Alg. 1 steps 2
  * and 4): Philox4x64-10 (Salmon et al., SC'11) keyed by (seed, instance),
