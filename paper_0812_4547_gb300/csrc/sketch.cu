@@ -390,6 +390,244 @@ __global__ void __launch_bounds__(kThreads, 1)
   int q = 0;
   uint32_t phase = 0;
 
+  if constexpr (SLOTS >= 24) {
+    // Pipelined order (24 or more plan rows per thread in registers): the
+    // combine of step ls runs beside pass 1 of step ls + 1 (different stage
+    // buffers), so each step has one block barrier and the gather's loads
+    // overlap the transform's.  With fewer rows the extra registers this
+    // order needs cost more than it saves (a concurrent Gram block no longer
+    // fits beside the sketch block).
+    auto wait_copy = [&](int64_t sidx) {
+      if (!vec) return;
+      const uint32_t bar = smem_u32(&mbar[sidx % kStages]);
+      const uint32_t par = (uint32_t)((sidx / kStages) & 1);
+      const uint32_t limit = *(volatile int *)&stalled ? 64u : kSpinLimit;
+      bool ok = false;
+      for (uint32_t it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, par);
+      if (!ok) *(volatile int *)&stalled = 1;
+    };
+    auto fill = [&](int64_t jj, int cc, float *zw) {
+      const float *x = (cc < d) ? A + (int64_t)cc * lda : Bm + (int64_t)(cc - d) * ldb;
+      if (!vec) {
+        const int64_t row0 = (4 * jj + w) * (int64_t)kM;
+#pragma unroll 16
+        for (int i = wt; i < kM; i += 64) {
+          const int64_t row = row0 + i;
+          zw[swz128((uint32_t)i)] = (row < n_raw) ? x[row] : 0.0f;
+        }
+        bar_worker(w);
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t line = (4 * jj + w) * (int64_t)(kM / 32) + 64 * h + wt;
+          if (line == nrow32) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const int64_t row = 32 * line + e;
+              zw[swz128((uint32_t)((h << 11) | (wt << 5) | e))] = (row < n_raw) ? x[row] : 0.0f;
+            }
+          }
+        }
+      }
+    };
+    auto pass1 = [&](float (&v)[64], float *zw, int bq) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t sw = sgn[bq][w][2 * ((h << 5) | (wt >> 1)) + (wt & 1)];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          const float4 t =
+              *reinterpret_cast<const float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2)));
+          v[32 * h + 4 * g + 0] = xor_sign(t.x, (sw << (31 - (4 * g + 0))) & 0x80000000u);
+          v[32 * h + 4 * g + 1] = xor_sign(t.y, (sw << (31 - (4 * g + 1))) & 0x80000000u);
+          v[32 * h + 4 * g + 2] = xor_sign(t.z, (sw << (31 - (4 * g + 2))) & 0x80000000u);
+          v[32 * h + 4 * g + 3] = xor_sign(t.w, (sw << (31 - (4 * g + 3))) & 0x80000000u);
+        }
+      }
+      fwht64(v);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+          *reinterpret_cast<float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2))) =
+              make_float4(v[32 * h + 4 * g], v[32 * h + 4 * g + 1], v[32 * h + 4 * g + 2], v[32 * h + 4 * g + 3]);
+    };
+    auto pass2 = [&](float (&v)[64], float *zw) {
+      const uint32_t lane = (uint32_t)(wt & 31), hi = (uint32_t)(wt >> 5) << 11;
+#pragma unroll
+      for (int s2 = 0; s2 < 64; ++s2) v[s2] = zw[hi | ((uint32_t)s2 << 5) | (lane ^ (((uint32_t)s2 & 7u) << 2))];
+      fwht64(v);
+#pragma unroll
+      for (int s2 = 0; s2 < 64; ++s2) zw[hi | ((uint32_t)s2 << 5) | (lane ^ (((uint32_t)s2 & 7u) << 2))] = v[s2];
+    };
+    step_cursor tc = cur;  // the step being transformed (one ahead of `cur`)
+    {
+      wait_copy(0);
+      float *zw = stage + w * kM;
+      fill(tc.j, tc.col, zw);
+      float v[64];
+      pass1(v, zw, 0);
+      bar_worker(w);
+      pass2(v, zw);
+      tc.next(P, D1);
+    }
+    if (!signs_by_copy && nsteps > 1) make_signs(tc.j, 1);
+    for (int64_t ls = 0; ls < nsteps; ++ls) {
+      const int64_t j = cur.j;
+      const int col = cur.col;
+      const int bq = (int)(ls % kStages);
+      __syncthreads();  // step ls transformed; step ls-1 combined (its buffer is free); next signs visible
+      if (vec && tid == 0 && ls + 2 < nsteps) {
+        fence_proxy_async();
+        issue(true);
+      }
+      if (cur.kg != kg_loaded) {  // this plan group's words (row sums are zero here)
+#pragma unroll
+        for (int e = 0; e < SLOTS; ++e) pk_r[e] = plan_pk[((size_t)cur.kg * SLOTS + e) * kThreads + tid];
+        kg_loaded = cur.kg;
+      }
+      const bool more = ls + 1 < nsteps;
+      const int bn = (int)((ls + 1) % kStages);
+      float *zn = stage + bn * kStageFloats + w * kM;
+      float v[64];
+      if (more) {
+        wait_copy(ls + 1);
+        fill(tc.j, tc.col, zn);
+        pass1(v, zn, bn);
+      }
+      {
+        const uint32_t step_u32 = stage_u32 + (uint32_t)(bq * kStageFloats) * 4u;
+        const uint32_t jm = (uint32_t)(j + jg0) << 16;
+#pragma unroll
+        for (int e = 0; e < SLOTS; ++e) {
+          const uint32_t p = pk_r[e];
+          float z0, z1, z2, z3;
+          lds_x4(step_u32 + (p & 0x3ffcu), z0, z1, z2, z3);
+          const float s1 = __int_as_float((int)((p & 0x80000000u) | 0x3f800000u));
+          const float s2 = __int_as_float((int)(((p << 1) & 0x80000000u) | 0x3f800000u));
+          const float t = fmaf(s2, fmaf(s1, z3, z2), fmaf(s1, z1, z0));
+          acc_r[e] += xor_sign(t, (uint32_t)__popc(p & jm) << 31);
+        }
+      }
+      cur.next(P, D1);
+    // end of this block's part of unit u: write or hand over the sums
+      if (j == P.J - 1 || ls == nsteps - 1) {
+        const int64_t u = cur.u - ((j == P.J - 1) ? 1 : 0);  // cursor already moved on
+        const int64_t kg = kg_loaded;
+        const bool poisoned = *(volatile int *)&stalled != 0;
+        int64_t first = bid, last = bid;
+        if (!P.aligned) {
+          first = part_block_of(u * P.J, B, P);
+          last = part_block_of(u * P.J + P.J - 1, B, P);
+        }
+        const int64_t nseg = last - first + 1;
+        const int64_t seg = bid - first;
+        const int nsl = SLOTS > 0 ? SLOTS : slots;
+        if constexpr (SLOTS > 0) {
+          if (nseg == 1) {
+#pragma unroll
+            for (int e = 0; e < RS; ++e) {
+              const int32_t k = plan_k[((size_t)kg * SLOTS + e) * kThreads + tid];
+              if (k < 0) continue;
+              const float val = poisoned ? __int_as_float(0x7fc00000) : scale * acc_r[e];
+              if (col < d)
+                SA[(int64_t)col * ldsa + k] = val;
+              else
+                SB[(int64_t)(col - d) * ldsb + k] = val;
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < RS; ++e) {
+              const int32_t k = plan_k[((size_t)kg * SLOTS + e) * kThreads + tid];
+              if (k < 0) continue;
+              part[((size_t)seg * P.U + u) * rpg + (size_t)e * kThreads + tid] =
+                  poisoned ? __int_as_float(0x7fc00000) : acc_r[e];
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < RS; ++e) acc_r[e] = 0.0f;
+        } else {
+          tmem_wait_st();
+          // 32 rows at a time: their indices and sums are fetched together
+          for (int s32 = 0; s32 < slots; s32 += 32) {
+            const int n8 = min(4, (slots - s32) >> 3);
+            int32_t kk[32];
+            uint32_t acc[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+              kk[e] = (e < 8 * n8) ? plan_k[((size_t)kg * slots + s32 + e) * kThreads + tid] : -1;
+#pragma unroll
+            for (int b8 = 0; b8 < 4; ++b8)
+              if (b8 < n8) tmem_ld8(t_acc + s32 + 8 * b8, acc + 8 * b8);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              if (kk[e] < 0) continue;
+              const float a = poisoned ? __int_as_float(0x7fc00000) : __uint_as_float(acc[e]);
+              if (nseg == 1) {
+                if (col < d)
+                  SA[(int64_t)col * ldsa + kk[e]] = scale * a;
+                else
+                  SB[(int64_t)(col - d) * ldsb + kk[e]] = scale * a;
+              } else {
+                part[((size_t)seg * P.U + u) * rpg + (size_t)(s32 + e) * kThreads + tid] = a;
+              }
+            }
+#pragma unroll
+            for (int b8 = 0; b8 < 4; ++b8)
+              if (b8 < n8) tmem_st8(t_acc + s32 + 8 * b8, zero8);
+          }
+        }
+        if (nseg > 1) {
+          __threadfence();
+          __syncthreads();
+          if (tid == 0) last_flag = (atomicAdd(&counters[u], 1u) == (unsigned int)(nseg - 1)) ? 1u : 0u;
+          __syncthreads();
+          if (last_flag) {
+            __threadfence();
+            // every row's segment loads in flight together (register variants),
+            // or 32 rows at a time (TMEM variant)
+            constexpr int RB = SLOTS > 0 ? SLOTS : 32;
+            for (int s0b = 0; s0b < nsl; s0b += RB) {
+              int32_t kk[RB];
+              float sum[RB];
+#pragma unroll
+              for (int e = 0; e < RB; ++e) {
+                kk[e] = (s0b + e < nsl) ? plan_k[((size_t)kg * slots + s0b + e) * kThreads + tid] : -1;
+                sum[e] = 0.0f;
+              }
+              for (int64_t g = 0; g < nseg; ++g) {
+                const float *pg = part + ((size_t)g * P.U + u) * rpg + (size_t)s0b * kThreads + tid;
+                float t[RB];
+#pragma unroll
+                for (int e = 0; e < RB; ++e) t[e] = (kk[e] >= 0) ? __ldcg(pg + (size_t)e * kThreads) : 0.0f;
+#pragma unroll
+                for (int e = 0; e < RB; ++e) sum[e] += t[e];
+              }
+#pragma unroll
+              for (int e = 0; e < RB; ++e) {
+                if (kk[e] < 0) continue;
+                if (col < d)
+                  SA[(int64_t)col * ldsa + kk[e]] = scale * sum[e];
+                else
+                  SB[(int64_t)(col - d) * ldsb + kk[e]] = scale * sum[e];
+              }
+            }
+            if (tid == 0) counters[u] = 0u;
+          }
+        }
+      }
+
+      if (more) {
+        bar_worker(w);
+        pass2(v, zn);
+        tc.next(P, D1);
+      }
+      if (!signs_by_copy && ls + 2 < nsteps) make_signs(tc.j, (int)((ls + 2) % kStages));
+    }
+    return;
+  }
+
   for (int64_t ls = 0; ls < nsteps; ++ls) {
     const int64_t j = cur.j;
     const int col = cur.col;
