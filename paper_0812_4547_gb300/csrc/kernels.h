@@ -36,8 +36,11 @@ struct plan_t {
 size_t plan_ws_bytes(int slots, int kgroups);
 // The plan of the rows in idx (drawn before); with a sign table the same
 // launch also writes the first sign_words sign words of D.
-int launch_build_plan(cudaStream_t s, const int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
-                      uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed, uint64_t inst);
+// gen_L > 0: the plan launch also draws the r iid rows of an n = 2^gen_L
+// problem and writes them to idx (no separate row-sampling launch)
+int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
+                      uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed, uint64_t inst,
+                      int gen_L = 0);
 
 // Many instances' rows and plans in one launch each (iid rows; a sign table
 // per instance, its words counted from the instance's first chunk).

@@ -172,12 +172,15 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v) {
 // below 8 * slots (lane q), the spilled ones (into other lanes' free
 // positions, in bank order) and lane q's free positions no spilled row
 // takes.  No block reads another block's output.
-__device__ __forceinline__ void plan_block(int blk, const int32_t *__restrict__ idx, int64_t r,
+// gen_L > 0: the block draws the iid rows itself (draw k = word k of stream
+// 2 shifted right by 64 - gen_L, as sample_iid_kernel does) and the bank-0
+// block of each plan group writes them to idx; gen_L = 0: rows read from idx.
+__device__ __forceinline__ void plan_block(int blk, int32_t *__restrict__ idx, int64_t r,
                                            const int64_t *__restrict__ d_count, uint32_t *__restrict__ plan_pk,
                                            int32_t *__restrict__ plan_k, int slots, int64_t rows_per_group,
                                            int kgroups, uint64_t seed, uint64_t inst,
                                            uint64_t *__restrict__ sign_table, int64_t sign_words,
-                                           int64_t sign_block0) {
+                                           int64_t sign_block0, int gen_L) {
   __shared__ uint32_t cnt[32], ov_start[32], free_start[32];
   __shared__ uint32_t wsum[kPlanThreads / 32];
   __shared__ uint32_t whist[kPlanThreads / 32][32];  // per-warp bank counts (no contention)
@@ -224,8 +227,20 @@ __device__ __forceinline__ void plan_block(int blk, const int32_t *__restrict__ 
     for (int64_t t0 = k0; t0 < k1; t0 += 4 * kPlanThreads) {
       const int64_t kb = t0 + 4 * tid;
       uint32_t rows[4], bank[4];
+      if (gen_L > 0) {
+        // kb is a multiple of 4: one Philox block gives draws kb .. kb + 3
+        const u64x4 u = philox4x64_10((uint64_t)(kb >> 2), kStreamIid, seed, inst);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) rows[e] = (kb + e < k1) ? (uint32_t)idx[kb + e] : 0u;
+        for (int e = 0; e < 4; ++e) rows[e] = (kb + e < k1) ? (uint32_t)(u.w[e] >> (64 - gen_L)) : 0u;
+        if (count_all && q == 0) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (kb + e < k1) idx[kb + e] = (int32_t)rows[e];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) rows[e] = (kb + e < k1) ? (uint32_t)idx[kb + e] : 0u;
+      }
       uint32_t mine = 0;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -319,18 +334,19 @@ __device__ __forceinline__ void plan_block(int blk, const int32_t *__restrict__ 
   }
 }
 
-__global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(const int32_t *__restrict__ idx, int64_t r,
+__global__ void __launch_bounds__(kPlanThreads) build_plan_kernel(int32_t *__restrict__ idx, int64_t r,
                                                                   const int64_t *__restrict__ d_count,
                                                                   uint32_t *__restrict__ plan_pk,
                                                                   int32_t *__restrict__ plan_k, int slots,
                                                                   int64_t rows_per_group, int kgroups, uint64_t seed,
                                                                   uint64_t inst, uint64_t *__restrict__ sign_table,
-                                                                  int64_t sign_words, int64_t sign_block0) {
+                                                                  int64_t sign_words, int64_t sign_block0,
+                                                                  int gen_L) {
   // the sketch launch that follows may be scheduled now (it waits for this
   // launch's completion before it reads the plan)
   asm volatile("griddepcontrol.launch_dependents;");
   plan_block((int)blockIdx.x, idx, r, d_count, plan_pk, plan_k, slots, rows_per_group, kgroups, seed, inst,
-             sign_table, sign_words, sign_block0);
+             sign_table, sign_words, sign_block0, gen_L);
 }
 
 // ---- many instances in one launch -----------------------------------------------
@@ -367,7 +383,7 @@ __global__ void __launch_bounds__(kPlanThreads) build_plan_batched_kernel(const 
   const int p = batch_owner(first, count, blockIdx.x);
   const plan_job jb = jobs[p];
   plan_block((int)(blockIdx.x - first[p]), jb.idx, jb.r, nullptr, jb.pk, jb.k, jb.slots, jb.rows_per_group,
-             jb.kgroups, jb.seed, jb.inst, jb.signs, jb.sign_words, 0);
+             jb.kgroups, jb.seed, jb.inst, jb.signs, jb.sign_words, 0, 0);
 }
 
 int64_t sample_blocks(int64_t r) { return ((r + 3) / 4 + 255) / 256; }
@@ -387,15 +403,16 @@ size_t plan_ws_bytes(int slots, int kgroups) {
   return align_up(e * sizeof(uint32_t), 256) + align_up(e * sizeof(int32_t), 256);
 }
 
-int launch_build_plan(cudaStream_t s, const int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
-                      uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed, uint64_t inst) {
+int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
+                      uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed, uint64_t inst,
+                      int gen_L) {
   if (plan.rows_per_group > kPlanMaxRows || plan.rows_per_group > (int64_t)plan.slots * kThreads)
     return RNNLS_EUNSUPPORTED;
   if (!sign_table) sign_words = 0;
   const int64_t sign_blocks = (sign_words / 4 + kPlanThreads - 1) / kPlanThreads;
   build_plan_kernel<<<(unsigned)(32 * plan.kgroups + sign_blocks), kPlanThreads, 0, s>>>(
       idx, r, d_count, plan.pk, plan.k, plan.slots, plan.rows_per_group, plan.kgroups, seed, inst, sign_table,
-      sign_words, sign_block0);
+      sign_words, sign_block0, gen_L);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 

@@ -1628,9 +1628,9 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
   {
     // the iid rows are drawn once by many blocks, then every plan block reads them
     prof_scope ps(ctx, K_PLAN);
-    if (a.gen_iid) st = launch_sample_iid(s, a.seed, a.inst, a.L, a.r, a.idx);
-    if (!st)
-      st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, signs, g.sign_words, 16 * a.chunk0, a.seed, a.inst);
+    // iid rows are drawn by the plan launch itself (every plan block needs them all)
+    st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, signs, g.sign_words, 16 * a.chunk0, a.seed, a.inst,
+                           a.gen_iid ? a.L : 0);
   }
   if (st) return st;
   if (ctx->plan_event) RNNLS_CUDA_TRY(cudaEventRecord(ctx->plan_event, s));
@@ -1824,8 +1824,8 @@ int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, vo
   float *part = g.maxseg ? wc.take<float>((size_t)g.maxseg * g.P.U * g.plan.rows_per_group) : nullptr;
   if (g.maxseg && cudaMemsetAsync(counters, 0, (size_t)g.P.U * sizeof(unsigned int), s) != cudaSuccess)
     return RNNLS_ECUDA;
-  int st = a.gen_iid ? launch_sample_iid(s, a.seed, a.inst, a.L, a.r, a.idx) : RNNLS_OK;
-  if (!st) st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, signs, g.sign_words, 16 * a.chunk0, a.seed, a.inst);
+  const int st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, signs, g.sign_words, 16 * a.chunk0, a.seed,
+                                   a.inst, a.gen_iid ? a.L : 0);
   if (st) return st;
   return launch_srht(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
 }
