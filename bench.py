@@ -237,6 +237,20 @@ def multi_problem(seed: int) -> MultiProblem:
     return MultiProblem(A, Bm, r)
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in txt.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.machine()
+
+
 def cpu_baseline(p, seconds: float) -> dict:
     import oracle
 
@@ -250,7 +264,7 @@ def cpu_baseline(p, seconds: float) -> dict:
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    out = {"value": done / dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
+    out = {"value": done / dt, "unit": "solves/s", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
            "sample": f"{done} full solves of the workload in {dt:.1f} s (FP64 C oracle, OpenMP over columns)"}
     # the same oracle on one core, when a solve fits in a few seconds there
     if dt / done * threads <= 6.0:
@@ -1008,8 +1022,33 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
     }
     for c in ctxs + [ctx_sketch, ctx_solve]:
         c.close()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_batch(insts[:32], args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def cpu_baseline_batch(insts, seconds: float) -> dict:
+    """The FP64 oracle on a seeded subset of the workload-5 instances (the
+    first ones of the batch, copied to the host), as many as fit in about
+    `seconds`; solves/s over the instances it ran."""
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    done, t_run = 0, 0.0
+    for A, b, r in insts:
+        Ah = A.cpu().numpy()
+        bh = b.cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.randomized_nnls(Ah, bh, r, seed=done, nthreads=threads)
+        t_run += time.perf_counter() - t0
+        done += 1
+        if t_run >= seconds:
+            break
+    return {"value": done / t_run, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"the first {done} instances of the batch in {t_run:.1f} s (FP64 C oracle, OpenMP over columns)"}
 
 
 if __name__ == "__main__":
