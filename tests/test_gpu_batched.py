@@ -87,3 +87,43 @@ def test_batched_rejects_bad_job(ctx):
     idx = torch.zeros(100, dtype=torch.int32, device="cuda")
     with pytest.raises(P.RNNLSError):
         ctx.sketch_batched([(A, b, 100, 1, 0, SA, Sb, idx), (A, b, 0, 1, 0, SA, Sb, idx)])
+
+
+def test_batched_workload_five_shapes_sampled_entries(orc):
+    """The first 16 instances of workload 5's recipe at their real sizes
+    (the benchmark's device generator and launch): every instance's rows
+    bit-exact and two sampled entries against the definition."""
+    import math
+
+    import torch
+
+    import bench
+    import paper_0812_4547_gb300 as P
+    import workloads
+
+    shapes = workloads.batch_shapes(count=16)
+    insts = bench.device_batch(shapes, 5, torch.device("cuda"))
+    c = P.Context(0)
+    try:
+        items = []
+        for i, (A, b, r) in enumerate(insts):
+            d = A.shape[1]
+            items.append((A, b, r, 5, i, torch.empty((d, r), device="cuda").t(), torch.empty(r, device="cuda"),
+                          torch.empty(r, dtype=torch.int32, device="cuda")))
+        c.sketch_batched(items)
+        torch.cuda.synchronize()
+    finally:
+        c.close()
+    rng = np.random.default_rng(16)
+    for (A, b, r, seed, inst, SA, Sb, idx) in items:
+        n_raw, d = A.shape
+        idx_o = orc.sample(seed, inst, P.padded_n(n_raw), r)
+        assert np.array_equal(host(idx), idx_o)
+        sc = 1 / math.sqrt(r)
+        for _ in range(2):
+            k = int(rng.integers(r))
+            j = int(rng.integers(d + 1))
+            col = host(A[:, j] if j < d else b).astype(np.float64)
+            want = orc.sketch_entry(col, seed, inst, int(idx_o[k]), sc)
+            got = host(SA)[k, j] if j < d else host(Sb)[k]
+            assert abs(got - want) <= 1e-5 * sc * np.linalg.norm(col)

@@ -140,3 +140,29 @@ def workloads_multi(n, d, nrhs):
     import workloads
 
     return workloads.multi_rhs(n=n, d=d, nrhs=nrhs, r=1024)[:3]
+
+
+def test_sketch_multi_full_size_sampled_entries(ctx, orc):
+    """Workload 4's sizes (A 2^20 x 100, B 2^20 x 256, r = 4096) in the
+    benchmark's launch configuration: rows bit-exact, sampled entries of A's
+    and B's sketches against the definition (O(n) each)."""
+    import math
+
+    import paper_0812_4547_gb300 as P
+
+    n, d, nrhs, r = 1 << 20, 100, 256, 4096
+    rng = np.random.default_rng(44)
+    A = rng.random((n, d), dtype=np.float32)
+    Bm = rng.random((n, nrhs), dtype=np.float32)
+    SA, SB, idx = ctx.sketch_multi(dev_colmajor(A), dev_colmajor(Bm), r, seed=9, instance=0)
+    idx_o = orc.sample(9, 0, P.padded_n(n), r)
+    assert np.array_equal(host(idx), idx_o)
+    SAh, SBh = host(SA), host(SB)
+    sc = 1 / math.sqrt(r)
+    for _ in range(10):
+        k = int(rng.integers(r))
+        c = int(rng.integers(d + nrhs))
+        col = (A[:, c] if c < d else Bm[:, c - d]).astype(np.float64)
+        want = orc.sketch_entry(col, 9, 0, int(idx_o[k]), sc)
+        got = SAh[k, c] if c < d else SBh[k, c - d]
+        assert abs(got - want) <= 1e-5 * sc * np.linalg.norm(col)
