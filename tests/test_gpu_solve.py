@@ -201,3 +201,31 @@ def test_d_beyond_the_limit_is_refused(ctx):
     s = torch.zeros(1100, device="cuda")
     with pytest.raises(P.RNNLSError):
         ctx.solve(S, s)
+
+
+def test_batched_solve_of_workload_five_sketches(ctx, orc):
+    """Workload 5's solve at its real sizes (r up to 32768, d up to 200): the
+    batched sketch of term-document instances, then the batched solve; every
+    x against the oracle's Lawson-Hanson on the same sketch bytes."""
+    import torch
+
+    import bench
+    import paper_0812_4547_gb300 as P
+
+    shapes = [(1 << 18, 200, 32768), (1 << 17, 150, 16384), (50000, 60, 8192), (20000, 16, 2048)]
+    insts = bench.device_batch(shapes, 7, torch.device("cuda"))
+    items, probs = [], []
+    for i, (A, b, r) in enumerate(insts):
+        d = A.shape[1]
+        SA = torch.empty((d, r), device="cuda").t()
+        Sb = torch.empty(r, device="cuda")
+        items.append((A, b, r, 3, i, SA, Sb, torch.empty(r, dtype=torch.int32, device="cuda")))
+        x = torch.empty(d, dtype=torch.float64, device="cuda")
+        info = torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device="cuda")
+        probs.append((SA, Sb, x, info))
+    ctx.sketch_batched(items)
+    ctx.solve_batched(probs)
+    torch.cuda.synchronize()
+    for SA, Sb, x, info in probs:
+        xo, io = orc.nnls(host(SA), host(Sb))
+        check_match(host(x), P.info_dict(info), xo, io)
