@@ -44,8 +44,6 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
-    ap.add_argument("--batch-streams", type=int, default=8,
-                    help="workload 5: streams (one library context each) the instances are spread over")
     ap.add_argument("--instances", type=int, default=None, help="workload 5: instance count (default 512)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -890,9 +888,9 @@ def device_batch(shapes, seed: int, dev):
 
 
 def run_batch(args, ws: int, rank: int, local: int, dev):
-    """Workload 5: 512 uneven instances per step, each sketched and solved by
-    the library, spread over --batch-streams streams and replayed as one CUDA
-    graph; also times the plain per-instance form (one stream, no graph)."""
+    """Workload 5: 512 uneven instances per step, sketched by one batched call
+    and solved by one batched call, replayed as one CUDA graph; also times the
+    plain per-instance form (one stream, no graph)."""
     import torch
 
     import paper_0812_4547_gb300 as P
@@ -902,18 +900,14 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
     shapes = workloads.batch_shapes(count=args.instances, seed=rank_seed(c5["seed"], rank, ws))
     insts = device_batch(shapes, rank_seed(c5["seed"], rank, ws), dev)
     count = len(insts)
-    S = max(1, args.batch_streams)
     main_s = torch.cuda.Stream(dev)
-    streams = [torch.cuda.Stream(dev) for _ in range(S)]
-    ctxs = [P.Context(local, st) for st in streams]
+    ctx_plain = P.Context(local, main_s)
     bufs = []
     for (A, b, r) in insts:
         d = A.shape[1]
         bufs.append((torch.empty((d, r), dtype=torch.float32, device=dev).t(), torch.empty(r, device=dev),
                      torch.empty(r, dtype=torch.int32, device=dev), torch.empty(d, dtype=torch.float64, device=dev),
                      torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device=dev)))
-    fork = torch.cuda.Event()
-    joins = [torch.cuda.Event() for _ in range(S)]
 
     # the batched calls stage their job tables through their context's pinned
     # buffer, which a captured graph reads again at every replay: one context each
@@ -921,37 +915,30 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
     ctx_solve = P.Context(local, main_s)
     problems = [(bufs[i][0], bufs[i][1], bufs[i][3], bufs[i][4]) for i in range(count)]
 
-    def enqueue(seed0: int, spread: bool = True):
-        fork.record(main_s)
-        for st in streams:
-            st.wait_event(fork)
-        if spread:
+    def enqueue(seed0: int, batched: bool = True):
+        if batched:
             # every sketch in one batched call, then every solve in one batched call
             ctx_sketch.sketch_batched([(A, b, r, seed0 + i, rank, bufs[i][0], bufs[i][1], bufs[i][2])
                                        for i, (A, b, r) in enumerate(insts)])
+            ctx_solve.solve_batched(problems)
         else:
             # the plain per-instance form: sketch and solve each instance in turn on one stream
             for i, (A, b, r) in enumerate(insts):
                 SA, Sb, idx, x, info = bufs[i]
-                ctxs[0].sketch(A, b, r, seed=seed0 + i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
-                ctxs[0].solve(SA, Sb, r=r, x=x, info=info)
-        for k, st in enumerate(streams):
-            joins[k].record(st)
-            main_s.wait_event(joins[k])
-        if spread:
-            ctx_solve.solve_batched(problems)
+                ctx_plain.sketch(A, b, r, seed=seed0 + i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
+                ctx_plain.solve(SA, Sb, r=r, x=x, info=info)
 
     with torch.cuda.stream(main_s):
         for w in range(max(1, args.warmup)):
             enqueue(0)
         torch.cuda.synchronize()
         # per-kernel times of one step (profiled, not in the graph)
-        for c in ctxs + [ctx_sketch, ctx_solve]:
+        for c in (ctx_sketch, ctx_solve):
             B.rnnls_profile_begin(c.handle, 8 * count + 64)
         enqueue(0)
         torch.cuda.synchronize()
         prof = {}
-        for c in ctxs + [ctx_sketch, ctx_solve]:
+        for c in (ctx_sketch, ctx_solve):
             for k, v in B.rnnls_profile_end(c.handle).items():
                 a = prof.get(k, (0, 0.0))
                 prof[k] = (a[0] + v[0], a[1] + v[1])
@@ -959,7 +946,7 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(main_s)
-        enqueue(0, spread=False)
+        enqueue(0, batched=False)
         t1.record(main_s)
         torch.cuda.synchronize()
         plain_ms = t0.elapsed_time(t1)
@@ -1020,7 +1007,7 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
         "solve_status_nonzero": int(sum(1 for x in stat if x != 0)),
         "cpu_baseline": None,
     }
-    for c in ctxs + [ctx_sketch, ctx_solve]:
+    for c in (ctx_plain, ctx_sketch, ctx_solve):
         c.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_batch(insts[:32], args.cpu_seconds)
