@@ -1213,7 +1213,9 @@ gram_plan plan_gram(int64_t m, int d, int num_sms) {
   gram_plan g;
   g.T = (d + 1 + kGT - 1) / kGT;
   g.ntiles = g.T * (g.T + 1) / 2;
-  int64_t want = std::max<int64_t>(1, (2 * (int64_t)num_sms + g.ntiles - 1) / g.ntiles);
+  // about six blocks per SM (blocks of 256 threads and 80 registers, three
+  // resident per SM): enough warps to keep the FP32 pipe busy
+  int64_t want = std::max<int64_t>(1, (6 * (int64_t)num_sms + g.ntiles - 1) / g.ntiles);
   want = std::min<int64_t>(want, std::max<int64_t>(1, (m + 255) / 256));
   int64_t rps = (m + want - 1) / want;
   rps = std::max<int64_t>(kGT, (rps + kGT - 1) / kGT * kGT);
