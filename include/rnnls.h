@@ -60,7 +60,9 @@ extern "C" {
 #define RNNLS_ENONFINITE 3   /* NaN or Inf in the Gram matrix of the sketch */
 #define RNNLS_ESINGULAR 4    /* passive-set system numerically singular */
 #define RNNLS_EMAXITER 5     /* Lawson-Hanson iteration cap reached */
-#define RNNLS_ETIMEOUT 6     /* a bounded device-side wait gave up */
+#define RNNLS_ETIMEOUT 6     /* reserved: a sketch block whose bounded wait on a tensor copy
+                                gives up writes NaN in its part of SA/Sb instead, which
+                                the solve reports as RNNLS_ENONFINITE */
 #define RNNLS_ECUDA 7        /* a CUDA runtime call failed */
 #define RNNLS_ENOMEM 8       /* workspace allocation failed */
 #define RNNLS_EUNSUPPORTED 9 /* size outside what this build handles */
@@ -195,8 +197,9 @@ typedef struct rnnls_sketch_job {
  * each exactly as rnnls_sketch in iid mode would give it (up to the FP32
  * summation order), computed together: one launch draws every instance's
  * rows, one makes every plan, and one persistent kernel walks all the
- * instances' chunk groups.  `jobs` is a HOST array; each job's pointers are
- * device pointers with the layouts of rnnls_sketch (ldsa >= r, lda >= n_raw).
+ * instances' chunk groups.  `jobs` is a HOST array (count = 0 enqueues
+ * nothing); each job's pointers are device pointers with the layouts of
+ * rnnls_sketch (ldsa >= r, lda >= n_raw).
  * Errors: EINVAL (a null pointer or a bad size in any job; nothing is
  * enqueued then), EUNSUPPORTED (n_raw > 2^28), ENOMEM, ECUDA. */
 int rnnls_sketch_batched(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count);
@@ -243,7 +246,10 @@ int rnnls_solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float
 /* Many independent small NNLS problems in one launch sequence (one
  * Lawson-Hanson block per problem, uneven d and r allowed, each d <= 1024).
  * `probs` is a HOST array of `count` descriptors whose pointers are device
- * pointers. */
+ * pointers; flags must be 0.  count = 0 enqueues nothing.  Each problem's
+ * own outcome is its info->status.  Errors: EINVAL (a null pointer, a bad
+ * size in any problem, nonzero flags; nothing is enqueued then),
+ * EUNSUPPORTED (a d above 1024), ENOMEM, ECUDA. */
 int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count, uint32_t flags);
 
 /* Repeated RandomizedNNLS (the footnote to Theorem 1 in Sec. 1: a few

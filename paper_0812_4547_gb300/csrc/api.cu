@@ -201,8 +201,22 @@ int rnnls_profile_begin(rnnls_ctx *ctx, int max_launches) {
     profile_free(ctx);
     ctx->prof_ev = new (std::nothrow) cudaEvent_t[2 * (size_t)max_launches];
     ctx->prof_kid = new (std::nothrow) int[(size_t)max_launches];
-    if (!ctx->prof_ev || !ctx->prof_kid) return RNNLS_ENOMEM;
-    for (int i = 0; i < 2 * max_launches; ++i) RNNLS_CUDA_TRY(cudaEventCreate(&ctx->prof_ev[i]));
+    if (!ctx->prof_ev || !ctx->prof_kid) {
+      delete[] ctx->prof_ev;
+      delete[] ctx->prof_kid;
+      ctx->prof_ev = nullptr;
+      ctx->prof_kid = nullptr;
+      return RNNLS_ENOMEM;
+    }
+    for (int i = 0; i < 2 * max_launches; ++i) {
+      if (cudaEventCreate(&ctx->prof_ev[i]) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->prof_cap = i / 2;  // profile_free destroys the 2 * prof_cap events made so far ...
+        if (i & 1) cudaEventDestroy(ctx->prof_ev[i - 1]);  // ... and this pair's first one here
+        profile_free(ctx);
+        return RNNLS_ECUDA;
+      }
+    }
     ctx->prof_cap = max_launches;
   }
   ctx->prof_n = 0;
@@ -494,12 +508,13 @@ int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double
 }
 
 int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count, uint32_t flags) {
-  if (!ctx || !probs || count < 1 || flags != 0) return RNNLS_EINVAL;
+  if (!ctx || (!probs && count > 0) || count < 0 || flags != 0) return RNNLS_EINVAL;
   for (int64_t i = 0; i < count; ++i) {
     const rnnls_problem &p = probs[i];
     if (!p.SA || !p.Sb || !p.x || p.r < 1 || p.d < 1 || p.ldsa < p.r) return RNNLS_EINVAL;
     if (p.d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
   }
+  if (count == 0) return RNNLS_OK;
   RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
   return solve_batched(ctx, probs, count);
 }
