@@ -26,6 +26,9 @@
  *   - Return value: RNNLS_OK or an error code below.  Argument errors are
  *     detected on the host before anything is enqueued.  Per-solve
  *     outcomes (singular, iteration cap) are reported in rnnls_info.
+ *   - A call that takes a context makes the context's device current while
+ *     it runs and gives the calling thread's current device back before it
+ *     returns; rnnls_sketch_noalloc runs on the current device.
  *   - A context is used by one host thread at a time (its workspace and
  *     staging buffer are reused call after call); use one context per
  *     thread or stream for concurrent work.  Different contexts may share a

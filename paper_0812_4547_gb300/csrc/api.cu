@@ -88,6 +88,26 @@ using namespace rnnls;
 
 namespace {
 
+// Makes a context's device current while an entry point runs and gives the
+// caller's current device back when it returns (so that a call never moves
+// the calling thread to another device).
+struct device_guard {
+  int prev = -1;
+  cudaError_t set(int dev) {
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess || prev == dev) {
+      prev = -1;
+      return e;
+    }
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) prev = -1;
+    return e;
+  }
+  ~device_guard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 constexpr int64_t kMaxRows = (int64_t)1 << 28;
 // Largest d of the small NNLS (beyond about 230 the passive-block inverse
 // leaves shared memory for the workspace)
@@ -164,7 +184,8 @@ int rnnls_create(rnnls_ctx **out, int device, void *stream) {
     cudaGetLastError();
     return RNNLS_ECUDA;
   }
-  RNNLS_CUDA_TRY(cudaSetDevice(device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(device));
   rnnls_ctx *ctx = new (std::nothrow) rnnls_ctx();
   if (!ctx) return RNNLS_ENOMEM;
   memset(ctx, 0, sizeof(*ctx));
@@ -195,7 +216,8 @@ static void profile_free(rnnls_ctx *ctx) {
 
 int rnnls_profile_begin(rnnls_ctx *ctx, int max_launches) {
   if (!ctx || max_launches < 1) return RNNLS_EINVAL;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   if (ctx->prof_cap < max_launches) {
     RNNLS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     profile_free(ctx);
@@ -252,6 +274,8 @@ int rnnls_profile_end(rnnls_ctx *ctx, rnnls_kernel_time *out, int max_out, int *
 
 int rnnls_destroy(rnnls_ctx *ctx) {
   if (!ctx) return RNNLS_EINVAL;
+  device_guard dg;
+  dg.set(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   profile_free(ctx);
   if (ctx->ws) cudaFree(ctx->ws);
@@ -287,7 +311,8 @@ int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, in
                  int64_t cap, int64_t *r_out) {
   int st = check_sketch_args(ctx, A, lda, b, n_raw, d, r, flags, SA, ldsa, Sb, cap);
   if (st) return st;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   const int L = log2_ceil64(n_raw);
   const bool bern = (flags & RNNLS_SAMPLE_MASK) == RNNLS_SAMPLE_BERNOULLI;
   const int64_t rows = bern ? cap : r;
@@ -345,7 +370,8 @@ int rnnls_sketch_multi(rnnls_ctx *ctx, const float *A, int64_t lda, const float 
   if (n_raw < 1 || d < 1 || nrhs < 1 || r < 1 || lda < n_raw || ldb < n_raw || ldsa < r || ldsb < r)
     return RNNLS_EINVAL;
   if (n_raw > kMaxRows || d + nrhs > (1 << 20) || r > ((int64_t)1 << 30)) return RNNLS_EUNSUPPORTED;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   const int L = log2_ceil64(n_raw);
   aux_view av;
   int st = get_aux(ctx, r, (int64_t)1 << L, idx == nullptr, av);
@@ -396,7 +422,8 @@ int rnnls_sketch_shard(rnnls_ctx *ctx, const float *A, int64_t lda, const float 
   if (row0 == 0 && rows >= n_raw)
     return rnnls_sketch(ctx, A, lda, b, n_raw, d, r, seed, instance, RNNLS_SAMPLE_IID, SA, ldsa, Sb, idx, r, nullptr);
   if (n <= 8192) return RNNLS_EUNSUPPORTED;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   aux_view av;
   int st = get_aux(ctx, r, n, idx == nullptr, av);
   if (st) return st;
@@ -442,7 +469,8 @@ int rnnls_sketch_batched(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t c
     if (j.n_raw > kMaxRows || j.d > (1 << 20) || j.r > ((int64_t)1 << 30)) return RNNLS_EUNSUPPORTED;
   }
   if (count == 0) return RNNLS_OK;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   return sketch_batched_f32(ctx, jobs, count);
 }
 
@@ -451,7 +479,8 @@ int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double 
                      int32_t *idx, int64_t cap, int64_t *r_out) {
   int st = check_sketch_args(ctx, A, lda, b, n_raw, d, r, flags, SA, ldsa, Sb, cap);
   if (st) return st;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   const int L = log2_ceil64(n_raw);
   const bool bern = (flags & RNNLS_SAMPLE_MASK) == RNNLS_SAMPLE_BERNOULLI;
   const int64_t rows = bern ? cap : r;
@@ -495,7 +524,8 @@ int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, 
                 rnnls_info *info) {
   if (!ctx || !SA || !Sb || !x || r < 1 || d < 1 || ldsa < r) return RNNLS_EINVAL;
   if (d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   return solve_f32(ctx, SA, ldsa, Sb, r, d, x, info);
 }
 
@@ -503,7 +533,8 @@ int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double
                     double *x, rnnls_info *info) {
   if (!ctx || !SA || !Sb || !x || r < 1 || d < 1 || ldsa < r) return RNNLS_EINVAL;
   if (d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   return solve_f64(ctx, SA, ldsa, Sb, r, d, x, info);
 }
 
@@ -515,7 +546,8 @@ int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t coun
     if (p.d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
   }
   if (count == 0) return RNNLS_OK;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   return solve_batched(ctx, probs, count);
 }
 
@@ -524,14 +556,16 @@ int rnnls_solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float
   if (!ctx || !SA || !SB || !X) return RNNLS_EINVAL;
   if (r < 1 || d < 1 || nrhs < 1 || ldsa < r || ldsb < r || ldx < d) return RNNLS_EINVAL;
   if (d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   return solve_multi(ctx, SA, ldsa, SB, ldsb, r, d, nrhs, X, ldx, infos);
 }
 
 int rnnls_residual(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
                    const double *x, double *out) {
   if (!ctx || !A || !b || !x || !out || n < 1 || d < 1 || lda < n) return RNNLS_EINVAL;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   return residual_f32(ctx, A, lda, b, n, d, x, out);
 }
 
@@ -540,7 +574,8 @@ int rnnls_solve_boosted(rnnls_ctx *ctx, const float *A, int64_t lda, const float
                         rnnls_info *info) {
   if (!ctx || !A || !b || !x || n_raw < 1 || d < 1 || r < 1 || lda < n_raw || k < 1) return RNNLS_EINVAL;
   if (k > kBoostMaxK || d > kBoostMaxD || n_raw > kMaxRows || r > ((int64_t)1 << 30)) return RNNLS_EUNSUPPORTED;
-  RNNLS_CUDA_TRY(cudaSetDevice(ctx->device));
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
   return solve_boosted_f32(ctx, A, lda, b, n_raw, d, r, seed, instance0, k, x, resid, best, info);
 }
 

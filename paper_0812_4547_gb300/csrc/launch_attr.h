@@ -12,7 +12,7 @@
 
 namespace rnnls {
 
-constexpr int kAttrDevices = 64;  // device ordinals beyond this share entries
+constexpr int kAttrDevices = 64;  // devices remembered; higher ordinals set on every call
 
 // Runs `set` the first time it is reached on the current device; later calls
 // on that device return cudaSuccess without running it (a failed `set` is
@@ -26,8 +26,9 @@ struct once_per_device {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev >= kAttrDevices) return set();
     std::lock_guard<std::mutex> g(m);
-    bool &d = done[dev % kAttrDevices];
+    bool &d = done[dev];
     if (d) return cudaSuccess;
     e = set();
     if (e == cudaSuccess) d = true;
@@ -45,8 +46,9 @@ struct smem_attr {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev >= kAttrDevices) return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     std::lock_guard<std::mutex> g(m);
-    int &have = bytes[dev % kAttrDevices];
+    int &have = bytes[dev];
     if ((int)need <= have) return cudaSuccess;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     if (e == cudaSuccess) have = (int)need;
