@@ -1626,9 +1626,9 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
     if (st) return st;
   }
   {
-    // the iid rows are drawn once by many blocks, then every plan block reads them
+    // one launch: the plan entries, D's sign words and, in iid mode, the
+    // rows, which every plan block draws in full for itself
     prof_scope ps(ctx, K_PLAN);
-    // iid rows are drawn by the plan launch itself (every plan block needs them all)
     st = launch_build_plan(s, a.idx, a.r, a.d_count, g.plan, signs, g.sign_words, 16 * a.chunk0, a.seed, a.inst,
                            a.gen_iid ? a.L : 0);
   }
