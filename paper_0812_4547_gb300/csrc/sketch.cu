@@ -8,14 +8,14 @@
 // the chunks y_c of y.  The work is a list of steps, one per column and
 // group j of four chunks c = 4j..4j+3 that hold data; a persistent grid of
 // one 256-thread block per SM walks equal contiguous stretches of that list:
-//   - bulk asynchronous copies (cp.async.bulk, completion on an mbarrier)
-//     bring the four chunks of a step into shared memory two steps ahead
-//     (three stage buffers), so HBM reads never wait on compute,
-//   - each 64-thread worker flips its chunk's signs with D (Philox words made
-//     one step ahead), transforms it with two 64-point register FWHT passes
-//     joined by one swizzled transpose, in place in its stage buffer,
+//   - thread 0 issues tensor copies (cp.async.bulk.tensor, 128-byte swizzle,
+//     completion on an mbarrier) of the four chunks of a step and a bulk copy
+//     of their sign words, two steps ahead (three stage buffers),
+//   - each 64-thread worker flips its chunk's signs with D (words of the sign
+//     table the plan launch writes), transforms it with two 64-point register
+//     FWHT passes joined by one swizzled transpose, in place in its stage buffer,
 //   - and every thread adds, for the sampled rows it owns (the plan, kept in
-//     registers), the four signed chunk values into per-row registers.
+//     registers or TMEM), the four signed chunk values into per-row sums.
 // A column handled by several blocks leaves one partial-sum vector per
 // block; the last of them to finish adds them in block order.  HBM sees one
 // read of X plus, per split column, a few r-vectors.
