@@ -34,10 +34,10 @@ struct plan_t {
   int64_t rows_per_group;
 };
 size_t plan_ws_bytes(int slots, int kgroups);
-// The plan of the rows in idx (drawn before); with a sign table the same
-// launch also writes the first sign_words sign words of D.
-// gen_L > 0: the plan launch also draws the r iid rows of an n = 2^gen_L
-// problem and writes them to idx (no separate row-sampling launch)
+// The plan of the sampled rows; with a sign table the same launch also
+// writes the first sign_words sign words of D.  gen_L = 0: the rows are
+// read from idx (drawn before); gen_L > 0: the launch draws the r iid rows
+// of an n = 2^gen_L problem itself and writes them to idx.
 int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_count, plan_t plan,
                       uint64_t *sign_table, int64_t sign_words, int64_t sign_block0, uint64_t seed, uint64_t inst,
                       int gen_L = 0);
