@@ -32,7 +32,7 @@ CONFIGS = {
             zeros=10, noise_abs=0.01, seed=0),
     2: dict(name="plain-fp32 2^20x64 term-doc r=4096", n=2 ** 20, d=64, r=4096, dist="termdoc", dtype="f32",
             zero_frac=0.5, noise_rel=0.05, seed=2),
-    3: dict(name="bf16x2 2^22x128 term-doc r=8192", n=2 ** 22, d=128, r=8192, dist="termdoc", dtype="f32",
+    3: dict(name="fp32 2^22x128 term-doc r=8192", n=2 ** 22, d=128, r=8192, dist="termdoc", dtype="f32",
             zero_frac=0.5, noise_rel=0.05, seed=3),
     4: dict(name="multi-rhs 2^20x100 + 256 rhs r=4096", n=2 ** 20, d=100, nrhs=256, r=4096, dist="termdoc",
             dtype="f32", zero_frac_range=(0.3, 0.8), noise_rel=0.05, seed=4),
