@@ -1,4 +1,4 @@
-"""Multi-process paths on CPU (gloo, world size 2).
+"""Multi-process paths on CPU (gloo, world sizes 2 and 4).
 
 1. The row-shard identity behind rnnls_sketch_shard: with the rows split
    into G blocks, rank g transforms only its block with the length-n/G
@@ -71,9 +71,9 @@ def _shard_worker(rank: int, world: int, port: int, n_raw: int, d: int, r: int, 
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("n_raw,d,r", [(3000, 3, 200), (1 << 12, 2, 5000)])
-def test_row_shard_sum_reduce_gives_the_sketch(tmp_path, n_raw, d, r):
-    world = 2
+@pytest.mark.parametrize("n_raw,d,r,world", [(3000, 3, 200, 2), (1 << 12, 2, 5000, 2), (3000, 3, 200, 4),
+                                            ((1 << 13) + 5, 2, 700, 4)])
+def test_row_shard_sum_reduce_gives_the_sketch(tmp_path, n_raw, d, r, world):
     mp.spawn(_shard_worker, args=(world, _free_port(), n_raw, d, r, str(tmp_path)), nprocs=world, join=True)
     got = np.load(tmp_path / "sum.npy")
     want = np.load(tmp_path / "full.npy")
