@@ -104,10 +104,12 @@ typedef struct rnnls_problem {
  * Errors: EINVAL (ctx null), ECUDA (device unusable). */
 int rnnls_create(rnnls_ctx **ctx, int device, void *stream);
 
-/* Free the context and its workspace (synchronises its stream first). */
+/* Free the context and its workspace (synchronises its stream first).
+ * Errors: EINVAL (ctx null). */
 int rnnls_destroy(rnnls_ctx *ctx);
 
-/* Replace the stream the context enqueues on (borrowed). */
+/* Replace the stream the context enqueues on (borrowed; the caller orders
+ * work already enqueued on the old stream).  Errors: EINVAL (ctx null). */
 int rnnls_set_stream(rnnls_ctx *ctx, void *stream);
 
 /* Cap the number of SMs the large-n sketch kernel of this context occupies
@@ -139,7 +141,10 @@ int rnnls_set_plan_event(rnnls_ctx *ctx, void *event);
  * this synchronises the stream.  Requires n_raw >= 1, d >= 1, r >= 1,
  * n_raw <= 2^28.  A and b need not be 16-byte aligned (aligned is faster).
  * Accuracy: FP32 accumulation; relative Frobenius error vs FP64 about
- * 1e-7 * sqrt(log2 n). */
+ * 1e-7 * sqrt(log2 n).  Errors: EINVAL (null A, b, SA or Sb; a size < 1;
+ * lda < n_raw; ldsa < cap; unknown flags; cap < r in iid mode; nothing is
+ * enqueued then), EUNSUPPORTED (n_raw > 2^28, d > 2^20, r > 2^30),
+ * ECAPACITY, ENOMEM, ECUDA. */
 int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d,
                  int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, float *SA, int64_t ldsa, float *Sb,
                  int32_t *idx, int64_t cap, int64_t *r_out);
@@ -207,7 +212,9 @@ typedef struct rnnls_sketch_job {
  * enqueued then), EUNSUPPORTED (n_raw > 2^28), ENOMEM, ECUDA. */
 int rnnls_sketch_batched(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count);
 
-/* The same sketch in FP64 throughout (for FP64 inputs). */
+/* The same sketch in FP64 throughout (for FP64 inputs), with the same
+ * arguments, sampling, scale and errors as rnnls_sketch; every sum is
+ * formed in FP64. */
 int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double *b, int64_t n_raw, int64_t d,
                      int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, double *SA, int64_t ldsa,
                      double *Sb, int32_t *idx, int64_t cap, int64_t *r_out);
@@ -226,11 +233,14 @@ int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double 
  * above about 230 the passive-block inverse is kept in the context's
  * workspace instead of shared memory),
  * r >= 1.  A return of RNNLS_OK means the work was enqueued; the solve's
- * own outcome is info->status. */
+ * own outcome is info->status (RNNLS_ENONFINITE with x = 0 when SA or Sb
+ * holds a NaN or an infinity).  Errors: EINVAL (null SA, Sb or x; r < 1;
+ * d < 1; ldsa < r), EUNSUPPORTED (d > 1024), ENOMEM, ECUDA. */
 int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
                 rnnls_info *info);
 
-/* The same solve for FP64 sketches. */
+/* The same solve for FP64 sketches (same rules, limits and errors; the
+ * Gram is summed in FP64). */
 int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,
                     double *x, rnnls_info *info);
 
@@ -278,7 +288,8 @@ int rnnls_solve_boosted(rnnls_ctx *ctx, const float *A, int64_t lda, const float
 
 /* Objective of Definition 1 on the full data: out[0] = ||A x - b||^2 with
  * A n x d (lda >= n) and b FP32, x FP64 (device), accumulated in FP64.
- * out: device double. */
+ * out: device double.  Errors: EINVAL (a null pointer, n < 1, d < 1,
+ * lda < n), ENOMEM, ECUDA. */
 int rnnls_residual(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,
                    const double *x, double *out);
 
