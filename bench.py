@@ -39,16 +39,21 @@ FALLBACK_HBM_GBS = 6800.0
 
 
 def parse():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap = argparse.ArgumentParser(description="RandomizedNNLS throughput and sketch roofline on synthetic workloads "
+                                             "(one JSON line on stdout)")
+    ap.add_argument("--gpus", type=int, default=1, help="GPUs (one process each under torchrun)")
+    ap.add_argument("--steps", type=int, default=1000, help="timed steps")
+    ap.add_argument("--warmup", type=int, default=20, help="untimed warm-up steps")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
+                    help="workload: 1 4096x20 FP64 r=512; 2 2^20x64 r=4096; 3 2^22x128 r=8192; "
+                         "4 2^20x100 with 256 targets r=4096; 5 512 uneven instances")
     ap.add_argument("--instances", type=int, default=None, help="workload 5: instance count (default 512)")
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"],
+                    help="reference: the FP64 oracle on the host cores instead of the GPU library")
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end leg (host inputs copied in, x read back)")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host cores")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="host-core time budget of the CPU baseline")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="run each step's sketch and solve back to back on one stream")
     ap.add_argument("--copy-streams", type=int, default=1,
