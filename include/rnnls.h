@@ -320,17 +320,25 @@ int rnnls_profile_end(rnnls_ctx *ctx, rnnls_kernel_time *out, int max_out, int *
  * cudaStream_t, NULL = legacy default stream) of the current device.
  * Inputs and outputs are the caller's, as in rnnls_sketch (idx nullable);
  * all scratch lives in one 8 MiB array compiled into the library, which
- * every GPU that loads the library holds until the process exits.
- * The first call on a device looks up that device's address of the array
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  Every call shares the array and overwrites
- * all of the scratch it reads (nothing needs clearing), so calls whose work
- * overlaps on the GPU (other streams, other threads) race: serialise them.
+ * every GPU on which this entry point has been called holds until the
+ * process exits.
+ * Set-up: the first call on a device (and the first call after the current
+ * context changed, e.g. after cudaDeviceReset) looks up that device's
+ * address of the array (cudaGetSymbolAddress) with the device current.
+ * With lazy module loading the driver also reserves the array and the
+ * kernels' code on that device at this first call, so make one first
+ * (warm-up) call while device memory is still free, and before any stream
+ * capture; later calls allocate nothing.  Every call shares the array and
+ * overwrites all of the scratch it reads (nothing needs clearing), so calls
+ * whose work overlaps on the GPU (other streams, other threads) race:
+ * serialise them.
  * Limits: 1 <= r <= 16384 (RNNLS_EUNSUPPORTED above), n_raw <= 2^28;
  * large column counts get fewer chunk groups (less parallelism) so that the
  * partial sums fit.  Calls no cudaMalloc, cudaFree or allocating library
  * routine.  Errors: EINVAL (null pointer, bad size or stride),
- * EUNSUPPORTED (r above the limit), ECUDA. */
+ * EUNSUPPORTED (r above the limit, n_raw above 2^28, a current device
+ * ordinal of 64 or more), ECUDA (the set-up's address lookup or a launch
+ * failed). */
 int rnnls_sketch_noalloc(void *stream, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d,
                          int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa, float *Sb,
                          int32_t *idx);

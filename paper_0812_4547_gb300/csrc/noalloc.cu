@@ -9,11 +9,17 @@
 // when no idx buffer is given, the combine plan, the per-chunk-range partial
 // sums) comes from one fixed array compiled into this library.
 //
-// The array is a file-scope __device__ variable, so every GPU that loads the
-// library holds kNoAllocScratchBytes of it until the process exits.  Host
-// code cannot use the array's name as a device address; the first call on a
-// device asks the runtime for that device's address (cudaGetSymbolAddress)
-// and remembers it.
+// The array is a file-scope __device__ variable: every GPU on which the
+// entry point has been called holds kNoAllocScratchBytes of it until the
+// process exits (with lazy module loading the driver reserves it, with this
+// file's kernels, at the first call on a device).  Host code cannot use the
+// array's name as a device address; the set-up asks the runtime for the
+// current device's address (cudaGetSymbolAddress) and remembers it together
+// with the unique ID of the context it belongs to.  When the current context
+// changes (cudaDeviceReset and a new primary context, or a context the
+// caller made current) the next call repeats the set-up, since the array
+// can then sit at another address.
+#include <cuda.h>  // CUcontext (the two driver calls are fetched at run time)
 #include <math.h>
 
 #include <mutex>
@@ -28,31 +34,73 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices];
-int g_num_sms[kMaxDevices];
+typedef CUresult (*ctx_get_current_fn)(CUcontext *);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long *);
 
-// Once per device, with that device current: the device address of the
-// scratch array and the SM count.
+std::mutex g_setup_mutex;
+struct device_setup {
+  unsigned long long ctx_id;  // unique ID of the context the address belongs to
+  void *addr;                 // device address of g_noalloc_scratch in that context
+  int num_sms;
+};
+device_setup g_setup[kMaxDevices];
+
+// The unique ID of the current context (cuCtxGetId: never reused within the
+// process, unlike the context handle), or 0 when it cannot be read.
+unsigned long long current_context_id() {
+  static ctx_get_current_fn get_current = nullptr;
+  static ctx_get_id_fn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<ctx_get_current_fn>(p);
+    else
+      cudaGetLastError();
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<ctx_get_id_fn>(p);
+    else
+      cudaGetLastError();
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// With device `dev` current: the device address of the scratch array and the
+// SM count, looked up once per device and again whenever the current
+// context is not the one the stored address was taken in.
 int setup_device(int dev, void **addr, int *num_sms) {
   if (dev < 0 || dev >= kMaxDevices) return RNNLS_EUNSUPPORTED;
+  unsigned long long id = current_context_id();  // 0 also when no context is bound to the thread yet
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  device_setup &su = g_setup[dev];
+  if (id == 0 || su.ctx_id != id || !su.addr) {
+    // the lookup binds the runtime's context of `dev` to this thread if needed
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
       cudaGetLastError();
       return RNNLS_ECUDA;
     }
+    id = current_context_id();
+    if (id == 0) return RNNLS_ECUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
       cudaGetLastError();
       return RNNLS_ECUDA;
     }
-    g_num_sms[dev] = sms;
-    g_scratch_addr[dev] = p;
+    su.ctx_id = id;
+    su.addr = p;
+    su.num_sms = sms;
   }
-  *addr = g_scratch_addr[dev];
-  *num_sms = g_num_sms[dev];
+  *addr = su.addr;
+  *num_sms = su.num_sms;
   return RNNLS_OK;
 }
 
