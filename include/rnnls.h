@@ -227,9 +227,9 @@ int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double 
  * (pivot^2 <= 1e-13 Q_tt) is rejected for that selection; interpolate with
  * alpha = min x_j/(x_j - z_j) (ties to the smallest j) and drop x_j <= 0;
  * caps 3d additions and 30d interpolation solves (EMAXITER).
- * Q = SA'SA and q = SA'Sb are formed with products exact and sums
- * compensated (about 2^-44 relative), the Lawson-Hanson decisions use
- * passive solves refined to that accuracy.  Requires 1 <= d <= 1024 (for d
+ * Q = SA'SA and q = SA'Sb are formed as rnnls_gram forms them (tensor
+ * cores, exact slice products), the Lawson-Hanson decisions use passive
+ * solves refined to that accuracy.  Requires 1 <= d <= 1024 (for d
  * above about 230 the passive-block inverse is kept in the context's
  * workspace instead of shared memory),
  * r >= 1.  A return of RNNLS_OK means the work was enqueued; the solve's
@@ -243,6 +243,26 @@ int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, 
  * Gram is summed in FP64). */
 int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,
                     double *x, rnnls_info *info);
+
+/* Sketch moments of Sec. 3.4 (the quadratic-programming form of the small
+ * problem): Q = X'X for X = [SA | Sb], i.e. Q~ = SA'SA in the leading d x d
+ * block, q~ = SA'Sb in row and column d, ||Sb||^2 at (d, d).
+ * SA: r x d FP32 column-major (ldsa >= r), Sb: r, device.  Q: device FP64,
+ * (d + 1) x (d + 1) row-major (symmetric, every entry written).  colabs:
+ * device FP64, d entries sum_k |SA_kj| (nullable).
+ * Arithmetic: each column j is scaled by the power of two that brings its
+ * largest magnitude into [64, 128) and cut into six 8-bit integer slices
+ * (exact in BF16); the slice products are summed exactly on the tcgen05
+ * tensor cores (FP32 accumulators drained before their integer sums reach
+ * 2^24) and the drained sums are added in float-float arithmetic.  The
+ * error is below about 2^-40 max_k|SA_ki| max_k|SA_kj| per row, plus the
+ * float-float rounding (about 2^-44 relative).  Data must stay in the FP32
+ * exponent range (Gram entries between about 1e-30 and 1e30).  A NaN or
+ * an infinity in a column makes that column's entries of Q NaN.
+ * Errors: EINVAL (null ctx, SA, Sb or Q; r < 1; d < 1; ldsa < r),
+ * EUNSUPPORTED (d > 1024), ENOMEM, ECUDA. */
+int rnnls_gram(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *Q,
+               double *colabs);
 
 /* The small NNLS problems of Alg. 1 step 5 for nrhs targets that share one
  * sketch (rnnls_sketch_multi): X[:, t] = argmin_{x >= 0} ||SA x - SB[:, t]||_2

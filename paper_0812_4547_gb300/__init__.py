@@ -189,6 +189,20 @@ class Context:
         fn(self.handle, SA.data_ptr(), _ld(SA), Sb.data_ptr(), rr, d, x.data_ptr(), info.data_ptr())
         return x, info
 
+    def gram(self, SA, Sb, r: int | None = None, Q=None, colabs=None):
+        """Sketch moments Q = [SA | Sb]'[SA | Sb] ((d+1) x (d+1), FP64) and the
+        column 1-norms of SA; returns (Q, colabs), device tensors."""
+        torch = _torch()
+        SA = colmajor(SA)
+        rr = SA.shape[0] if r is None else r
+        d = SA.shape[1]
+        if Q is None:
+            Q = torch.empty((d + 1, d + 1), dtype=torch.float64, device=SA.device)
+        if colabs is None:
+            colabs = torch.empty(d, dtype=torch.float64, device=SA.device)
+        B.rnnls_gram(self.handle, SA.data_ptr(), _ld(SA), Sb.data_ptr(), rr, d, Q.data_ptr(), colabs.data_ptr())
+        return Q, colabs
+
     def solve_batched(self, problems):
         """problems: list of (SA, Sb, x, info) tensors; FP32 sketches."""
         descs = []

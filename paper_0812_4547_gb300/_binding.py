@@ -31,7 +31,7 @@ EXPORTS = (
     "rnnls_create", "rnnls_destroy", "rnnls_set_stream", "rnnls_sketch", "rnnls_sketch_f64", "rnnls_solve",
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
-    "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted", "rnnls_set_plan_event",
+    "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted", "rnnls_set_plan_event", "rnnls_gram",
 )
 
 
@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_solve_f64.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_batched.argtypes = [P, ctypes.POINTER(rnnls_problem), I64, U32]
         L.rnnls_solve_multi.argtypes = [P, P, I64, P, I64, I64, I64, I64, P, I64, P]
+        L.rnnls_gram.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_sketch_batched.argtypes = [P, ctypes.POINTER(rnnls_sketch_job), I64]
         L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_boosted.argtypes = [P, P, I64, P, I64, I64, I64, U64, U64, I32, P, P, P, P]
@@ -213,6 +214,11 @@ def rnnls_solve_f64(ctx, SA, ldsa, Sb, r, d, x, info) -> None:
 def rnnls_sketch_batched(ctx, jobs) -> None:
     arr = (rnnls_sketch_job * len(jobs))(*jobs)
     check(lib().rnnls_sketch_batched(ctypes.c_void_p(ctx), arr, len(jobs)), "rnnls_sketch_batched")
+
+
+def rnnls_gram(ctx, SA, ldsa, Sb, r, d, Q, colabs) -> None:
+    check(lib().rnnls_gram(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
+                           ctypes.c_void_p(Q), ctypes.c_void_p(colabs)), "rnnls_gram")
 
 
 def rnnls_solve_multi(ctx, SA, ldsa, SB, ldsb, r, d, nrhs, X, ldx, infos) -> None:

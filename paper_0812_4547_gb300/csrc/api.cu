@@ -78,7 +78,8 @@ int ensure_pinned(rnnls_ctx *ctx, size_t bytes) {
 const char *kernel_name(int kid) {
   static const char *names[K_COUNT] = {"sample_rows", "build_plan", "sketch_srht_f32", "sketch_small",
                                        "reduce_partials", "sketch_f64", "gram", "gram_reduce", "colabs",
-                                       "lawson_hanson", "residual", "boost_residual", "boost_select"};
+                                       "lawson_hanson", "residual", "boost_residual", "boost_select",
+                                       "colstats", "gram_tc"};
   return (kid >= 0 && kid < K_COUNT) ? names[kid] : "?";
 }
 
@@ -527,6 +528,15 @@ int rnnls_solve(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, 
   device_guard dg;
   RNNLS_CUDA_TRY(dg.set(ctx->device));
   return solve_f32(ctx, SA, ldsa, Sb, r, d, x, info);
+}
+
+int rnnls_gram(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *Q,
+               double *colabs) {
+  if (!ctx || !SA || !Sb || !Q || r < 1 || d < 1 || ldsa < r) return RNNLS_EINVAL;
+  if (d > kMaxSolveD) return RNNLS_EUNSUPPORTED;
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
+  return gram_f32(ctx, SA, ldsa, Sb, r, d, Q, colabs);
 }
 
 int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,

@@ -228,6 +228,8 @@ enum kernel_id {
   K_RESIDUAL,
   K_BOOST_RES,
   K_BOOST_SEL,
+  K_COLSTATS,
+  K_GRAM_TC,
   K_COUNT
 };
 const char *kernel_name(int kid);

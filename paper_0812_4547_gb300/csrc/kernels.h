@@ -109,6 +109,70 @@ struct sketch_args_f64 {
 };
 int sketch_f64(rnnls_ctx *ctx, const sketch_args_f64 &a);
 
+// ---- tensor-core Gram (gram_tc.cu) --------------------------------------------
+// Q = X'X for X = [S | s_0 .. s_{nb-1}] (m rows, c = d + nb columns), exact
+// to about 2^-40 of the column maxima's products per row, written as FP64
+// (Qd) and float pairs (Qhi + Qlo), c x c row-major, plus colabs[g] =
+// sum_k |S_kg| for g < d.  multi = 1: products between two different target
+// columns are not needed (tiles holding none of them and no diagonal entry
+// are skipped).
+constexpr int kGramTileM = 128;
+constexpr int kGramTileN = 64;
+struct gram_tc_job {
+  const float *S, *s;
+  int64_t lds, ldt, m;
+  int d, nb, c, multi;
+  int tiles, splits, vec4;
+  int64_t chunks_per_split;  // 32-row chunks per K-split
+  float *colscale;           // [2c] the two factors of 2^(7 - E_g)
+  float *colunscale;         // [c] 2^(E_g - 7)
+  double *part;              // [splits][tiles][128 * 64] partial tiles (splits > 1)
+  unsigned int *counters;    // [tiles] zeroed completion counters
+  double *Qd;
+  float *Qhi, *Qlo;
+  double *colabs;
+};
+// Tile (mt, nt) = rows 128 mt.., columns 64 nt.. of Q; kept when it holds an
+// entry on or above the diagonal (and, with multi, a row of S or a diagonal
+// entry).
+__host__ __device__ inline bool gram_tc_tile_needed(int mt, int nt, int c, int d, int multi) {
+  const int i0 = mt * kGramTileM, j0 = nt * kGramTileN;
+  if (i0 >= c || j0 >= c) return false;
+  const int i1 = i0 + kGramTileM < c ? i0 + kGramTileM : c;
+  const int j1 = j0 + kGramTileN < c ? j0 + kGramTileN : c;
+  if (j1 - 1 < i0) return false;
+  if (multi && i0 >= d) return j0 < i1 && j1 > i0;
+  return true;
+}
+__host__ __device__ inline void gram_tc_tile_at(int t, int c, int d, int multi, int &mt, int &nt) {
+  for (int a = 0; a * kGramTileM < c; ++a)
+    for (int b = 0; b * kGramTileN < c; ++b)
+      if (gram_tc_tile_needed(a, b, c, d, multi)) {
+        if (t == 0) {
+          mt = a;
+          nt = b;
+          return;
+        }
+        --t;
+      }
+  mt = nt = 0;
+}
+int gram_tc_tile_count(int c, int d, int multi);
+// Tiles and K-splits of one problem: about want_ctas CTAs, at most
+// max_chunks_per_cta chunks of 32 rows each (pointers left for gram_tc_carve).
+gram_tc_job gram_tc_plan(const float *S, int64_t lds, const float *s, int64_t ldt, int nb, int64_t m, int d,
+                         int multi, int want_ctas, int64_t max_chunks_per_cta);
+size_t gram_tc_ws_bytes(const gram_tc_job &j);
+void gram_tc_carve(gram_tc_job &j, ws_carver &wc, unsigned int *counters, double *Qd, float *Qhi, float *Qlo,
+                   double *colabs);
+// column statistics, then the Gram (two launches)
+int gram_tc_launch_one(rnnls_ctx *ctx, const gram_tc_job &j);
+int gram_tc_launch_batched(rnnls_ctx *ctx, const gram_tc_job *d_jobs, const int64_t *d_first_col,
+                           const int64_t *d_first_cta, int count, int64_t cols, int64_t ctas);
+// rnnls_gram: Q (FP64, (d+1) x (d+1)) and colabs (nullable) into caller buffers
+int gram_f32(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *Q,
+             double *colabs);
+
 // ---- solve (solve.cu) ----------------------------------------------------------
 int solve_f32(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
               rnnls_info *info);

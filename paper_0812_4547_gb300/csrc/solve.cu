@@ -4,8 +4,9 @@
 // Definition 1.
 //
 // Precision plan for GB300 (whose FP64 rate is a small fraction of FP32):
-//   - Gram: products of FP32 entries are exact as float pairs (FMA), sums
-//     are compensated (Ogita-Rump-Oishi Dot2), partial sums combined in FP64.
+//   - Gram of FP32 sketches: on the tensor cores from an exact split of
+//     every column into six 8-bit slices (gram_tc.cu); of FP64 sketches:
+//     plain FP64 sums.
 //   - Lawson-Hanson: an FP32 inverse of the equilibrated passive block
 //     D Q_PP D (D = diag(Q)^-1/2) is kept up to date by bordering (adding a
 //     column) and Schur-complement downdates (dropping one); every passive
@@ -32,7 +33,8 @@ constexpr int kGT = 32;         // Gram tile
 constexpr int kLHThreads = RNNLS_LH_THREADS;  // Lawson-Hanson block
 
 // ---------------------------------------------------------------------------
-// Gram of X = [S | s] (m x (d+1)) in tiles of 32 x 32, split over rows.
+// FP64 Gram of X = [S | s] (m x (d+1)) in tiles of 32 x 32, split over rows
+// (the FP32 Gram runs on the tensor cores, gram_tc.cu).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void tile_coords(int t, int T, int &ti, int &tj) {
   ti = 0;
@@ -47,52 +49,6 @@ template <typename T>
 __device__ __forceinline__ const T *gram_col(const T *S, int64_t lds, const T *s, int d, int g) {
   return (g < d) ? S + (int64_t)g * lds : (g == d ? s : nullptr);
 }
-// column g of [S | s_0 .. s_{nb-1}] (targets with leading dimension ldt)
-// ---- packed f32x2 Dot2 step (two lanes per instruction) ----------------------
-__device__ __forceinline__ void unpack_f2(unsigned long long r, float &a, float &b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
-                                                     unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-// (s, c) += a * b on two lanes with the roundings of dot2::add_prod:
-// aa = (a, a), b = (b0, b1), nb = (-b0, -b1).  pn = -fl(a b) exactly, so
-// fma(a, b, pn) is TwoProduct's error, s - pn is s + p, and
-// -(pn + bb) is p - bb (negation commutes with round-to-nearest).
-__device__ __forceinline__ void dot2_add_prod_x2(unsigned long long &s, unsigned long long &c, unsigned long long aa,
-                                                 unsigned long long b, unsigned long long nb) {
-  const unsigned long long pn = f2_mul(aa, nb);
-  const unsigned long long e = f2_fma(aa, b, pn);
-  const unsigned long long s1 = f2_sub(s, pn);
-  const unsigned long long bb = f2_sub(s1, s);
-  const unsigned long long err = f2_sub(f2_sub(s, f2_sub(s1, bb)), f2_add(pn, bb));
-  s = s1;
-  c = f2_add(c, f2_add(err, e));
-}
-
-__device__ __forceinline__ const float *gram_col_nb(const float *S, int64_t lds, const float *s, int64_t ldt, int d,
-                                                    int nb, int g) {
-  return (g < d) ? S + (int64_t)g * lds : (g < d + nb ? s + (int64_t)(g - d) * ldt : nullptr);
-}
-
 __global__ void __launch_bounds__(256) gram_f64_kernel(const double *__restrict__ S, int64_t lds,
                                                        const double *__restrict__ s, int64_t m, int d, int T,
                                                        int64_t rows_per_split, double *__restrict__ part) {
@@ -158,194 +114,6 @@ __global__ void gram_reduce_kernel(const double *__restrict__ part, int splits, 
     Qlo[(int64_t)i * D1 + j] = l;
     Qlo[(int64_t)j * D1 + i] = l;
   }
-}
-
-// Gram, split reduction and column 1-norms in one launch.  Every block
-// writes its split's partial tile (and, on diagonal tiles, the partial
-// |.|-sums of its columns); the last block to finish a tile (counter per
-// tile, reset by that block) adds the splits in order 0..splits-1 and writes
-// Q as FP64 and as float pairs, plus the column 1-norms.
-__device__ __forceinline__ void gram_fused_block(int tile, int split, int splits, const float *__restrict__ S,
-                                                 int64_t lds, const float *__restrict__ s, int64_t ldt, int nb,
-                                                 int64_t m, int d, int T,
-                                                             int64_t rows_per_split, double *__restrict__ part,
-                                                             double *__restrict__ part_abs,
-                                                             unsigned int *__restrict__ counters,
-                                                             double *__restrict__ Qd, float *__restrict__ Qhi,
-                                                             float *__restrict__ Qlo, double *__restrict__ colabs) {
-  // Xi as duplicated pairs (a, a); Xj and its negation as pairs of
-  // neighbouring columns (rows padded to an even length for 8-byte loads)
-  __shared__ float2 Xi2[kGT][kGT + 1];
-  __shared__ __align__(8) float Xj[kGT][kGT + 2];
-  __shared__ __align__(8) float Xn[kGT][kGT + 2];
-  __shared__ unsigned int last_flag;
-  (void)splits;
-  int ti, tj;
-  tile_coords(tile, T, ti, tj);
-  // target-by-target products are needed on the diagonal only
-  if (ti != tj && ti * kGT >= d) return;
-  const int ntiles = T * (T + 1) / 2;
-  const int64_t k0 = (int64_t)split * rows_per_split;
-  const int64_t k1 = min(m, k0 + rows_per_split);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const bool diag = (ti == tj);
-  // Dot2 sums of the thread's 2 x 2 outputs, row a's two columns as one
-  // packed pair: s[a] = (s_a0, s_a1), c[a] likewise
-  unsigned long long sp[2] = {0ull, 0ull}, cp[2] = {0ull, 0ull};
-  dot2 absacc[4];
-  // this thread's four (row, column) positions of a stage; the next stage's
-  // values are loaded while the current one is multiplied
-  const float *ci[4], *cj[4];
-  int kq[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int e = threadIdx.x + 256 * q;
-    kq[q] = e & 31;
-    ci[q] = gram_col_nb(S, lds, s, ldt, d, nb, ti * kGT + (e >> 5));
-    cj[q] = gram_col_nb(S, lds, s, ldt, d, nb, tj * kGT + (e >> 5));
-  }
-  float vi[4], vj[4];
-  auto fetch = [&](int64_t kb) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t k = kb + kq[q];
-      vi[q] = (ci[q] && k < k1) ? ci[q][k] : 0.0f;
-      vj[q] = (cj[q] && k < k1) ? cj[q][k] : 0.0f;
-    }
-  };
-  if (k0 < k1) fetch(k0);
-  for (int64_t kb = k0; kb < k1; kb += kGT) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int kk = kq[q], cc = (threadIdx.x + 256 * q) >> 5;
-      Xi2[kk][cc] = make_float2(vi[q], vi[q]);
-      Xj[kk][cc] = vj[q];
-      Xn[kk][cc] = -vj[q];
-      if (diag) absacc[q].add(fabsf(vi[q]));
-    }
-    __syncthreads();
-    if (kb + kGT < k1) fetch(kb + kGT);
-#pragma unroll 8
-    for (int kk = 0; kk < kGT; ++kk) {
-      const unsigned long long b = *reinterpret_cast<const unsigned long long *>(&Xj[kk][2 * tx]);
-      const unsigned long long nbv = *reinterpret_cast<const unsigned long long *>(&Xn[kk][2 * tx]);
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const unsigned long long aa = *reinterpret_cast<const unsigned long long *>(&Xi2[kk][2 * ty + a]);
-        dot2_add_prod_x2(sp[a], cp[a], aa, b, nbv);
-      }
-    }
-    __syncthreads();
-  }
-  double *out = part + ((int64_t)split * ntiles + tile) * (kGT * kGT);
-#pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    float s0, s1, c0, c1;
-    unpack_f2(sp[a], s0, s1);
-    unpack_f2(cp[a], c0, c1);
-    const ff v0 = fast_two_sum(s0, c0), v1 = fast_two_sum(s1, c1);
-    out[(2 * ty + a) * kGT + 2 * tx] = (double)v0.hi + (double)v0.lo;
-    out[(2 * ty + a) * kGT + 2 * tx + 1] = (double)v1.hi + (double)v1.lo;
-  }
-  if (diag) {
-    // column ti*32 + (warp + 8q): the 32 lanes of a warp hold 32 rows of it
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const ff v = absacc[q].value();
-      double t = (double)v.hi + (double)v.lo;
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if ((threadIdx.x & 31) == 0) part_abs[(int64_t)split * (T * kGT) + ti * kGT + (threadIdx.x >> 5) + 8 * q] = t;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned int done = atomicAdd(&counters[tile], 1u);
-    last_flag = (done == (unsigned int)(splits - 1)) ? 1u : 0u;
-  }
-  __syncthreads();
-  if (!last_flag) return;
-  __threadfence();
-  const int D1 = d + nb;
-  // fixed order sp = 0..splits-1; the thread's four positions in flight per sp
-  double v4[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int sp = 0; sp < splits; ++sp) {
-    const double *src = part + ((int64_t)sp * ntiles + tile) * (kGT * kGT);
-    double t4[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) t4[u] = __ldcg(src + threadIdx.x + 256 * u);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v4[u] += t4[u];
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int pos = threadIdx.x + 256 * u;
-    const int i = ti * kGT + pos / kGT, j = tj * kGT + pos % kGT;
-    if (i >= D1 || j >= D1 || i > j) continue;
-    const double v = v4[u];
-    const float h = (float)v;
-    const float l = (float)(v - (double)h);
-    Qd[(int64_t)i * D1 + j] = v;
-    Qd[(int64_t)j * D1 + i] = v;
-    Qhi[(int64_t)i * D1 + j] = h;
-    Qhi[(int64_t)j * D1 + i] = h;
-    Qlo[(int64_t)i * D1 + j] = l;
-    Qlo[(int64_t)j * D1 + i] = l;
-  }
-  if (diag) {
-    for (int c = threadIdx.x; c < kGT; c += blockDim.x) {
-      const int col = ti * kGT + c;
-      if (col >= d) continue;
-      double v = 0.0;
-      for (int sp = 0; sp < splits; ++sp) v += __ldcg(part_abs + (int64_t)sp * (T * kGT) + col);
-      colabs[col] = v;
-    }
-  }
-  if (threadIdx.x == 0) counters[tile] = 0u;
-}
-
-// SHARE = 1: the one-problem launch, whose blocks may share SMs with a
-// concurrent sketch (it gets its own carveout attribute); SHARE = 0: the
-// multi-target launch.
-template <int SHARE>
-__global__ void __launch_bounds__(256) gram_fused_f32_kernel(const float *__restrict__ S, int64_t lds,
-                                                             const float *__restrict__ s, int64_t ldt, int nb,
-                                                             int64_t m, int d, int T, int64_t rows_per_split,
-                                                             double *__restrict__ part, double *__restrict__ part_abs,
-                                                             unsigned int *__restrict__ counters,
-                                                             double *__restrict__ Qd, float *__restrict__ Qhi,
-                                                             float *__restrict__ Qlo, double *__restrict__ colabs) {
-  gram_fused_block((int)blockIdx.x, (int)blockIdx.y, (int)gridDim.y, S, lds, s, ldt, nb, m, d, T, rows_per_split, part,
-                   part_abs, counters, Qd, Qhi, Qlo, colabs);
-}
-
-// Many problems' Grams in one launch: block b belongs to the problem p with
-// first[p] <= b < first[p + 1] (tiles x splits blocks each).
-struct gram_job {
-  const float *S;
-  const float *s;
-  int64_t lds, m, rows_per_split;
-  int d, T, ntiles, splits;
-  double *part, *part_abs, *Qd, *colabs;
-  float *Qhi, *Qlo;
-  unsigned int *counters;
-};
-
-__global__ void __launch_bounds__(256) gram_batched_f32_kernel(const gram_job *__restrict__ jobs,
-                                                               const int64_t *__restrict__ first, int count) {
-  int lo = 0, hi = count - 1;
-  const int64_t bid = blockIdx.x;
-  while (lo < hi) {  // last p with first[p] <= bid
-    const int mid = (lo + hi + 1) >> 1;
-    if (first[mid] <= bid)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  const gram_job jb = jobs[lo];
-  const int64_t local = bid - first[lo];
-  gram_fused_block((int)(local % jb.ntiles), (int)(local / jb.ntiles), jb.splits, jb.S, jb.lds, jb.s, jb.m, 1, jb.m,
-                   jb.d, jb.T, jb.rows_per_split, jb.part, jb.part_abs, jb.counters, jb.Qd, jb.Qhi, jb.Qlo, jb.colabs);
 }
 
 // ||S||_1 = max_j sum_k |S_kj| (compensated), one warp per column.
@@ -1190,20 +958,6 @@ __global__ void sum_partials_kernel(const double *__restrict__ partial, int nb, 
   }
 }
 
-// The one-problem FP32 Gram asks for the largest shared-memory carveout, so
-// that its blocks can run on SMs that also hold a sketch block (about 200 KiB)
-// when solves overlap the next sketch.  (Not the multi-target and batched
-// Grams: a following Lawson-Hanson launch that reads Q from global memory
-// needs the L1 share; a function's carveout is per function, hence the
-// separate instantiation.)
-void gram_carveout_once() {
-  static once_per_device carve;
-  carve.run([] {
-    return cudaFuncSetAttribute(gram_fused_f32_kernel<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                (int)cudaSharedmemCarveoutMaxShared);
-  });
-}
-
 struct gram_plan {
   int T, ntiles, splits;
   int64_t rows_per_split;
@@ -1279,38 +1033,49 @@ int lh_launch_one(rnnls_ctx *ctx, const lh_job &jb) {
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 
+// One problem: the FP32 Gram on the tensor cores (column statistics, then
+// the exact sliced products), the FP64 Gram as a plain two-pass reduction.
 template <typename T>
 int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r, int64_t d, double *x,
               rnnls_info *info) {
-  const gram_plan g = plan_gram(r, (int)d, ctx->num_sms);
   const bool fits = lh_q_fits(ctx, (int)d);
-  const size_t bytes = solve_ws_bytes(g, (int)d, 1) + lh_bg_bytes(ctx, (int)d);
-  int st = ensure_workspace(ctx, bytes);
-  if (st) return st;
-  ws_carver wc(ctx->ws);
-  solve_ws w;
   const size_t D1 = d + 1;
-  w.part = wc.take<double>((size_t)g.splits * g.ntiles * kGT * kGT);
-  w.Qd = wc.take<double>(D1 * D1);
-  w.Qhi = wc.take<float>(D1 * D1);
-  w.Qlo = wc.take<float>(D1 * D1);
-  w.colabs = wc.take<double>((size_t)d);
-  w.part_abs = wc.take<double>((size_t)g.splits * g.T * kGT);
-  float *Bg = lh_b_fits(ctx, (int)d) ? nullptr : wc.take<float>((size_t)odd_ld((int)d) * d);
   cudaStream_t s = ctx->stream;
-  dim3 grid((unsigned)g.ntiles, (unsigned)g.splits);
+  int st = RNNLS_OK;
+  solve_ws w;
+  float *Bg = nullptr;
   if (sizeof(T) == 4) {
-    unsigned int *counters = nullptr;
-    st = ensure_counters(ctx, (size_t)g.ntiles, &counters);
+    gram_tc_job gj = gram_tc_plan((const float *)SA, ldsa, (const float *)Sb, r, 1, r, (int)d, 0, ctx->num_sms,
+                                  (int64_t)1 << 40);
+    const size_t bytes = align_up(D1 * D1 * 8, 256) + 2 * align_up(D1 * D1 * 4, 256) + align_up((size_t)d * 8, 256) +
+                         gram_tc_ws_bytes(gj) + lh_bg_bytes(ctx, (int)d) + 1024;
+    st = ensure_workspace(ctx, bytes);
     if (st) return st;
-    prof_scope ps(ctx, K_GRAM);
-    // Q held in the Lawson-Hanson block's shared memory: the following solve
-    // does not lean on L1, so the Gram may take the shared-SM carveout
-    auto kern = fits ? gram_fused_f32_kernel<1> : gram_fused_f32_kernel<0>;
-    if (fits) gram_carveout_once();
-    kern<<<grid, 256, 0, s>>>((const float *)SA, ldsa, (const float *)Sb, r, 1, r, (int)d, g.T, g.rows_per_split,
-                              w.part, w.part_abs, counters, w.Qd, w.Qhi, w.Qlo, w.colabs);
+    unsigned int *counters = nullptr;
+    st = ensure_counters(ctx, (size_t)gj.tiles, &counters);
+    if (st) return st;
+    ws_carver wc(ctx->ws);
+    w.Qd = wc.take<double>(D1 * D1);
+    w.Qhi = wc.take<float>(D1 * D1);
+    w.Qlo = wc.take<float>(D1 * D1);
+    w.colabs = wc.take<double>((size_t)d);
+    gram_tc_carve(gj, wc, counters, w.Qd, w.Qhi, w.Qlo, w.colabs);
+    Bg = lh_b_fits(ctx, (int)d) ? nullptr : wc.take<float>((size_t)odd_ld((int)d) * d);
+    st = gram_tc_launch_one(ctx, gj);
+    if (st) return st;
   } else {
+    const gram_plan g = plan_gram(r, (int)d, ctx->num_sms);
+    const size_t bytes = solve_ws_bytes(g, (int)d, 1) + lh_bg_bytes(ctx, (int)d);
+    st = ensure_workspace(ctx, bytes);
+    if (st) return st;
+    ws_carver wc(ctx->ws);
+    w.part = wc.take<double>((size_t)g.splits * g.ntiles * kGT * kGT);
+    w.Qd = wc.take<double>(D1 * D1);
+    w.Qhi = wc.take<float>(D1 * D1);
+    w.Qlo = wc.take<float>(D1 * D1);
+    w.colabs = wc.take<double>((size_t)d);
+    Bg = lh_b_fits(ctx, (int)d) ? nullptr : wc.take<float>((size_t)odd_ld((int)d) * d);
+    dim3 grid((unsigned)g.ntiles, (unsigned)g.splits);
     {
       prof_scope ps(ctx, K_GRAM);
       gram_f64_kernel<<<grid, 256, 0, s>>>((const double *)SA, ldsa, (const double *)Sb, r, (int)d, g.T,
@@ -1355,21 +1120,29 @@ int solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, 
   return solve_one<double>(ctx, SA, ldsa, Sb, r, d, x, info);
 }
 
+// Maximum 32-row chunks per Gram CTA in a batched launch (4096 rows), so
+// that the CTAs of a batch of uneven problems carry comparable work.
+constexpr int64_t kBatchChunksPerCta = 128;
+
 int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
-  // one launch for every problem's Gram, then one Lawson-Hanson launch over all
-  std::vector<gram_plan> plans((size_t)count);
-  const size_t tbytes = align_up((size_t)count * sizeof(gram_job), 256) +
-                        align_up((size_t)(count + 1) * sizeof(int64_t), 256) +
-                        align_up((size_t)count * sizeof(lh_job), 256);
+  // one launch for every problem's column statistics, one for every Gram,
+  // then one Lawson-Hanson launch over all
+  std::vector<gram_tc_job> gjs((size_t)count);
+  const size_t tab_jobs = align_up((size_t)count * sizeof(gram_tc_job), 256);
+  const size_t tab_first = align_up((size_t)(count + 1) * sizeof(int64_t), 256);
+  const size_t tbytes = tab_jobs + 2 * tab_first + align_up((size_t)count * sizeof(lh_job), 256);
   size_t bytes = tbytes + 256;
   size_t smem = 0;
   int64_t tiles = 0;
   for (int64_t i = 0; i < count; ++i) {
-    const int di = (int)probs[i].d;
-    plans[(size_t)i] = plan_gram(probs[i].r, di, std::max(1, ctx->num_sms / 2));
-    bytes += solve_ws_bytes(plans[(size_t)i], di, 0) + lh_bg_bytes(ctx, di);
+    const rnnls_problem &pb = probs[i];
+    const int di = (int)pb.d;
+    gjs[(size_t)i] = gram_tc_plan(pb.SA, pb.ldsa, pb.Sb, pb.r, 1, pb.r, di, 0, 1, kBatchChunksPerCta);
+    const size_t D1 = di + 1;
+    bytes += align_up(D1 * D1 * 8, 256) + 2 * align_up(D1 * D1 * 4, 256) + align_up((size_t)di * 8, 256) +
+             gram_tc_ws_bytes(gjs[(size_t)i]) + lh_bg_bytes(ctx, di) + 1024;
     smem = std::max(smem, lh_smem_for(ctx, di));
-    tiles += plans[(size_t)i].ntiles;
+    tiles += gjs[(size_t)i].tiles;
   }
   int st = ensure_workspace(ctx, bytes);
   if (st) return st;
@@ -1381,42 +1154,33 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   ws_carver wc(ctx->ws);
   char *d_tables = wc.take<char>(tbytes);
   char *h_tables = (char *)ctx->pinned;
-  gram_job *gj = (gram_job *)h_tables;
-  int64_t *first = (int64_t *)(h_tables + align_up((size_t)count * sizeof(gram_job), 256));
-  lh_job *jobs = (lh_job *)(h_tables + align_up((size_t)count * sizeof(gram_job), 256) +
-                            align_up((size_t)(count + 1) * sizeof(int64_t), 256));
-  int64_t blocks = 0;
+  gram_tc_job *gj = (gram_tc_job *)h_tables;
+  int64_t *first_col = (int64_t *)(h_tables + tab_jobs);
+  int64_t *first_cta = (int64_t *)(h_tables + tab_jobs + tab_first);
+  lh_job *jobs = (lh_job *)(h_tables + tab_jobs + 2 * tab_first);
+  int64_t ctas = 0, cols = 0;
   for (int64_t i = 0; i < count; ++i) {
     const rnnls_problem &pb = probs[i];
-    const gram_plan &g = plans[(size_t)i];
     const size_t D1 = pb.d + 1;
-    gram_job &q = gj[i];
-    q.S = pb.SA;
-    q.s = pb.Sb;
-    q.lds = pb.ldsa;
-    q.m = pb.r;
-    q.rows_per_split = g.rows_per_split;
-    q.d = (int)pb.d;
-    q.T = g.T;
-    q.ntiles = g.ntiles;
-    q.splits = g.splits;
-    q.part = wc.take<double>((size_t)g.splits * g.ntiles * kGT * kGT);
-    q.part_abs = wc.take<double>((size_t)g.splits * g.T * kGT);
-    q.Qd = wc.take<double>(D1 * D1);
-    q.Qhi = wc.take<float>(D1 * D1);
-    q.Qlo = wc.take<float>(D1 * D1);
-    q.colabs = wc.take<double>((size_t)pb.d);
-    q.counters = counters;
-    counters += g.ntiles;
-    first[i] = blocks;
-    blocks += (int64_t)g.ntiles * g.splits;
+    gram_tc_job q = gjs[(size_t)i];
+    double *Qd = wc.take<double>(D1 * D1);
+    float *Qhi = wc.take<float>(D1 * D1);
+    float *Qlo = wc.take<float>(D1 * D1);
+    double *colabs = wc.take<double>((size_t)pb.d);
+    gram_tc_carve(q, wc, counters, Qd, Qhi, Qlo, colabs);
+    counters += q.tiles;
+    gj[i] = q;
+    first_col[i] = cols;
+    cols += q.c;
+    first_cta[i] = ctas;
+    ctas += (int64_t)q.tiles * q.splits;
     lh_job &jb = jobs[i];
-    jb.Qd = q.Qd;
-    jb.Qhi = q.Qhi;
-    jb.Qlo = q.Qlo;
+    jb.Qd = Qd;
+    jb.Qhi = Qhi;
+    jb.Qlo = Qlo;
     jb.ldq = (int)D1;
     jb.qcol = (int)pb.d;
-    jb.colabs = q.colabs;
+    jb.colabs = colabs;
     jb.r = pb.r;
     jb.d = (int)pb.d;
     jb.x = pb.x;
@@ -1424,21 +1188,19 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
     jb.q_smem = lh_q_fits(ctx, (int)pb.d) ? 1 : 0;
     jb.Bg = lh_b_fits(ctx, (int)pb.d) ? nullptr : wc.take<float>((size_t)odd_ld((int)pb.d) * pb.d);
   }
-  first[count] = blocks;
+  first_col[count] = cols;
+  first_cta[count] = ctas;
   cudaStream_t s = ctx->stream;
   // tables staged through the context's pinned buffer (ensure_pinned waited
   // for the previous call's copy out of it)
   RNNLS_CUDA_TRY(cudaMemcpyAsync(d_tables, h_tables, tbytes, cudaMemcpyHostToDevice, s));
   RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
-  const gram_job *d_gj = (const gram_job *)d_tables;
-  const int64_t *d_first = (const int64_t *)(d_tables + align_up((size_t)count * sizeof(gram_job), 256));
-  const lh_job *d_jobs = (const lh_job *)(d_tables + align_up((size_t)count * sizeof(gram_job), 256) +
-                                          align_up((size_t)(count + 1) * sizeof(int64_t), 256));
-  {
-    prof_scope ps(ctx, K_GRAM);
-    gram_batched_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_gj, d_first, (int)count);
-  }
-  if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
+  const gram_tc_job *d_gj = (const gram_tc_job *)d_tables;
+  const int64_t *d_first_col = (const int64_t *)(d_tables + tab_jobs);
+  const int64_t *d_first_cta = (const int64_t *)(d_tables + tab_jobs + tab_first);
+  const lh_job *d_jobs = (const lh_job *)(d_tables + tab_jobs + 2 * tab_first);
+  st = gram_tc_launch_batched(ctx, d_gj, d_first_col, d_first_cta, (int)count, cols, ctas);
+  if (st) return st;
   return lh_launch(ctx, d_jobs, count, smem);
 }
 
@@ -1447,31 +1209,27 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
   // one Gram of [SA | SB] (the target-by-target block only on its diagonal),
   // then one Lawson-Hanson block per target, all reading the same Q
   const int64_t D1 = d + nrhs;
-  const gram_plan g = plan_gram(r, (int)(D1 - 1), ctx->num_sms);
+  gram_tc_job gj = gram_tc_plan(SA, ldsa, SB, ldsb, (int)nrhs, r, (int)d, 1, ctx->num_sms, (int64_t)1 << 40);
   const bool bfit = lh_b_fits(ctx, (int)d);
-  const size_t bytes = solve_ws_bytes(g, (int)(D1 - 1), nrhs) + (size_t)nrhs * lh_bg_bytes(ctx, (int)d);
+  const size_t bytes = align_up((size_t)(D1 * D1) * 8, 256) + 2 * align_up((size_t)(D1 * D1) * 4, 256) +
+                       align_up((size_t)D1 * 8, 256) + gram_tc_ws_bytes(gj) +
+                       align_up((size_t)nrhs * sizeof(lh_job), 256) + (size_t)nrhs * lh_bg_bytes(ctx, (int)d) + 1024;
   int st = ensure_workspace(ctx, bytes);
+  if (st) return st;
+  unsigned int *counters = nullptr;
+  st = ensure_counters(ctx, (size_t)gj.tiles, &counters);
   if (st) return st;
   ws_carver wc(ctx->ws);
   solve_ws w;
-  w.part = wc.take<double>((size_t)g.splits * g.ntiles * kGT * kGT);
   w.Qd = wc.take<double>((size_t)(D1 * D1));
   w.Qhi = wc.take<float>((size_t)(D1 * D1));
   w.Qlo = wc.take<float>((size_t)(D1 * D1));
   w.colabs = wc.take<double>((size_t)D1);
-  w.part_abs = wc.take<double>((size_t)g.splits * g.T * kGT);
+  gram_tc_carve(gj, wc, counters, w.Qd, w.Qhi, w.Qlo, w.colabs);
   lh_job *d_jobs = wc.take<lh_job>((size_t)nrhs);
   cudaStream_t s = ctx->stream;
-  unsigned int *counters = nullptr;
-  st = ensure_counters(ctx, (size_t)g.ntiles, &counters);
+  st = gram_tc_launch_one(ctx, gj);
   if (st) return st;
-  {
-    prof_scope ps(ctx, K_GRAM);
-    dim3 grid((unsigned)g.ntiles, (unsigned)g.splits);
-    gram_fused_f32_kernel<0><<<grid, 256, 0, s>>>(SA, ldsa, SB, ldsb, (int)nrhs, r, (int)d, g.T, g.rows_per_split, w.part,
-                                               w.part_abs, counters, w.Qd, w.Qhi, w.Qlo, w.colabs);
-  }
-  if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
   std::vector<lh_job> jobs((size_t)nrhs);
   for (int64_t t = 0; t < nrhs; ++t) {
     lh_job &jb = jobs[(size_t)t];
