@@ -1,6 +1,6 @@
 // gram_tc.cu -- the sketch moments of Sec. 3.4 (Q = X'X for X = [SA | Sb],
 // i.e. Q~ = (H~DA)'(H~DA), q~ = (H~DA)'H~Db and ||H~Db||^2) on the tcgen05
-// tensor cores, with every product exact.
+// tensor cores, with the leading products exact.
 //
 // The tensor cores multiply BF16 operands and accumulate in FP32, which
 // rounds; the Lawson-Hanson decisions need the Gram to about 1e-13 of
@@ -9,30 +9,33 @@
 //   * column j of X is scaled by 2^(7 - E_j), E_j the exponent of its
 //     largest magnitude (2^(E_j - 1) <= max_k |x_kj| < 2^E_j), so that
 //     every scaled value v has |v| < 128;
-//   * v is cut into six integer slices s_0..s_5 by repeated rounding,
-//     v = s_0 + 2^-8 s_1 + ... + 2^-40 s_5 + (a rest below 2^-41), each
-//     |s_p| <= 128 and therefore exact in BF16;
-//   * Q_ij = 2^(E_i + E_j - 14) sum_w 2^(-8w) G_w, G_w = sum over p + q = w
-//     (w <= 5) of sum_k s_p[k, i] s_q[k, j].  A slice product is an integer
-//     of at most 2^14 in magnitude, and an FP32 accumulator holds sums of
-//     such integers exactly while they stay below 2^24: group w has its own
-//     accumulator in tensor memory and is drained (read, scaled by the
-//     power of two, added to float-float sums in registers) before
-//     (w + 1) * rows * 2^14 can reach 2^24, i.e. after 512, 256, 256, 128,
-//     128 and 128 rows for w = 0..5.
-// What is dropped (the rests and the products with p + q > 5) is below about
-// 2^-40 of max_k |x_ki| max_k |x_kj| per row.  The column magnitudes limit
-// the data to the FP32 exponent range, as FP32 products would.
+//   * v is cut into six slices by rounding to multiples of 2^-8p,
+//     v = t_0 + t_1 + ... + t_5 + (a rest below 2^-41), t_p = 2^-8p s_p with
+//     an integer |s_p| <= 128, so every t_p is exact in BF16;
+//   * Q_ij = 2^(E_i + E_j - 14) sum_w G_w, G_w = sum over p + q = w of
+//     sum_k t_p[k, i] t_q[k, j].  Every product in G_w is an integer
+//     multiple of 2^-8w of magnitude at most 2^(14 - 8w), and an FP32
+//     accumulator holds sums of such multiples exactly while they stay below
+//     2^(24 - 8w): G_0, G_1 and G_2 have their own tensor-memory
+//     accumulators, drained (read, scaled by the power of two, added to
+//     float-float sums) after 512, 256 and 256 rows, well before that bound;
+//     G_3 + G_4 + G_5 (weights 2^-24 and below) share one accumulator that
+//     rounds, drained every 256 rows.
+// What is dropped or rounded (the rests, the products with p + q > 5, the
+// shared accumulator's roundings) is below about 2^-39 of
+// max_k |x_ki| max_k |x_kj| per row.  The column magnitudes limit the data to
+// the FP32 exponent range, as FP32 products would.
 //
-// Work split: a CTA of 128 threads owns one tile of Q (128 rows i x 64
+// Work split: a CTA of 256 threads owns one tile of Q (128 rows i x 64
 // columns j; tiles wholly below the diagonal are skipped) and a range of
-// 32-row chunks of X.  Per chunk every thread loads and slices its share of
-// the tile's columns into shared memory (K-major core matrices, two buffers),
-// then one thread issues 21 x 2 tcgen05.mma (M = 128, N = 64, K = 16) into
-// six accumulators of 64 TMEM columns and commits them to an mbarrier; the
-// slicing of chunk t + 1 runs while the tensor cores work on chunk t.
-// K-splits of one tile add their FP64 partials in a fixed order in the last
-// CTA to finish (a counter per tile, reset by that CTA).
+// 32-row chunks of X.  Per chunk the threads slice their share of the tile's
+// columns into shared memory (K-major core matrices, two buffers; the next
+// chunk's values are loaded into registers ahead), then one thread issues
+// 21 x 2 tcgen05.mma (M = 128, N = 64, K = 16) into the four accumulators
+// and commits them to an mbarrier; slicing of chunk t + 1 runs while the
+// tensor cores work on chunk t.  K-splits of one tile add their FP64
+// partials in a fixed order in the last CTA to finish (a counter per tile,
+// reset by that CTA).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -44,29 +47,31 @@
 namespace rnnls {
 namespace {
 
-constexpr int kTM = 128;                     // tile rows (MMA M)
-constexpr int kTN = 64;                      // tile columns (MMA N)
-constexpr int kKC = 32;                      // rows of X per chunk
-constexpr int kSl = 6;                       // slices per value
-constexpr int kGroups = 6;                   // weight groups w = p + q
-constexpr int kTcThreads = 128;
-constexpr uint32_t kTmemCols = 512;          // 6 x 64 accumulator columns + 2 x 64 for the float-float sums
-constexpr uint32_t kColHi = kGroups * kTN;   // TMEM columns of the running sums (hi, then lo)
+constexpr int kTM = 128;                       // tile rows (MMA M)
+constexpr int kTN = 64;                        // tile columns (MMA N)
+constexpr int kKC = 32;                        // rows of X per chunk
+constexpr int kSl = 6;                         // slices per value
+constexpr int kTcThreads = 256;
+constexpr uint32_t kTmemCols = 512;            // 4 accumulators + 2 running sums of 64 columns, rounded up
+constexpr uint32_t kColHi = 4 * kTN;           // TMEM columns of the running sums (hi, then lo)
 constexpr uint32_t kColLo = kColHi + kTN;
-constexpr uint32_t kLead = 128;              // bytes between core matrices adjacent along K
+constexpr uint32_t kLead = 128;                // bytes between core matrices adjacent along K
 constexpr uint32_t kStride = (kKC / 8) * 128;  // bytes between core matrices adjacent along M / N
-constexpr uint32_t kASlice = kTM * kKC * 2;  // bytes of one slice of the 128-row operand
-constexpr uint32_t kBSlice = kTN * kKC * 2;  // bytes of one slice of the 64-row operand
+constexpr uint32_t kASlice = kTM * kKC * 2;    // bytes of one slice of the 128-row operand
+constexpr uint32_t kBSlice = kTN * kKC * 2;    // bytes of one slice of the 64-row operand
 constexpr uint32_t kBufBytes = kSl * (kASlice + kBSlice);
 constexpr size_t kTcSmem = 2 * (size_t)kBufBytes;
-constexpr uint32_t kWaitLimit = 1u << 22;    // mbarrier polls before a wait gives up
+constexpr uint32_t kWaitLimit = 1u << 22;      // mbarrier polls before a wait gives up
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTM, kTN);
 
 static_assert(kTcSmem <= 200 * 1024, "tile buffers exceed shared memory");
 static_assert(kColLo + kTN <= kTmemCols, "accumulators exceed the TMEM allocation");
 
-// Chunks between drains of group w: (w + 1) * 32 * period * 2^14 < 2^24.
-__device__ __forceinline__ int drain_period(int w) { return w == 0 ? 16 : (w <= 2 ? 8 : 4); }
+// Accumulator a (0, 1, 2: the exact groups G_0, G_1, G_2; 3: G_3 + G_4 + G_5)
+// is drained after every drain_period(a) chunks: (w + 1) * 32 * period *
+// 2^14 stays within 2^23 for the exact ones.
+__host__ __device__ constexpr int drain_period(int a) { return a == 0 ? 16 : 8; }
+__device__ __forceinline__ constexpr int acc_of(int w) { return w < 3 ? w : 3; }
 
 __device__ __forceinline__ const float *tc_col(const gram_tc_job &j, int g) {
   if (g < j.d) return j.S + (int64_t)g * j.lds;
@@ -74,44 +79,79 @@ __device__ __forceinline__ const float *tc_col(const gram_tc_job &j, int g) {
   return nullptr;
 }
 
-// x[0..7] = rows k..k+7 of column `col` (zero past m or for a missing column)
-__device__ __forceinline__ void load8(const float *col, int64_t k, int64_t m, int vec4, float *x) {
-  if (col && vec4 && k + 8 <= m) {
-    const float4 a = __ldg(reinterpret_cast<const float4 *>(col + k));
-    const float4 b = __ldg(reinterpret_cast<const float4 *>(col + k + 4));
-    x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w, x[4] = b.x, x[5] = b.y, x[6] = b.z, x[7] = b.w;
+// x[0..n-1] = rows k..k+n-1 of column `col` (zero past m or for a missing column)
+template <int n>
+__device__ __forceinline__ void load_rows(const float *col, int64_t k, int64_t m, int vec4, float *x) {
+  if (col && vec4 && k + n <= m) {
+#pragma unroll
+    for (int e = 0; e < n; e += 4) {
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(col + k + e));
+      x[e] = a.x, x[e + 1] = a.y, x[e + 2] = a.z, x[e + 3] = a.w;
+    }
   } else {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) x[e] = (col && k + e < m) ? __ldg(col + k + e) : 0.0f;
+    for (int e = 0; e < n; ++e) x[e] = (col && k + e < m) ? __ldg(col + k + e) : 0.0f;
   }
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // lo in the lower half (lower address)
-  return *reinterpret_cast<const uint32_t *>(&v);
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// two FP32 values (lower half first) as a BF16 pair, the first in the lower half
+__device__ __forceinline__ uint32_t f2_to_bf16x2(uint64_t v) {
+  uint32_t d;
+  asm("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tcvt.rn.bf16x2.f32 %0, hi, lo;\n\t}" : "=r"(d) : "l"(v));
+  return d;
 }
 
 // The six slices of eight values (one 16-byte row of a core matrix each),
-// written to dst + p * slice_bytes.  f1 * f2 = 2^(7 - E) (two factors so
-// that each stays a normal FP32 number); every step is exact.
-__device__ __forceinline__ void store_slices(uint32_t dst, uint32_t slice_bytes, const float *x, float f1, float f2) {
-  float v[8];
+// written to dst + p * slice_bytes.  sc = (f1, f1), (f2, f2) with
+// f1 f2 = 2^(7 - E).  Slice p rounds the rest to a multiple of 2^-8p by
+// adding and subtracting 1.5 * 2^(23 - 8p) (round to nearest even); every
+// step is exact, on pairs of values (packed f32x2).
+__device__ __forceinline__ void store_slices(uint32_t dst, uint32_t slice_bytes, const float *x, uint64_t sc1,
+                                             uint64_t sc2) {
+  uint64_t v[4];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) v[e] = __fmul_rn(__fmul_rn(x[e], f1), f2);
+  for (int e = 0; e < 4; ++e) v[e] = f2_mul(f2_mul(f2_pack(x[2 * e], x[2 * e + 1]), sc1), sc2);
 #pragma unroll
   for (int p = 0; p < kSl; ++p) {
-    float s[8];
+    const float cf = 1.5f * __int_as_float((127 + 23 - 8 * p) << 23);
+    const uint64_t C = f2_pack(cf, cf);
+    uint32_t w[4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      s[e] = rintf(v[e]);
-      v[e] = __fmul_rn(__fsub_rn(v[e], s[e]), 256.0f);
+    for (int e = 0; e < 4; ++e) {
+      const uint64_t t = f2_sub(f2_add(v[e], C), C);
+      v[e] = f2_sub(v[e], t);
+      w[e] = f2_to_bf16x2(t);
     }
-    const uint32_t w0 = pack_bf16x2(s[0], s[1]), w1 = pack_bf16x2(s[2], s[3]);
-    const uint32_t w2 = pack_bf16x2(s[4], s[5]), w3 = pack_bf16x2(s[6], s[7]);
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + (uint32_t)p * slice_bytes), "r"(w0), "r"(w1),
-                 "r"(w2), "r"(w3)
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + (uint32_t)p * slice_bytes), "r"(w[0]),
+                 "r"(w[1]), "r"(w[2]), "r"(w[3])
                  : "memory");
   }
+}
+
+__device__ __forceinline__ void store_zero_slices(uint32_t dst, uint32_t slice_bytes) {
+#pragma unroll
+  for (int p = 0; p < kSl; ++p)
+    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(dst + (uint32_t)p * slice_bytes), "r"(0u) : "memory");
 }
 
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float y) {
@@ -129,6 +169,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
   __shared__ float colun_s[kTN];
   __shared__ int last_s;  // this CTA finished the tile's last K-split
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const int tile = (int)(local % jb.tiles);
   const int split = (int)(local / jb.tiles);
   int mt = 0, nt = 0;
@@ -148,61 +189,75 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
     tc::fence_mbar_init();
     last_s = 0;
   }
-  if (tid < 32) tc::tmem_alloc(tc::smem_addr(&tmem_base_s), kTmemCols);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tmem_base_s), kTmemCols);
   if (tid < kTN) colun_s[tid] = (j0 + tid < jb.c) ? jb.colunscale[j0 + tid] : 0.0f;
 
-  // this thread's A column (tile row tid, TMEM lane tid) and B column
-  const int gi = i0 + tid;
-  const float *colA = tc_col(jb, gi);
-  const float fa1 = colA ? jb.colscale[2 * gi] : 0.0f, fa2 = colA ? jb.colscale[2 * gi + 1] : 0.0f;
-  const float row_un = colA ? jb.colunscale[gi] : 0.0f;
-  const int gb = j0 + (tid & (kTN - 1));
-  const float *colB = alias ? nullptr : tc_col(jb, gb);
-  const float fb1 = colB ? jb.colscale[2 * gb] : 0.0f, fb2 = colB ? jb.colscale[2 * gb + 1] : 0.0f;
+  // slicing roles: A feature fa (tile row), its rows 16 ha .. 16 ha + 15 of a
+  // chunk (core matrices ki = 2 ha, 2 ha + 1); B feature fb, rows 8 kb ..
+  const int fa = tid & (kTM - 1), ha = tid >> 7;
+  const float *colA = tc_col(jb, i0 + fa);
+  const float a1 = colA ? jb.colscale[2 * (i0 + fa)] : 0.0f, a2 = colA ? jb.colscale[2 * (i0 + fa) + 1] : 0.0f;
+  const uint64_t scA1 = f2_pack(a1, a1), scA2 = f2_pack(a2, a2);
+  const int fb = tid & (kTN - 1), kb = tid >> 6;
+  const float *colB = alias ? nullptr : tc_col(jb, j0 + fb);
+  const float b1 = colB ? jb.colscale[2 * (j0 + fb)] : 0.0f, b2 = colB ? jb.colscale[2 * (j0 + fb) + 1] : 0.0f;
+  const uint64_t scB1 = f2_pack(b1, b1), scB2 = f2_pack(b2, b2);
+  const uint32_t offA = (uint32_t)(fa >> 3) * kStride + (uint32_t)(fa & 7) * 16 + (uint32_t)(2 * ha) * kLead;
+  const uint32_t offB = kSl * kASlice + (uint32_t)(fb >> 3) * kStride + (uint32_t)(fb & 7) * 16 + (uint32_t)kb * kLead;
+  // drain roles: TMEM lane (tile row) 32 (warp % 4) + lane, columns 32 (warp / 4) ..
+  const int drow = 32 * (warp & 3) + lane, dcol = 32 * (warp >> 2);
+  const float row_un = (i0 + drow < jb.c) ? jb.colunscale[i0 + drow] : 0.0f;
 
-  auto slice_chunk = [&](int64_t ch, int buf) {
+  float xa[16], xb[8];
+  auto load_chunk = [&](int64_t ch) {
     const int64_t k0 = ch * kKC;
-    const uint32_t bA = sbase + (uint32_t)buf * kBufBytes;
-    const uint32_t rowA = bA + (uint32_t)(tid >> 3) * kStride + (uint32_t)(tid & 7) * 16;
-#pragma unroll
-    for (int ki = 0; ki < kKC / 8; ++ki) {
-      float x[8];
-      load8(colA, k0 + 8 * ki, jb.m, jb.vec4, x);
-      store_slices(rowA + (uint32_t)ki * kLead, kASlice, x, fa1, fa2);
-    }
-    if (!alias) {
-      const uint32_t bB = bA + kSl * kASlice;
-      const int f = tid & (kTN - 1);
-      const uint32_t rowB = bB + (uint32_t)(f >> 3) * kStride + (uint32_t)(f & 7) * 16;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int ki = (tid >> 6) + 2 * q;
-        float x[8];
-        load8(colB, k0 + 8 * ki, jb.m, jb.vec4, x);
-        store_slices(rowB + (uint32_t)ki * kLead, kBSlice, x, fb1, fb2);
-      }
-    }
+    load_rows<16>(colA, k0 + 16 * ha, jb.m, jb.vec4, xa);
+    if (colB) load_rows<8>(colB, k0 + 8 * kb, jb.m, jb.vec4, xb);
   };
+  auto slice_chunk = [&](int buf) {
+    const uint32_t base = sbase + (uint32_t)buf * kBufBytes;
+    if (colA) {
+      store_slices(base + offA, kASlice, xa, scA1, scA2);
+      store_slices(base + offA + kLead, kASlice, xa + 8, scA1, scA2);
+    }
+    if (colB) store_slices(base + offB, kBSlice, xb, scB1, scB2);
+  };
+  // columns past c slice to zero: written once into both buffers
+#pragma unroll
+  for (int buf = 0; buf < 2; ++buf) {
+    const uint32_t base = sbase + (uint32_t)buf * kBufBytes;
+    if (!colA) {
+      store_zero_slices(base + offA, kASlice);
+      store_zero_slices(base + offA + kLead, kASlice);
+    }
+    if (!alias && !colB) store_zero_slices(base + offB, kBSlice);
+  }
 
-  if (nch > 0) slice_chunk(ch0, 0);
+  if (nch > 0) {
+    load_chunk(ch0);
+    slice_chunk(0);
+    if (nch > 1) load_chunk(ch0 + 1);
+  }
   tc::fence_proxy_async();
   tc::tmem_fence_before();
   __syncthreads();
   tc::tmem_fence_after();
   const uint32_t tbase = tmem_base_s;
-  const uint32_t tlane = tbase + ((uint32_t)(32 * (tid >> 5)) << 16);
+  const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)dcol;
   {
-    // the running float-float sums of this thread's row start at zero
+    // the running float-float sums of this thread's 32 entries start at zero
     uint32_t z[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) z[q] = 0u;
-#pragma unroll
-    for (int h = 0; h < 2 * kTN / 16; ++h) tc::tmem_st16(tlane + kColHi + 16 * h, z);
+    tc::tmem_st16(tlane + kColHi, z);
+    tc::tmem_st16(tlane + kColHi + 16, z);
+    tc::tmem_st16(tlane + kColLo, z);
+    tc::tmem_st16(tlane + kColLo + 16, z);
     tc::tmem_wait_st();
   }
-  uint32_t fresh = (1u << kGroups) - 1;  // groups whose next MMA overwrites (thread 0's view)
+  uint32_t fresh = 0xFu;  // accumulators whose next MMA overwrites (thread 0's view)
   int64_t last_commit = -1;
-  bool stalled = false;  // a bounded wait gave up (the same in every thread after each barrier)
+  bool stalled = false;   // a bounded wait gave up (the same in every thread after each barrier)
 
   for (int64_t t = 0; t < nch; ++t) {
     const int buf = (int)(t & 1);
@@ -211,16 +266,19 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       const uint32_t bA = sbase + (uint32_t)buf * kBufBytes;
       const uint32_t bB = alias ? bA + (uint32_t)((j0 - i0) >> 3) * kStride : bA + kSl * kASlice;
       const uint32_t bSl = alias ? kASlice : kBSlice;
+      const uint64_t dA = tc::smem_desc(bA, kLead, kStride);
+      const uint64_t dB = tc::smem_desc(bB, kLead, kStride);
 #pragma unroll
-      for (int w = 0; w < kGroups; ++w) {
-        const uint32_t dcol = tbase + (uint32_t)(w * kTN);
+      for (int w = 0; w < kSl; ++w) {
+        const int a = acc_of(w);
+#pragma unroll
         for (int p = 0; p <= w; ++p) {
 #pragma unroll
           for (int kk = 0; kk < kKC / 16; ++kk) {
-            const uint64_t ad = tc::smem_desc(bA + (uint32_t)p * kASlice + (uint32_t)kk * 2 * kLead, kLead, kStride);
-            const uint64_t bd = tc::smem_desc(bB + (uint32_t)(w - p) * bSl + (uint32_t)kk * 2 * kLead, kLead, kStride);
-            const uint32_t acc = ((fresh >> w) & 1u) && p == 0 && kk == 0 ? 0u : 1u;
-            tc::mma_bf16(dcol, ad, bd, kIdesc, acc);
+            const uint64_t ad = dA + (uint64_t)((p * kASlice + kk * 2 * kLead) >> 4);
+            const uint64_t bd = dB + (uint64_t)(((uint32_t)(w - p) * bSl + (uint32_t)kk * 2 * kLead) >> 4);
+            const bool first = (p == 0 && kk == 0 && (a < 3 || w == 3));
+            tc::mma_bf16(tbase + (uint32_t)(a * kTN), ad, bd, kIdesc, (first && ((fresh >> a) & 1u)) ? 0u : 1u);
           }
         }
       }
@@ -232,46 +290,42 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       // the other buffer was read by the MMAs of chunk t - 1
       if (t >= 1 && !tc::mbar_wait_bounded(buf ? bar0 : bar1, (uint32_t)(((t - 1) >> 1) & 1), kWaitLimit))
         stalled = true;
-      slice_chunk(ch0 + t + 1, buf ^ 1);
+      slice_chunk(buf ^ 1);
       tc::fence_proxy_async();
+      if (t + 2 < nch) load_chunk(ch0 + t + 2);
     }
     uint32_t due = 0;
 #pragma unroll
-    for (int w = 0; w < kGroups; ++w)
-      if (t + 1 == nch || ((t + 1) % drain_period(w)) == 0) due |= 1u << w;
+    for (int a = 0; a < 4; ++a)
+      if (t + 1 == nch || ((t + 1) % drain_period(a)) == 0) due |= 1u << a;
     if (due) {
       if (!tc::mbar_wait_bounded(buf ? bar1 : bar0, (uint32_t)((t >> 1) & 1), kWaitLimit)) stalled = true;
       tc::tmem_fence_after();
+      uint32_t h[32], l[32];
+      tc::tmem_ld16(tlane + kColHi, h);
+      tc::tmem_ld16(tlane + kColHi + 16, h + 16);
+      tc::tmem_ld16(tlane + kColLo, l);
+      tc::tmem_ld16(tlane + kColLo + 16, l + 16);
 #pragma unroll 1
-      for (int half = 0; half < 2; ++half) {
-        // columns 32 half .. + 31 of the row: running sums in, every due group added, sums out
-        uint32_t h[32], l[32];
-        tc::tmem_ld16(tlane + kColHi + 32 * half, h);
-        tc::tmem_ld16(tlane + kColHi + 32 * half + 16, h + 16);
-        tc::tmem_ld16(tlane + kColLo + 32 * half, l);
-        tc::tmem_ld16(tlane + kColLo + 32 * half + 16, l + 16);
-#pragma unroll 1
-        for (int w = 0; w < kGroups; ++w) {
-          if (!((due >> w) & 1u)) continue;
-          uint32_t r[32];
-          tc::tmem_ld16(tlane + (uint32_t)(w * kTN + 32 * half), r);
-          tc::tmem_ld16(tlane + (uint32_t)(w * kTN + 32 * half + 16), r + 16);
-          tc::tmem_wait_ld();
-          const float fw = __fmul_rn(row_un, __int_as_float((127 - 8 * w) << 23));  // row scale x 2^-8w
+      for (int a = 0; a < 4; ++a) {
+        if (!((due >> a) & 1u)) continue;
+        uint32_t r[32];
+        tc::tmem_ld16(tlane + (uint32_t)(a * kTN), r);
+        tc::tmem_ld16(tlane + (uint32_t)(a * kTN + 16), r + 16);
+        tc::tmem_wait_ld();
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            float hv = __uint_as_float(h[q]), lv = __uint_as_float(l[q]);
-            two_sum_acc(hv, lv, __fmul_rn(__fmul_rn(__uint_as_float(r[q]), fw), colun_s[32 * half + q]));
-            h[q] = __float_as_uint(hv);
-            l[q] = __float_as_uint(lv);
-          }
+        for (int q = 0; q < 32; ++q) {
+          float hv = __uint_as_float(h[q]), lv = __uint_as_float(l[q]);
+          two_sum_acc(hv, lv, __fmul_rn(__fmul_rn(__uint_as_float(r[q]), row_un), colun_s[dcol + q]));
+          h[q] = __float_as_uint(hv);
+          l[q] = __float_as_uint(lv);
         }
-        tc::tmem_st16(tlane + kColHi + 32 * half, h);
-        tc::tmem_st16(tlane + kColHi + 32 * half + 16, h + 16);
-        tc::tmem_st16(tlane + kColLo + 32 * half, l);
-        tc::tmem_st16(tlane + kColLo + 32 * half + 16, l + 16);
-        tc::tmem_wait_st();
       }
+      tc::tmem_st16(tlane + kColHi, h);
+      tc::tmem_st16(tlane + kColHi + 16, h + 16);
+      tc::tmem_st16(tlane + kColLo, l);
+      tc::tmem_st16(tlane + kColLo + 16, l + 16);
+      tc::tmem_wait_st();
       tc::tmem_fence_before();
       if (tid == 0) fresh |= due;
     }
@@ -286,6 +340,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
   }
   const double nanv = __longlong_as_double(0x7ff8000000000000ll);
   const int c = jb.c;
+  const int gi = i0 + drow;
   auto write_q = [&](int i, int j, double v) {
     const float h = (float)v;
     const float l = (float)(v - (double)h);
@@ -296,40 +351,31 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
     jb.Qlo[(int64_t)i * c + j] = l;
     jb.Qlo[(int64_t)j * c + i] = l;
   };
-  // the row's sums as FP64, 32 columns at a time (the final drain ended with wait::st)
-  auto row_sums = [&](int half, double *v) {
+  double v[32];
+  {
+    // this thread's 32 sums as FP64 (the final drain ended with wait::st)
     uint32_t h[32], l[32];
-    tc::tmem_ld16(tlane + kColHi + 32 * half, h);
-    tc::tmem_ld16(tlane + kColHi + 32 * half + 16, h + 16);
-    tc::tmem_ld16(tlane + kColLo + 32 * half, l);
-    tc::tmem_ld16(tlane + kColLo + 32 * half + 16, l + 16);
+    tc::tmem_ld16(tlane + kColHi, h);
+    tc::tmem_ld16(tlane + kColHi + 16, h + 16);
+    tc::tmem_ld16(tlane + kColLo, l);
+    tc::tmem_ld16(tlane + kColLo + 16, l + 16);
     tc::tmem_wait_ld();
 #pragma unroll
     for (int q = 0; q < 32; ++q)
       v[q] = stalled ? nanv : (double)__uint_as_float(h[q]) + (double)__uint_as_float(l[q]);
-  };
+  }
   if (jb.splits == 1) {
-#pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-      double v[32];
-      row_sums(half, v);
-      if (gi < c) {
+    if (gi < c) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int j = j0 + 32 * half + q;
-          if (j < c && gi <= j) write_q(gi, j, v[q]);
-        }
+      for (int q = 0; q < 32; ++q) {
+        const int j = j0 + dcol + q;
+        if (j < c && gi <= j) write_q(gi, j, v[q]);
       }
     }
   } else {
-    double *mine = jb.part + ((int64_t)split * jb.tiles + tile) * (kTM * kTN) + (int64_t)tid * kTN;
-#pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-      double v[32];
-      row_sums(half, v);
+    double *mine = jb.part + ((int64_t)split * jb.tiles + tile) * (kTM * kTN) + (int64_t)drow * kTN + dcol;
 #pragma unroll
-      for (int q = 0; q < 32; ++q) mine[32 * half + q] = v[q];
-    }
+    for (int q = 0; q < 32; ++q) mine[q] = v[q];
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -339,23 +385,18 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
     __syncthreads();
     if (last_s) {
       __threadfence();
-#pragma unroll 1
-      for (int half = 0; half < 2; ++half) {
-        double acc[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-        for (int sp = 0; sp < jb.splits; ++sp) {
-          const double *src =
-              jb.part + ((int64_t)sp * jb.tiles + tile) * (kTM * kTN) + (int64_t)tid * kTN + 32 * half;
+      for (int q = 0; q < 32; ++q) v[q] = 0.0;
+      for (int sp = 0; sp < jb.splits; ++sp) {
+        const double *src = jb.part + ((int64_t)sp * jb.tiles + tile) * (kTM * kTN) + (int64_t)drow * kTN + dcol;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) acc[q] += __ldcg(src + q);
-        }
-        if (gi < c) {
+        for (int q = 0; q < 32; ++q) v[q] += __ldcg(src + q);
+      }
+      if (gi < c) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int j = j0 + 32 * half + q;
-            if (j < c && gi <= j) write_q(gi, j, acc[q]);
-          }
+        for (int q = 0; q < 32; ++q) {
+          const int j = j0 + dcol + q;
+          if (j < c && gi <= j) write_q(gi, j, v[q]);
         }
       }
       if (tid == 0) jb.counters[tile] = 0u;
@@ -364,7 +405,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
   tc::tmem_fence_before();
   __syncthreads();
   tc::tmem_fence_after();
-  if (tid < 32) tc::tmem_dealloc(tbase, kTmemCols);
+  if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel_one(const gram_tc_job jb) {
