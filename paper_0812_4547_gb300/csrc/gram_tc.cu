@@ -26,16 +26,18 @@
 // max_k |x_ki| max_k |x_kj| per row.  The column magnitudes limit the data to
 // the FP32 exponent range, as FP32 products would.
 //
-// Work split: a CTA of 256 threads owns one tile of Q (128 rows i x 64
-// columns j; tiles wholly below the diagonal are skipped) and a range of
-// 32-row chunks of X.  Per chunk the threads slice their share of the tile's
-// columns into shared memory (K-major core matrices, two buffers; the next
-// chunk's values are loaded into registers ahead), then one thread issues
-// 21 x 2 tcgen05.mma (M = 128, N = 64, K = 16) into the four accumulators
-// and commits them to an mbarrier; slicing of chunk t + 1 runs while the
-// tensor cores work on chunk t.  K-splits of one tile add their FP64
-// partials in a fixed order in the last CTA to finish (a counter per tile,
-// reset by that CTA).
+// Work split: a CTA owns one tile of Q (128 rows i x 64 columns j; tiles
+// wholly below the diagonal are skipped) and a range of 32-row chunks of X.
+// Eight warps slice their share of the tile's columns into shared memory
+// (K-major core matrices, two buffers; the next chunk's values are loaded
+// into registers ahead) and drain the accumulators; a ninth warp issues, per
+// chunk, 21 x 2 tcgen05.mma (M = 128, N = 64, K = 16) into the four
+// accumulators and commits them to an mbarrier.  The warps meet only at
+// mbarriers: "full" (a buffer is sliced), "mma_done" (the tensor cores are
+// through a buffer) and "drained" (the due accumulators were read back), so
+// slicing of chunk t + 1 runs while the tensor cores work on chunk t.
+// K-splits of one tile add their FP64 partials in a fixed order in the last
+// CTA to finish (a counter per tile, reset by that CTA).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -51,7 +53,8 @@ constexpr int kTM = 128;                       // tile rows (MMA M)
 constexpr int kTN = 64;                        // tile columns (MMA N)
 constexpr int kKC = 32;                        // rows of X per chunk
 constexpr int kSl = 6;                         // slices per value
-constexpr int kTcThreads = 256;
+constexpr int kSliceThreads = 256;            // eight slicing / draining warps
+constexpr int kTcThreads = kSliceThreads + 32; // plus the MMA warp
 constexpr uint32_t kTmemCols = 512;            // 4 accumulators + 2 running sums of 64 columns, rounded up
 constexpr uint32_t kColHi = 4 * kTN;           // TMEM columns of the running sums (hi, then lo)
 constexpr uint32_t kColLo = kColHi + kTN;
@@ -62,6 +65,7 @@ constexpr uint32_t kBSlice = kTN * kKC * 2;    // bytes of one slice of the 64-r
 constexpr uint32_t kBufBytes = kSl * (kASlice + kBSlice);
 constexpr size_t kTcSmem = 2 * (size_t)kBufBytes;
 constexpr uint32_t kWaitLimit = 1u << 22;      // mbarrier polls before a wait gives up
+constexpr uint32_t kShortWait = 64;            // polls once some wait has given up
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTM, kTN);
 
 static_assert(kTcSmem <= 200 * 1024, "tile buffers exceed shared memory");
@@ -162,9 +166,18 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float y) {
   lo = __fadd_rn(lo, e);
 }
 
+// Accumulators drained after chunk t (relative to the CTA's first chunk).
+__device__ __forceinline__ uint32_t due_after(int64_t t, int64_t nch) {
+  uint32_t due = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+    if (t + 1 == nch || ((t + 1) % drain_period(a)) == 0) due |= 1u << a;
+  return due;
+}
+
 __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t local) {
   extern __shared__ __align__(128) unsigned char tc_smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[5];  // full[2], mma_done[2], drained
   __shared__ uint32_t tmem_base_s;
   __shared__ float colun_s[kTN];
   __shared__ int last_s;  // this CTA finished the tile's last K-split
@@ -182,125 +195,79 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
   const int64_t nch = max((int64_t)0, min(nchunks, ch0 + jb.chunks_per_split) - ch0);
 
   const uint32_t sbase = tc::smem_addr(tc_smem);
-  const uint32_t bar0 = tc::smem_addr(&mbar[0]), bar1 = tc::smem_addr(&mbar[1]);
+  const uint32_t full0 = tc::smem_addr(&mbar[0]), done0 = tc::smem_addr(&mbar[2]);
+  const uint32_t drained = tc::smem_addr(&mbar[4]);
+  auto full_bar = [&](int b) { return full0 + 8u * (uint32_t)b; };
+  auto done_bar = [&](int b) { return done0 + 8u * (uint32_t)b; };
   if (tid == 0) {
-    tc::mbar_init(bar0, 1);
-    tc::mbar_init(bar1, 1);
+    tc::mbar_init(full_bar(0), kSliceThreads / 32);
+    tc::mbar_init(full_bar(1), kSliceThreads / 32);
+    tc::mbar_init(done_bar(0), 1);
+    tc::mbar_init(done_bar(1), 1);
+    tc::mbar_init(drained, kSliceThreads / 32);
     tc::fence_mbar_init();
     last_s = 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tmem_base_s), kTmemCols);
   if (tid < kTN) colun_s[tid] = (j0 + tid < jb.c) ? jb.colunscale[j0 + tid] : 0.0f;
-
-  // slicing roles: A feature fa (tile row), its rows 16 ha .. 16 ha + 15 of a
-  // chunk (core matrices ki = 2 ha, 2 ha + 1); B feature fb, rows 8 kb ..
-  const int fa = tid & (kTM - 1), ha = tid >> 7;
-  const float *colA = tc_col(jb, i0 + fa);
-  const float a1 = colA ? jb.colscale[2 * (i0 + fa)] : 0.0f, a2 = colA ? jb.colscale[2 * (i0 + fa) + 1] : 0.0f;
-  const uint64_t scA1 = f2_pack(a1, a1), scA2 = f2_pack(a2, a2);
-  const int fb = tid & (kTN - 1), kb = tid >> 6;
-  const float *colB = alias ? nullptr : tc_col(jb, j0 + fb);
-  const float b1 = colB ? jb.colscale[2 * (j0 + fb)] : 0.0f, b2 = colB ? jb.colscale[2 * (j0 + fb) + 1] : 0.0f;
-  const uint64_t scB1 = f2_pack(b1, b1), scB2 = f2_pack(b2, b2);
-  const uint32_t offA = (uint32_t)(fa >> 3) * kStride + (uint32_t)(fa & 7) * 16 + (uint32_t)(2 * ha) * kLead;
-  const uint32_t offB = kSl * kASlice + (uint32_t)(fb >> 3) * kStride + (uint32_t)(fb & 7) * 16 + (uint32_t)kb * kLead;
-  // drain roles: TMEM lane (tile row) 32 (warp % 4) + lane, columns 32 (warp / 4) ..
-  const int drow = 32 * (warp & 3) + lane, dcol = 32 * (warp >> 2);
-  const float row_un = (i0 + drow < jb.c) ? jb.colunscale[i0 + drow] : 0.0f;
-
-  float xa[16], xb[8];
-  auto load_chunk = [&](int64_t ch) {
-    const int64_t k0 = ch * kKC;
-    load_rows<16>(colA, k0 + 16 * ha, jb.m, jb.vec4, xa);
-    if (colB) load_rows<8>(colB, k0 + 8 * kb, jb.m, jb.vec4, xb);
-  };
-  auto slice_chunk = [&](int buf) {
-    const uint32_t base = sbase + (uint32_t)buf * kBufBytes;
-    if (colA) {
-      store_slices(base + offA, kASlice, xa, scA1, scA2);
-      store_slices(base + offA + kLead, kASlice, xa + 8, scA1, scA2);
-    }
-    if (colB) store_slices(base + offB, kBSlice, xb, scB1, scB2);
-  };
-  // columns past c slice to zero: written once into both buffers
-#pragma unroll
-  for (int buf = 0; buf < 2; ++buf) {
-    const uint32_t base = sbase + (uint32_t)buf * kBufBytes;
-    if (!colA) {
-      store_zero_slices(base + offA, kASlice);
-      store_zero_slices(base + offA + kLead, kASlice);
-    }
-    if (!alias && !colB) store_zero_slices(base + offB, kBSlice);
-  }
-
-  if (nch > 0) {
-    load_chunk(ch0);
-    slice_chunk(0);
-    if (nch > 1) load_chunk(ch0 + 1);
-  }
-  tc::fence_proxy_async();
   tc::tmem_fence_before();
   __syncthreads();
   tc::tmem_fence_after();
   const uint32_t tbase = tmem_base_s;
-  const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)dcol;
-  {
-    // the running float-float sums of this thread's 32 entries start at zero
-    uint32_t z[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) z[q] = 0u;
-    tc::tmem_st16(tlane + kColHi, z);
-    tc::tmem_st16(tlane + kColHi + 16, z);
-    tc::tmem_st16(tlane + kColLo, z);
-    tc::tmem_st16(tlane + kColLo + 16, z);
-    tc::tmem_wait_st();
-  }
-  uint32_t fresh = 0xFu;  // accumulators whose next MMA overwrites (thread 0's view)
-  int64_t last_commit = -1;
-  bool stalled = false;   // a bounded wait gave up (the same in every thread after each barrier)
+  bool stalled = false;  // some bounded wait of this thread gave up
+  auto wait = [&](uint32_t bar, uint32_t parity) {
+    if (!tc::mbar_wait_bounded(bar, parity, stalled ? kShortWait : kWaitLimit)) stalled = true;
+  };
 
-  for (int64_t t = 0; t < nch; ++t) {
-    const int buf = (int)(t & 1);
-    if (tid == 0) {
-      tc::tmem_fence_after();
-      const uint32_t bA = sbase + (uint32_t)buf * kBufBytes;
-      const uint32_t bB = alias ? bA + (uint32_t)((j0 - i0) >> 3) * kStride : bA + kSl * kASlice;
-      const uint32_t bSl = alias ? kASlice : kBSlice;
-      const uint64_t dA = tc::smem_desc(bA, kLead, kStride);
-      const uint64_t dB = tc::smem_desc(bB, kLead, kStride);
+  // drain roles: TMEM lane (tile row) 32 (warp % 4) + lane, columns 32 (warp / 4) ..
+  const int drow = 32 * (warp & 3) + lane, dcol = 32 * ((warp >> 2) & 1);
+  const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)dcol;
+
+  if (warp < kSliceThreads / 32) {
+    // ---- slicing and draining warps ----------------------------------------
+    // A feature fa (tile row), its rows 16 ha .. 16 ha + 15 of a chunk (core
+    // matrices ki = 2 ha, 2 ha + 1); B feature fb, rows 8 kb .. 8 kb + 7
+    const int fa = tid & (kTM - 1), ha = tid >> 7;
+    const float *colA = tc_col(jb, i0 + fa);
+    const float a1 = colA ? jb.colscale[2 * (i0 + fa)] : 0.0f, a2 = colA ? jb.colscale[2 * (i0 + fa) + 1] : 0.0f;
+    const uint64_t scA1 = f2_pack(a1, a1), scA2 = f2_pack(a2, a2);
+    const int fb = tid & (kTN - 1), kb = tid >> 6;
+    const float *colB = alias ? nullptr : tc_col(jb, j0 + fb);
+    const float b1 = colB ? jb.colscale[2 * (j0 + fb)] : 0.0f, b2 = colB ? jb.colscale[2 * (j0 + fb) + 1] : 0.0f;
+    const uint64_t scB1 = f2_pack(b1, b1), scB2 = f2_pack(b2, b2);
+    const uint32_t offA = (uint32_t)(fa >> 3) * kStride + (uint32_t)(fa & 7) * 16 + (uint32_t)(2 * ha) * kLead;
+    const uint32_t offB =
+        kSl * kASlice + (uint32_t)(fb >> 3) * kStride + (uint32_t)(fb & 7) * 16 + (uint32_t)kb * kLead;
+    const float row_un = (i0 + drow < jb.c) ? jb.colunscale[i0 + drow] : 0.0f;
+
+    float xa[16], xb[8];
+    auto load_chunk = [&](int64_t ch) {
+      const int64_t k0 = ch * kKC;
+      load_rows<16>(colA, k0 + 16 * ha, jb.m, jb.vec4, xa);
+      if (colB) load_rows<8>(colB, k0 + 8 * kb, jb.m, jb.vec4, xb);
+    };
+    // columns past c slice to zero: written once into both buffers
 #pragma unroll
-      for (int w = 0; w < kSl; ++w) {
-        const int a = acc_of(w);
-#pragma unroll
-        for (int p = 0; p <= w; ++p) {
-#pragma unroll
-          for (int kk = 0; kk < kKC / 16; ++kk) {
-            const uint64_t ad = dA + (uint64_t)((p * kASlice + kk * 2 * kLead) >> 4);
-            const uint64_t bd = dB + (uint64_t)(((uint32_t)(w - p) * bSl + (uint32_t)kk * 2 * kLead) >> 4);
-            const bool first = (p == 0 && kk == 0 && (a < 3 || w == 3));
-            tc::mma_bf16(tbase + (uint32_t)(a * kTN), ad, bd, kIdesc, (first && ((fresh >> a) & 1u)) ? 0u : 1u);
-          }
-        }
+    for (int b = 0; b < 2; ++b) {
+      const uint32_t base = sbase + (uint32_t)b * kBufBytes;
+      if (!colA) {
+        store_zero_slices(base + offA, kASlice);
+        store_zero_slices(base + offA + kLead, kASlice);
       }
-      tc::mma_commit(buf ? bar1 : bar0);
-      fresh = 0;
+      if (!alias && !colB) store_zero_slices(base + offB, kBSlice);
     }
-    last_commit = t;
-    if (t + 1 < nch) {
-      // the other buffer was read by the MMAs of chunk t - 1
-      if (t >= 1 && !tc::mbar_wait_bounded(buf ? bar0 : bar1, (uint32_t)(((t - 1) >> 1) & 1), kWaitLimit))
-        stalled = true;
-      slice_chunk(buf ^ 1);
-      tc::fence_proxy_async();
-      if (t + 2 < nch) load_chunk(ch0 + t + 2);
-    }
-    uint32_t due = 0;
+    {
+      // the running float-float sums of this thread's 32 entries start at zero
+      uint32_t z[16];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-      if (t + 1 == nch || ((t + 1) % drain_period(a)) == 0) due |= 1u << a;
-    if (due) {
-      if (!tc::mbar_wait_bounded(buf ? bar1 : bar0, (uint32_t)((t >> 1) & 1), kWaitLimit)) stalled = true;
-      tc::tmem_fence_after();
+      for (int q = 0; q < 16; ++q) z[q] = 0u;
+      tc::tmem_st16(tlane + kColHi, z);
+      tc::tmem_st16(tlane + kColHi + 16, z);
+      tc::tmem_st16(tlane + kColLo, z);
+      tc::tmem_st16(tlane + kColLo + 16, z);
+      tc::tmem_wait_st();
+    }
+    auto drain = [&](uint32_t due) {
       uint32_t h[32], l[32];
       tc::tmem_ld16(tlane + kColHi, h);
       tc::tmem_ld16(tlane + kColHi + 16, h + 16);
@@ -326,21 +293,85 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       tc::tmem_st16(tlane + kColLo, l);
       tc::tmem_st16(tlane + kColLo + 16, l + 16);
       tc::tmem_wait_st();
-      tc::tmem_fence_before();
-      if (tid == 0) fresh |= due;
-    }
-    stalled = __syncthreads_or(stalled) != 0;
-    if (stalled) break;
-  }
+    };
 
-  if (stalled && last_commit >= 0) {
-    // let the MMAs in flight finish (bounded) before the memory they use is released
-    const int64_t t = last_commit;
-    tc::mbar_wait_bounded((t & 1) ? bar1 : bar0, (uint32_t)((t >> 1) & 1), kWaitLimit);
+    if (nch > 0) load_chunk(ch0);
+    for (int64_t t = 0; t < nch; ++t) {
+      const int b = (int)(t & 1);
+      if (t >= 2) wait(done_bar(b), (uint32_t)(((t - 2) >> 1) & 1));  // the MMAs of chunk t - 2 read this buffer
+      const uint32_t base = sbase + (uint32_t)b * kBufBytes;
+      if (colA) {
+        store_slices(base + offA, kASlice, xa, scA1, scA2);
+        store_slices(base + offA + kLead, kASlice, xa + 8, scA1, scA2);
+      }
+      if (colB) store_slices(base + offB, kBSlice, xb, scB1, scB2);
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(full_bar(b));
+      if (t + 1 < nch) load_chunk(ch0 + t + 1);
+      if (t >= 1) {
+        const uint32_t due = due_after(t - 1, nch);
+        if (due) {
+          wait(done_bar((int)((t - 1) & 1)), (uint32_t)(((t - 1) >> 1) & 1));
+          tc::tmem_fence_after();
+          drain(due);
+          tc::tmem_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(drained);
+        }
+      }
+    }
+    if (nch > 0) {
+      const int64_t t = nch - 1;
+      wait(done_bar((int)(t & 1)), (uint32_t)((t >> 1) & 1));
+      tc::tmem_fence_after();
+      drain(due_after(t, nch));
+    }
+  } else if (lane == 0) {
+    // ---- the MMA warp (one issuing thread) ---------------------------------
+    uint32_t fresh = 0xFu;  // accumulators whose next MMA overwrites
+    uint32_t events = 0;    // drain events waited for
+    for (int64_t t = 0; t < nch; ++t) {
+      const int b = (int)(t & 1);
+      wait(full_bar(b), (uint32_t)((t >> 1) & 1));
+      if (t >= 1) {
+        const uint32_t due = due_after(t - 1, nch);
+        if (due) {
+          wait(drained, events & 1u);
+          ++events;
+          fresh |= due;
+        }
+      }
+      tc::tmem_fence_after();
+      const uint32_t bA = sbase + (uint32_t)b * kBufBytes;
+      const uint32_t bB = alias ? bA + (uint32_t)((j0 - i0) >> 3) * kStride : bA + kSl * kASlice;
+      const uint32_t bSl = alias ? kASlice : kBSlice;
+      const uint64_t dA = tc::smem_desc(bA, kLead, kStride);
+      const uint64_t dB = tc::smem_desc(bB, kLead, kStride);
+#pragma unroll
+      for (int w = 0; w < kSl; ++w) {
+        const int a = acc_of(w);
+#pragma unroll
+        for (int p = 0; p <= w; ++p) {
+#pragma unroll
+          for (int kk = 0; kk < kKC / 16; ++kk) {
+            const uint64_t ad = dA + (uint64_t)((p * kASlice + kk * 2 * kLead) >> 4);
+            const uint64_t bd = dB + (uint64_t)(((uint32_t)(w - p) * bSl + (uint32_t)kk * 2 * kLead) >> 4);
+            const bool first = (p == 0 && kk == 0 && (a < 3 || w == 3));
+            tc::mma_bf16(tbase + (uint32_t)(a * kTN), ad, bd, kIdesc, (first && ((fresh >> a) & 1u)) ? 0u : 1u);
+          }
+        }
+      }
+      tc::mma_commit(done_bar(b));
+      fresh = 0;
+    }
   }
+  stalled = __syncthreads_or(stalled) != 0;
+
   const double nanv = __longlong_as_double(0x7ff8000000000000ll);
   const int c = jb.c;
   const int gi = i0 + drow;
+  const bool worker = tid < kSliceThreads;
   auto write_q = [&](int i, int j, double v) {
     const float h = (float)v;
     const float l = (float)(v - (double)h);
@@ -352,7 +383,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
     jb.Qlo[(int64_t)j * c + i] = l;
   };
   double v[32];
-  {
+  if (worker) {
     // this thread's 32 sums as FP64 (the final drain ended with wait::st)
     uint32_t h[32], l[32];
     tc::tmem_ld16(tlane + kColHi, h);
@@ -365,7 +396,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       v[q] = stalled ? nanv : (double)__uint_as_float(h[q]) + (double)__uint_as_float(l[q]);
   }
   if (jb.splits == 1) {
-    if (gi < c) {
+    if (worker && gi < c) {
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int j = j0 + dcol + q;
@@ -374,8 +405,10 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
     }
   } else {
     double *mine = jb.part + ((int64_t)split * jb.tiles + tile) * (kTM * kTN) + (int64_t)drow * kTN + dcol;
+    if (worker) {
 #pragma unroll
-    for (int q = 0; q < 32; ++q) mine[q] = v[q];
+      for (int q = 0; q < 32; ++q) mine[q] = v[q];
+    }
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -383,14 +416,26 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       if (done == (unsigned int)(jb.splits - 1)) last_s = 1;
     }
     __syncthreads();
-    if (last_s) {
+    if (last_s && worker) {
       __threadfence();
 #pragma unroll
       for (int q = 0; q < 32; ++q) v[q] = 0.0;
-      for (int sp = 0; sp < jb.splits; ++sp) {
-        const double *src = jb.part + ((int64_t)sp * jb.tiles + tile) * (kTM * kTN) + (int64_t)drow * kTN + dcol;
+      // splits added in order 0, 1, ...; loads of two splits in flight at a time
+      const double *src = jb.part + (int64_t)tile * (kTM * kTN) + (int64_t)drow * kTN + dcol;
+      const int64_t sstride = (int64_t)jb.tiles * (kTM * kTN);
+      int sp = 0;
+      for (; sp + 2 <= jb.splits; sp += 2) {
+        double t0[32], t1[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] += __ldcg(src + q);
+        for (int q = 0; q < 32; ++q) t0[q] = __ldcg(src + sp * sstride + q);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) t1[q] = __ldcg(src + (sp + 1) * sstride + q);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = (v[q] + t0[q]) + t1[q];
+      }
+      if (sp < jb.splits) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] += __ldcg(src + sp * sstride + q);
       }
       if (gi < c) {
 #pragma unroll
@@ -432,17 +477,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel_batched(const gr
 // Per column g of X: the scale 2^(7 - E_g) as two factors, its inverse
 // 2^(E_g - 7), and for columns of S the compensated sum of magnitudes
 // (||S||_1 = max_g of these sums).  One block per column.
-constexpr int kStatThreads = 256;
+constexpr int kStatThreads = 512;
 __device__ __forceinline__ void colstats_block(const gram_tc_job &jb, int g) {
   __shared__ float smax[kStatThreads / 32];
   __shared__ double ssum[kStatThreads / 32];
   const float *col = tc_col(jb, g);
   float mx = 0.0f;
   dot2 acc;
-  for (int64_t k = threadIdx.x; k < jb.m; k += kStatThreads) {
+  // four rows per load where the column is 16-byte aligned (rows before the
+  // first aligned one and after the last full group one by one)
+  const int64_t head = jb.vec4 ? min(jb.m, (int64_t)((16 - ((uintptr_t)col & 15)) & 15) / 4) : jb.m;
+  for (int64_t k = threadIdx.x; k < head; k += kStatThreads) {
     const float a = fabsf(__ldg(col + k));
     mx = fmaxf(mx, a);
     acc.add(a);
+  }
+  if (jb.vec4) {
+    const int64_t nq = (jb.m - head) / 4;
+    const float4 *c4 = reinterpret_cast<const float4 *>(col + head);
+    for (int64_t k = threadIdx.x; k < nq; k += kStatThreads) {
+      const float4 a = __ldg(c4 + k);
+      const float v0 = fabsf(a.x), v1 = fabsf(a.y), v2 = fabsf(a.z), v3 = fabsf(a.w);
+      mx = fmaxf(fmaxf(mx, fmaxf(v0, v1)), fmaxf(v2, v3));
+      acc.add(v0);
+      acc.add(v1);
+      acc.add(v2);
+      acc.add(v3);
+    }
+    for (int64_t k = head + 4 * nq + threadIdx.x; k < jb.m; k += kStatThreads) {
+      const float a = fabsf(__ldg(col + k));
+      mx = fmaxf(mx, a);
+      acc.add(a);
+    }
   }
   const ff v = acc.value();
   double sum = (double)v.hi + (double)v.lo;
@@ -529,7 +595,9 @@ gram_tc_job gram_tc_plan(const float *S, int64_t lds, const float *s, int64_t ld
   j.tiles = gram_tc_tile_count(j.c, d, multi);
   const int64_t chunks = std::max<int64_t>(1, (m + kKC - 1) / kKC);
   int64_t splits = std::max<int64_t>(1, ((int64_t)want_ctas + j.tiles - 1) / j.tiles);
-  splits = std::min<int64_t>(splits, std::max<int64_t>(1, chunks / 8));  // at least 8 chunks per CTA
+  // at least 16 chunks per CTA and at most 64 K-splits: the last CTA of a
+  // tile adds every split's partial tile
+  splits = std::min<int64_t>(std::min<int64_t>(splits, 64), std::max<int64_t>(1, chunks / 16));
   splits = std::max<int64_t>(splits, (chunks + max_chunks_per_cta - 1) / max_chunks_per_cta);
   j.chunks_per_split = (chunks + splits - 1) / splits;
   j.splits = (int)((chunks + j.chunks_per_split - 1) / j.chunks_per_split);
