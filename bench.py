@@ -78,6 +78,9 @@ def parse():
                     help="pipelined mode: steps alternate over this many sketch streams")
     ap.add_argument("--solve-streams", type=int, default=3,
                     help="solve streams when pipelined (each solve runs in one block)")
+    ap.add_argument("--free-sms", type=int, default=None,
+                    help="pipelined mode: SMs the sketch leaves to the solves (default: 8 + one per solve stream; "
+                         "a Gram CTA needs a whole SM's shared memory)")
     args = ap.parse_args()
     if args.config is None:
         args.config = 2 if (args.boost > 0) else 5
@@ -418,9 +421,11 @@ def main():
     s_sks = [s_sketch] + [torch.cuda.Stream(dev, priority=s_sketch.priority) for _ in range(nsk - 1)]
     ctx_sks = [ctx] + [P.Context(local, st) for st in s_sks[1:]]
     if pipeline:
-        # one SM per concurrent Lawson-Hanson solve stays free of sketch blocks
+        # SMs free of sketch blocks: one per concurrent Lawson-Hanson solve,
+        # plus room for the tensor-core Gram CTAs of the solves
+        free = args.free_sms if args.free_sms is not None else 8 + nsolve
         for cs in ctx_sks:
-            cs.set_sketch_sms(torch.cuda.get_device_properties(local).multi_processor_count - nsolve)
+            cs.set_sketch_sms(torch.cuda.get_device_properties(local).multi_processor_count - free)
     nbuf = nsolve + nsk if pipeline else 1
     SAs = [torch.empty((p.d, r), dtype=tdt, device=dev).t() for _ in range(nbuf)]
     Sbs = [torch.empty(r, dtype=tdt, device=dev) for _ in range(nbuf)]

@@ -240,8 +240,10 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
         kSl * kASlice + (uint32_t)(fb >> 3) * kStride + (uint32_t)(fb & 7) * 16 + (uint32_t)kb * kLead;
     const float row_un = (i0 + drow < jb.c) ? jb.colunscale[i0 + drow] : 0.0f;
 
-    float xa[16], xb[8];
-    auto load_chunk = [&](int64_t ch) {
+    // two register sets: chunk t is sliced from set t % 2 while the values of
+    // chunk t + 1 are in flight in the other set
+    float xa0[16], xb0[8], xa1[16], xb1[8];
+    auto load_chunk = [&](int64_t ch, float *xa, float *xb) {
       const int64_t k0 = ch * kKC;
       load_rows<16>(colA, k0 + 16 * ha, jb.m, jb.vec4, xa);
       if (colB) load_rows<8>(colB, k0 + 8 * kb, jb.m, jb.vec4, xb);
@@ -267,36 +269,36 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       tc::tmem_st16(tlane + kColLo + 16, z);
       tc::tmem_wait_st();
     }
+    // due accumulators into the running sums, 16 of the thread's 32 columns at a time
     auto drain = [&](uint32_t due) {
-      uint32_t h[32], l[32];
-      tc::tmem_ld16(tlane + kColHi, h);
-      tc::tmem_ld16(tlane + kColHi + 16, h + 16);
-      tc::tmem_ld16(tlane + kColLo, l);
-      tc::tmem_ld16(tlane + kColLo + 16, l + 16);
 #pragma unroll 1
-      for (int a = 0; a < 4; ++a) {
-        if (!((due >> a) & 1u)) continue;
-        uint32_t r[32];
-        tc::tmem_ld16(tlane + (uint32_t)(a * kTN), r);
-        tc::tmem_ld16(tlane + (uint32_t)(a * kTN + 16), r + 16);
-        tc::tmem_wait_ld();
+      for (int hh = 0; hh < 32; hh += 16) {
+        uint32_t h[16], l[16];
+        tc::tmem_ld16(tlane + kColHi + hh, h);
+        tc::tmem_ld16(tlane + kColLo + hh, l);
+#pragma unroll 1
+        for (int a = 0; a < 4; ++a) {
+          if (!((due >> a) & 1u)) continue;
+          uint32_t r[16];
+          tc::tmem_ld16(tlane + (uint32_t)(a * kTN + hh), r);
+          tc::tmem_wait_ld();
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          float hv = __uint_as_float(h[q]), lv = __uint_as_float(l[q]);
-          two_sum_acc(hv, lv, __fmul_rn(__fmul_rn(__uint_as_float(r[q]), row_un), colun_s[dcol + q]));
-          h[q] = __float_as_uint(hv);
-          l[q] = __float_as_uint(lv);
+          for (int q = 0; q < 16; ++q) {
+            float hv = __uint_as_float(h[q]), lv = __uint_as_float(l[q]);
+            two_sum_acc(hv, lv, __fmul_rn(__fmul_rn(__uint_as_float(r[q]), row_un), colun_s[dcol + hh + q]));
+            h[q] = __float_as_uint(hv);
+            l[q] = __float_as_uint(lv);
+          }
         }
+        tc::tmem_st16(tlane + kColHi + hh, h);
+        tc::tmem_st16(tlane + kColLo + hh, l);
       }
-      tc::tmem_st16(tlane + kColHi, h);
-      tc::tmem_st16(tlane + kColHi + 16, h + 16);
-      tc::tmem_st16(tlane + kColLo, l);
-      tc::tmem_st16(tlane + kColLo + 16, l + 16);
       tc::tmem_wait_st();
     };
 
-    if (nch > 0) load_chunk(ch0);
-    for (int64_t t = 0; t < nch; ++t) {
+    // one chunk: slice it from (xa, xb), refill (xa, xb) with chunk t + 2,
+    // then drain what is due after chunk t - 1
+    auto step = [&](int64_t t, float *xa, float *xb) {
       const int b = (int)(t & 1);
       if (t >= 2) wait(done_bar(b), (uint32_t)(((t - 2) >> 1) & 1));  // the MMAs of chunk t - 2 read this buffer
       const uint32_t base = sbase + (uint32_t)b * kBufBytes;
@@ -308,7 +310,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       tc::fence_proxy_async();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(full_bar(b));
-      if (t + 1 < nch) load_chunk(ch0 + t + 1);
+      if (t + 2 < nch) load_chunk(ch0 + t + 2, xa, xb);
       if (t >= 1) {
         const uint32_t due = due_after(t - 1, nch);
         if (due) {
@@ -320,6 +322,12 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
           if (lane == 0) tc::mbar_arrive(drained);
         }
       }
+    };
+    if (nch > 0) load_chunk(ch0, xa0, xb0);
+    if (nch > 1) load_chunk(ch0 + 1, xa1, xb1);
+    for (int64_t t = 0; t < nch; t += 2) {
+      step(t, xa0, xb0);
+      if (t + 1 < nch) step(t + 1, xa1, xb1);
     }
     if (nch > 0) {
       const int64_t t = nch - 1;
@@ -404,10 +412,12 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       }
     }
   } else {
-    double *mine = jb.part + ((int64_t)split * jb.tiles + tile) * (kTM * kTN) + (int64_t)drow * kTN + dcol;
+    // partial tiles as [entry q][thread]: each warp instruction moves 256
+    // contiguous bytes (thread tid holds row drow, columns dcol .. dcol + 31)
+    double *mine = jb.part + ((int64_t)split * jb.tiles + tile) * (kTM * kTN) + tid;
     if (worker) {
 #pragma unroll
-      for (int q = 0; q < 32; ++q) mine[q] = v[q];
+      for (int q = 0; q < 32; ++q) __stcg(mine + q * kSliceThreads, v[q]);
     }
     __threadfence();
     __syncthreads();
@@ -421,21 +431,21 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
 #pragma unroll
       for (int q = 0; q < 32; ++q) v[q] = 0.0;
       // splits added in order 0, 1, ...; loads of two splits in flight at a time
-      const double *src = jb.part + (int64_t)tile * (kTM * kTN) + (int64_t)drow * kTN + dcol;
+      const double *src = jb.part + (int64_t)tile * (kTM * kTN) + tid;
       const int64_t sstride = (int64_t)jb.tiles * (kTM * kTN);
       int sp = 0;
       for (; sp + 2 <= jb.splits; sp += 2) {
         double t0[32], t1[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) t0[q] = __ldcg(src + sp * sstride + q);
+        for (int q = 0; q < 32; ++q) t0[q] = __ldcg(src + sp * sstride + q * kSliceThreads);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) t1[q] = __ldcg(src + (sp + 1) * sstride + q);
+        for (int q = 0; q < 32; ++q) t1[q] = __ldcg(src + (sp + 1) * sstride + q * kSliceThreads);
 #pragma unroll
         for (int q = 0; q < 32; ++q) v[q] = (v[q] + t0[q]) + t1[q];
       }
       if (sp < jb.splits) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] += __ldcg(src + sp * sstride + q);
+        for (int q = 0; q < 32; ++q) v[q] += __ldcg(src + sp * sstride + q * kSliceThreads);
       }
       if (gi < c) {
 #pragma unroll
@@ -595,9 +605,9 @@ gram_tc_job gram_tc_plan(const float *S, int64_t lds, const float *s, int64_t ld
   j.tiles = gram_tc_tile_count(j.c, d, multi);
   const int64_t chunks = std::max<int64_t>(1, (m + kKC - 1) / kKC);
   int64_t splits = std::max<int64_t>(1, ((int64_t)want_ctas + j.tiles - 1) / j.tiles);
-  // at least 16 chunks per CTA and at most 64 K-splits: the last CTA of a
+  // at least 8 chunks per CTA and at most 32 K-splits: the last CTA of a
   // tile adds every split's partial tile
-  splits = std::min<int64_t>(std::min<int64_t>(splits, 64), std::max<int64_t>(1, chunks / 16));
+  splits = std::min<int64_t>(std::min<int64_t>(splits, 32), std::max<int64_t>(1, chunks / 8));
   splits = std::max<int64_t>(splits, (chunks + max_chunks_per_cta - 1) / max_chunks_per_cta);
   j.chunks_per_split = (chunks + splits - 1) / splits;
   j.splits = (int)((chunks + j.chunks_per_split - 1) / j.chunks_per_split);
