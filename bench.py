@@ -645,7 +645,7 @@ def main():
                                   oracle_ratio(p.A.astype(dt_np), p.b.astype(dt_np), r, seed=0,
                                                instance=rank)),
         "solve_info": {"status": sketch_info["status"], "passive_count": sketch_info["passive_count"],
-                       "outer_iters": sketch_info["outer_iters"]},
+                       "outer_iters": sketch_info["outer_iters"], "accurate_mode": sketch_info["accurate_mode"]},
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
@@ -740,7 +740,8 @@ def run_multi(args, ws: int, rank: int, local: int, dev):
         x_opt, _ = ctx.solve(A, bt, r=n)
         xt = X[:, t].contiguous()
         ratios.append(float(ctx.residual(A, bt, xt).item()) / float(ctx.residual(A, bt, x_opt).item()))
-    stat = [P.info_dict(infos[t])["status"] for t in range(nrhs)]
+    tinfo = [P.info_dict(infos[t]) for t in range(nrhs)]
+    stat = [f["status"] for f in tinfo]
 
     kname = "sketch_srht_f32"
     launches, kms = prof[kname]
@@ -769,6 +770,7 @@ def run_multi(args, ws: int, rank: int, local: int, dev):
                                           oracle_ratio(p.A.astype(np.float32), p.B[:, 0].astype(np.float32), r,
                                                        seed=0, instance=rank)),
         "solve_status_nonzero": int(sum(1 for x in stat if x != 0)),
+        "lh_accurate_mode_solves": int(sum(1 for f in tinfo if f["accurate_mode"] > 0)),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
@@ -1136,7 +1138,9 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
         "gpu_launches": int(args.steps * sum(v[0] for v in prof.values()) / nprof),
         "clocks": clk,
         "solve_status_nonzero": int(sum(1 for x in stat if x != 0)),
-        "lh_accurate_restarts": int(sum(int(f.get("restarts", 0)) for f in infos)),
+        # solves whose FP32 end point failed its float-float check and that
+        # continued in the accurate mode (rnnls_info.accurate_mode > 0)
+        "lh_accurate_mode_solves": int(sum(1 for f in infos if f.get("accurate_mode", 0) > 0)),
     }
     out["e2e"] = e2e_batch(args, insts, bufs, dev, local, rank, ws)
     out.update(batch_accuracy(args, insts, bufs, ctx_plain, rank, dev))

@@ -86,6 +86,11 @@ typedef struct rnnls_info {
   double tol;            /* dual tolerance used: 10 eps ||SA||_1 max(r, d) ||Sb||_2 */
   double dual_max;       /* max over j not in P of w_j = (SA'(Sb - SA x))_j at exit */
   double objective;      /* ||SA x - Sb||^2 at exit */
+  int32_t accurate_mode; /* 0: the FP32 iterations' end point passed its float-float
+                            check; 1: a refined passive solve there had z_j <= 0, or
+                            2: a float-float dual there exceeded tol, and the solve
+                            continued with every step refined (see rnnls_solve) */
+  int32_t reserved;      /* zero */
 } rnnls_info;
 
 /* One problem of a batched solve.  All pointers are device pointers. */
@@ -228,8 +233,13 @@ int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double 
  * alpha = min x_j/(x_j - z_j) (ties to the smallest j) and drop x_j <= 0;
  * caps 3d additions and 30d interpolation solves (EMAXITER).
  * Q = SA'SA and q = SA'Sb are formed as rnnls_gram forms them (tensor
- * cores, exact slice products), the Lawson-Hanson decisions use passive
- * solves refined to that accuracy.  Requires 1 <= d <= 1024 (for d
+ * cores, exact slice products).  The iterations run in FP32 (an inverse of
+ * the equilibrated passive block, FP32 duals); their end point is checked
+ * in float-float (a refined passive solve must be positive, the float-float
+ * dual must not exceed tol off the passive set).  If a check fails the
+ * solve continues from that point with every passive solve refined and the
+ * dual in float-float, so every decision is taken on refined values;
+ * info->accurate_mode records which check sent it there.  Requires 1 <= d <= 1024 (for d
  * above about 230 the passive-block inverse is kept in the context's
  * workspace instead of shared memory),
  * r >= 1.  A return of RNNLS_OK means the work was enqueued; the solve's

@@ -44,6 +44,8 @@ class rnnls_info(ctypes.Structure):
         ("tol", ctypes.c_double),
         ("dual_max", ctypes.c_double),
         ("objective", ctypes.c_double),
+        ("accurate_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

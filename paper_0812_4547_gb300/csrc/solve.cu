@@ -522,11 +522,16 @@ __device__ __noinline__ void residual_slots(const lh_vecs &V, int np) {
 // is the inverse of D Q_PP D.  With bordering, B covers slots 0..np-2 and
 // the candidate in slot np-1 enters through v = f3 = B u and the Schur
 // value sc.  Unless `have_initial` (zs already holds an FP32 estimate), one
-// FP32 solve comes first; then `iters` float-float refinement steps.
+// FP32 solve comes first; then `iters` float-float refinement steps, and
+// (iters > 0) more until the correction is below 2^-44 of z in every slot
+// (at most 60 more: the FP32 inverse contracts the error by about
+// cond(D Q_PP D) 2^-24 per step, so ill-conditioned blocks need more).
+constexpr int kMaxExtraRefine = 60;
 __device__ __noinline__ void passive_solve(const lh_vecs &V, lh_shared &sh, int np, bool bordered, float sc,
                                            int iters, bool have_initial = false) {
   const int pb = bordered ? np - 1 : np;
-  for (int step = have_initial ? 1 : 0; step <= iters; ++step) {
+  const int cap = iters > 0 ? iters + kMaxExtraRefine : 0;
+  for (int step = have_initial ? 1 : 0; step <= cap; ++step) {
     if (step > 0) {
       residual_slots(V, np);
       __syncthreads();
@@ -547,11 +552,14 @@ __device__ __noinline__ void passive_solve(const lh_vecs &V, lh_shared &sh, int 
       if (threadIdx.x == 0) V.f2[pb] = yt;
       __syncthreads();
     }
+    int big = 0;
     for (int s = threadIdx.x; s < np; s += kLHThreads) {
       const float dz = V.f2[s] * V.Dsc[V.slotvar[s]];
       V.zs[s] = (step == 0) ? ff_make(dz) : ff_add(V.zs[s], ff_make(dz));
+      big |= (fabsf(dz) > 0x1p-44f * fabsf(V.zs[s].hi)) ? 1 : 0;
     }
-    __syncthreads();
+    // past the fixed steps: stop once no slot moved by more than 2^-44
+    if (__syncthreads_or(big) == 0 && step >= iters && step > 0) break;
   }
 }
 
@@ -694,6 +702,8 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
         inf.tol = tol_d;
         inf.dual_max = 0.0;
         inf.objective = 0.0;
+        inf.accurate_mode = 0;
+        inf.reserved = 0;
         *jb.info = inf;
       }
       return;
@@ -718,6 +728,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
   // float-float, exactly as the FP64 algorithm would.
   int outer = 0, inner = 0;
   bool accurate = false;
+  int accurate_mode = 0;  // which end-point check switched to the accurate mode
   bool go_inner = false;
   for (;;) {
     bool need_inner = true;
@@ -817,6 +828,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
         for (int s = tid; s < p; s += kLHThreads) neg |= ff_le0(V.zs[s]) ? 1 : 0;
         if (__syncthreads_or(neg)) {
           accurate = true;
+          accurate_mode = 1;
           go_inner = true;
           continue;
         }
@@ -828,6 +840,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
         for (int j = tid; j < d; j += kLHThreads) up |= (V.varslot[j] < 0 && ff_gt(V.w[j], tol)) ? 1 : 0;
         if (__syncthreads_or(up)) {
           accurate = true;
+          accurate_mode = 2;
           continue;
         }
         break;
@@ -911,6 +924,8 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
     inf.tol = tol_d;
     inf.dual_max = (dbi >= 0) ? ff_to_double(dbest) : 0.0;
     inf.objective = jb.Qd[(int64_t)jb.qcol * jb.ldq + jb.qcol] - ff_to_double(qxpxw);
+    inf.accurate_mode = accurate_mode;
+    inf.reserved = 0;
     *jb.info = inf;
   }
 }

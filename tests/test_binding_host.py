@@ -54,9 +54,9 @@ def test_leading_dimension(n, d):
 
 
 def test_info_dict_decodes_the_struct():
-    inf = P.rnnls_info(3, 11, 17, 5, 1.5e-12, -2.0, 42.25)
+    inf = P.rnnls_info(3, 11, 17, 5, 1.5e-12, -2.0, 42.25, 2, 0)
     raw = torch.frombuffer(bytearray(bytes(inf)), dtype=torch.uint8)
-    assert raw.numel() == P.INFO_BYTES == ctypes.sizeof(P.rnnls_info)
+    assert raw.numel() == P.INFO_BYTES == ctypes.sizeof(P.rnnls_info) == 48
     got = P.info_dict(raw)
     assert got == {"status": 3, "outer_iters": 11, "inner_iters": 17, "passive_count": 5, "tol": 1.5e-12,
-                   "dual_max": -2.0, "objective": 42.25}
+                   "dual_max": -2.0, "objective": 42.25, "accurate_mode": 2, "reserved": 0}
