@@ -46,12 +46,30 @@ def test_binding_names_match_header(libpath):
         assert hasattr(lib, name)
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """Every field offset and struct size of the ctypes mirrors equals what a
+    C compiler makes of include/rnnls.h."""
     from paper_0812_4547_gb300 import _binding
 
-    # rnnls_info: 4 int32 then 3 doubles; rnnls_problem: 7 pointer-sized fields
-    assert ctypes.sizeof(_binding.rnnls_info) == 40
-    assert ctypes.sizeof(_binding.rnnls_problem) == 56
+    structs = [_binding.rnnls_info, _binding.rnnls_problem, _binding.rnnls_sketch_job, _binding.rnnls_kernel_time]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "rnnls.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'  printf("{n} %zu\\n", sizeof({n}));')
+        for f in st._fields_:
+            lines.append(f'  printf("{n}.{f[0]} %zu\\n", offsetof({n}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(got[n]) == ctypes.sizeof(st), n
+        for f in st._fields_:
+            assert int(got[f"{n}.{f[0]}"]) == getattr(st, f[0]).offset, (n, f[0])
 
 
 def test_strerror_needs_no_device(libpath):
