@@ -274,6 +274,30 @@ int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double
 int rnnls_gram(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *Q,
                double *colabs);
 
+/* The small NNLS problem of Alg. 1 step 5 by an iterative method on the
+ * quadratic-programming form of Sec. 3.4 (min x'Qx - 2q'x over x >= 0 with
+ * Q = SA'SA, q = SA'Sb formed as rnnls_gram forms them), for d beyond the
+ * active-set solve's limit: accelerated projected gradient (FISTA) with
+ * gradient-based restarts on the diagonally equilibrated problem
+ * (y = x / D, D = diag(Q)^-1/2), each iteration one O(d^2) product with Q~
+ * (float-float) spread over all SMs in one cooperative launch.
+ * Stops when the equilibrated gradient map is small:
+ *   max_j L |z_j - max(0, z_j - g_j / L)| <= tol * max_j |D_j q_j|
+ * (L >= the largest eigenvalue of DQD), or after max_iter iterations.
+ * The result approaches the unique minimiser (SA of full column rank) at a
+ * rate that depends on cond(DQD); it is not the exact active set of
+ * rnnls_solve, but within the stated residual of it.
+ * SA: r x d FP32 column-major (ldsa >= r), Sb: r, device; x: device FP64 d;
+ * info (device, nullable): status (OK, EMAXITER, ENONFINITE, ETIMEOUT when
+ * the launch's grid barrier gave up), outer_iters = iterations,
+ * inner_iters = restarts, passive_count = positive entries, tol = the
+ * residual threshold used, dual_max = max of q - Qx over the zero entries,
+ * objective = ||SA x - Sb||^2.  Requires 1 <= d <= 8192 (EUNSUPPORTED
+ * above), tol > 0, max_iter >= 1.  Errors: EINVAL, EUNSUPPORTED, ENOMEM,
+ * ECUDA. */
+int rnnls_solve_pg(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
+                   rnnls_info *info, double tol, int max_iter);
+
 /* The small NNLS problems of Alg. 1 step 5 for nrhs targets that share one
  * sketch (rnnls_sketch_multi): X[:, t] = argmin_{x >= 0} ||SA x - SB[:, t]||_2
  * for t < nrhs, each by the Lawson-Hanson method of rnnls_solve with the

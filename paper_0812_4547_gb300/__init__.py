@@ -189,6 +189,21 @@ class Context:
         fn(self.handle, SA.data_ptr(), _ld(SA), Sb.data_ptr(), rr, d, x.data_ptr(), info.data_ptr())
         return x, info
 
+    def solve_pg(self, SA, Sb, r: int | None = None, x=None, info=None, tol: float = 1e-12, max_iter: int = 50000):
+        """x ~ argmin_{x>=0} ||SA x - Sb||^2 by accelerated projected gradient on the
+        quadratic-programming form (d up to 8192); returns (x, info bytes)."""
+        torch = _torch()
+        SA = colmajor(SA)
+        rr = SA.shape[0] if r is None else r
+        d = SA.shape[1]
+        if x is None:
+            x = torch.empty(d, dtype=torch.float64, device=SA.device)
+        if info is None:
+            info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=SA.device)
+        B.rnnls_solve_pg(self.handle, SA.data_ptr(), _ld(SA), Sb.data_ptr(), rr, d, x.data_ptr(), info.data_ptr(),
+                         tol, max_iter)
+        return x, info
+
     def gram(self, SA, Sb, r: int | None = None, Q=None, colabs=None):
         """Sketch moments Q = [SA | Sb]'[SA | Sb] ((d+1) x (d+1), FP64) and the
         column 1-norms of SA; returns (Q, colabs), device tensors."""

@@ -32,6 +32,7 @@ EXPORTS = (
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
     "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted", "rnnls_set_plan_event", "rnnls_gram",
+    "rnnls_solve_pg",
 )
 
 
@@ -119,6 +120,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_solve_batched.argtypes = [P, ctypes.POINTER(rnnls_problem), I64, U32]
         L.rnnls_solve_multi.argtypes = [P, P, I64, P, I64, I64, I64, I64, P, I64, P]
         L.rnnls_gram.argtypes = [P, P, I64, P, I64, I64, P, P]
+        L.rnnls_solve_pg.argtypes = [P, P, I64, P, I64, I64, P, P, ctypes.c_double, I32]
         L.rnnls_sketch_batched.argtypes = [P, ctypes.POINTER(rnnls_sketch_job), I64]
         L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_boosted.argtypes = [P, P, I64, P, I64, I64, I64, U64, U64, I32, P, P, P, P]
@@ -221,6 +223,11 @@ def rnnls_sketch_batched(ctx, jobs) -> None:
 def rnnls_gram(ctx, SA, ldsa, Sb, r, d, Q, colabs) -> None:
     check(lib().rnnls_gram(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
                            ctypes.c_void_p(Q), ctypes.c_void_p(colabs)), "rnnls_gram")
+
+
+def rnnls_solve_pg(ctx, SA, ldsa, Sb, r, d, x, info, tol, max_iter) -> None:
+    check(lib().rnnls_solve_pg(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
+                               ctypes.c_void_p(x), ctypes.c_void_p(info), tol, max_iter), "rnnls_solve_pg")
 
 
 def rnnls_solve_multi(ctx, SA, ldsa, SB, ldsb, r, d, nrhs, X, ldx, infos) -> None:

@@ -79,7 +79,7 @@ const char *kernel_name(int kid) {
   static const char *names[K_COUNT] = {"sample_rows", "build_plan", "sketch_srht_f32", "sketch_small",
                                        "reduce_partials", "sketch_f64", "gram", "gram_reduce", "colabs",
                                        "lawson_hanson", "residual", "boost_residual", "boost_select",
-                                       "colstats", "gram_tc"};
+                                       "colstats", "gram_tc", "projected_gradient"};
   return (kid >= 0 && kid < K_COUNT) ? names[kid] : "?";
 }
 
@@ -537,6 +537,15 @@ int rnnls_gram(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, i
   device_guard dg;
   RNNLS_CUDA_TRY(dg.set(ctx->device));
   return gram_f32(ctx, SA, ldsa, Sb, r, d, Q, colabs);
+}
+
+int rnnls_solve_pg(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
+                   rnnls_info *info, double tol, int max_iter) {
+  if (!ctx || !SA || !Sb || !x || r < 1 || d < 1 || ldsa < r || !(tol > 0.0) || max_iter < 1) return RNNLS_EINVAL;
+  if (d > kMaxSolvePgD) return RNNLS_EUNSUPPORTED;
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
+  return solve_pg_f32(ctx, SA, ldsa, Sb, r, d, x, info, tol, max_iter);
 }
 
 int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,

@@ -230,6 +230,7 @@ enum kernel_id {
   K_BOOST_SEL,
   K_COLSTATS,
   K_GRAM_TC,
+  K_PG,
   K_COUNT
 };
 const char *kernel_name(int kid);
