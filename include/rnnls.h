@@ -217,6 +217,24 @@ typedef struct rnnls_sketch_job {
  * enqueued then), EUNSUPPORTED (n_raw > 2^28), ENOMEM, ECUDA. */
 int rnnls_sketch_batched(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count);
 
+/* rnnls_sketch for a sparse A held by columns (compressed sparse column),
+ * the form of the paper's term-document data (Sec. 4.1, 4.2): the same iid
+ * rows, signs and 1/sqrt(r) scale, so SA and Sb equal rnnls_sketch's of
+ * the dense A to FP32 rounding.  Column j's non-zeros are rowidx[p], val[p]
+ * for colptr[j] <= p < colptr[j + 1] (int64 offsets, colptr[0] = 0, row
+ * indices ascending within a column and in [0, n_raw); entries that break
+ * the order are skipped); b is dense (n_raw).  All pointers are device
+ * pointers; rowidx and val may be null when every column is empty.
+ * The transform still runs over every row (n log2(4096) additions per
+ * column); the read of A is 8 bytes per non-zero.  Limits: padded n >= 4096
+ * (n_raw > 2048) and r <= 16384 (EUNSUPPORTED otherwise), iid rows only.
+ * idx (nullable) receives the r sampled rows.  Scratch lives in the
+ * context.  Errors: EINVAL (null colptr, b, SA or Sb; a size < 1;
+ * ldsa < r), EUNSUPPORTED, ENOMEM, ECUDA. */
+int rnnls_sketch_csc(rnnls_ctx *ctx, const int64_t *colptr, const int32_t *rowidx, const float *val, const float *b,
+                     int64_t n_raw, int64_t d, int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa,
+                     float *Sb, int32_t *idx);
+
 /* The same sketch in FP64 throughout (for FP64 inputs), with the same
  * arguments, sampling, scale and errors as rnnls_sketch; every sum is
  * formed in FP64. */

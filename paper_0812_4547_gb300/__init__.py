@@ -189,6 +189,23 @@ class Context:
         fn(self.handle, SA.data_ptr(), _ld(SA), Sb.data_ptr(), rr, d, x.data_ptr(), info.data_ptr())
         return x, info
 
+    def sketch_csc(self, colptr, rowidx, val, b, n_raw: int, d: int, r: int, seed: int, instance: int = 0,
+                   SA=None, Sb=None, idx=None):
+        """Sketch of a sparse A in compressed columns (device int64 colptr, int32 rowidx,
+        float32 val) with a dense b; returns (SA, Sb, idx)."""
+        torch = _torch()
+        dev = b.device
+        if SA is None:
+            SA = torch.empty((d, r), dtype=torch.float32, device=dev).t()
+        if Sb is None:
+            Sb = torch.empty(r, dtype=torch.float32, device=dev)
+        if idx is None:
+            idx = torch.empty(r, dtype=torch.int32, device=dev)
+        B.rnnls_sketch_csc(self.handle, colptr.data_ptr(), rowidx.data_ptr() if rowidx.numel() else 0,
+                           val.data_ptr() if val.numel() else 0, b.data_ptr(), n_raw, d, r, seed, instance,
+                           SA.data_ptr(), _ld(SA), Sb.data_ptr(), idx.data_ptr())
+        return SA, Sb, idx
+
     def solve_pg(self, SA, Sb, r: int | None = None, x=None, info=None, tol: float = 1e-12, max_iter: int = 50000):
         """x ~ argmin_{x>=0} ||SA x - Sb||^2 by accelerated projected gradient on the
         quadratic-programming form (d up to 8192); returns (x, info bytes)."""

@@ -32,7 +32,7 @@ EXPORTS = (
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
     "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted", "rnnls_set_plan_event", "rnnls_gram",
-    "rnnls_solve_pg",
+    "rnnls_solve_pg", "rnnls_sketch_csc",
 )
 
 
@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_solve_multi.argtypes = [P, P, I64, P, I64, I64, I64, I64, P, I64, P]
         L.rnnls_gram.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_pg.argtypes = [P, P, I64, P, I64, I64, P, P, ctypes.c_double, I32]
+        L.rnnls_sketch_csc.argtypes = [P, P, P, P, P, I64, I64, I64, U64, U64, P, I64, P, P]
         L.rnnls_sketch_batched.argtypes = [P, ctypes.POINTER(rnnls_sketch_job), I64]
         L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_boosted.argtypes = [P, P, I64, P, I64, I64, I64, U64, U64, I32, P, P, P, P]
@@ -223,6 +224,13 @@ def rnnls_sketch_batched(ctx, jobs) -> None:
 def rnnls_gram(ctx, SA, ldsa, Sb, r, d, Q, colabs) -> None:
     check(lib().rnnls_gram(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
                            ctypes.c_void_p(Q), ctypes.c_void_p(colabs)), "rnnls_gram")
+
+
+def rnnls_sketch_csc(ctx, colptr, rowidx, val, b, n_raw, d, r, seed, instance, SA, ldsa, Sb, idx) -> None:
+    check(lib().rnnls_sketch_csc(ctypes.c_void_p(ctx), ctypes.c_void_p(colptr), ctypes.c_void_p(rowidx),
+                                 ctypes.c_void_p(val), ctypes.c_void_p(b), n_raw, d, r, seed, instance,
+                                 ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), ctypes.c_void_p(idx)),
+          "rnnls_sketch_csc")
 
 
 def rnnls_solve_pg(ctx, SA, ldsa, Sb, r, d, x, info, tol, max_iter) -> None:

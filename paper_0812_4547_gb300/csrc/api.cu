@@ -79,7 +79,8 @@ const char *kernel_name(int kid) {
   static const char *names[K_COUNT] = {"sample_rows", "build_plan", "sketch_srht_f32", "sketch_small",
                                        "reduce_partials", "sketch_f64", "gram", "gram_reduce", "colabs",
                                        "lawson_hanson", "residual", "boost_residual", "boost_select",
-                                       "colstats", "gram_tc", "projected_gradient"};
+                                       "colstats", "gram_tc", "projected_gradient",
+                                       "sketch_csc"};
   return (kid >= 0 && kid < K_COUNT) ? names[kid] : "?";
 }
 
@@ -546,6 +547,16 @@ int rnnls_solve_pg(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *S
   device_guard dg;
   RNNLS_CUDA_TRY(dg.set(ctx->device));
   return solve_pg_f32(ctx, SA, ldsa, Sb, r, d, x, info, tol, max_iter);
+}
+
+int rnnls_sketch_csc(rnnls_ctx *ctx, const int64_t *colptr, const int32_t *rowidx, const float *val, const float *b,
+                     int64_t n_raw, int64_t d, int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa,
+                     float *Sb, int32_t *idx) {
+  if (!ctx || !colptr || !b || !SA || !Sb || n_raw < 1 || d < 1 || r < 1 || ldsa < r) return RNNLS_EINVAL;
+  if (n_raw > ((int64_t)1 << 31) - 1 || d > (1 << 20)) return RNNLS_EUNSUPPORTED;
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
+  return sketch_csc_f32(ctx, colptr, rowidx, val, b, n_raw, d, r, seed, instance, SA, ldsa, Sb, idx);
 }
 
 int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,

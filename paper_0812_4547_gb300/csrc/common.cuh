@@ -231,6 +231,7 @@ enum kernel_id {
   K_COLSTATS,
   K_GRAM_TC,
   K_PG,
+  K_SKETCH_CSC,
   K_COUNT
 };
 const char *kernel_name(int kid);

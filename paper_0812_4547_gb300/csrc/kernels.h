@@ -188,6 +188,10 @@ constexpr int kBoostMaxD = 256;
 int solve_boosted_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d,
                       int64_t r, uint64_t seed, uint64_t instance0, int k, double *x, double *resid, int32_t *best,
                       rnnls_info *info);
+// sketch of a sparse A in compressed columns (sparse.cu)
+int sketch_csc_f32(rnnls_ctx *ctx, const int64_t *colptr, const int32_t *rowidx, const float *val, const float *b,
+                   int64_t n_raw, int64_t d, int64_t r, uint64_t seed, uint64_t instance, float *SA, int64_t ldsa,
+                   float *Sb, int32_t *idx);
 // iterative solve on the quadratic-programming form (pg.cu); d <= kMaxSolvePgD
 constexpr int64_t kMaxSolvePgD = 8192;
 int solve_pg_f32(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
