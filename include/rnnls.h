@@ -104,6 +104,35 @@ typedef struct rnnls_problem {
   rnnls_info *info;  /* out: nullable */
 } rnnls_problem;
 
+/* Launch-shape choices of one context (not part of the method: none of them
+ * changes what is computed beyond FP32 summation order).  0 in a field means
+ * the built-in default; rnnls_set_tuning validates the ranges.
+ *   sketch_sms           SMs the large-n sketch may occupy (default all;
+ *                        the same value as rnnls_set_sketch_sms)
+ *   full_step_min_slots  sampled rows per sketch thread from which the four
+ *                        chunks of a step are first combined by H_4 (a
+ *                        16384-point transform per step) so that each row
+ *                        reads one word instead of four (default 48; rows
+ *                        per thread below 48 live in registers and never use
+ *                        the pass; 48..1024, above 128 meaning never)
+ *   gram_min_chunks      least 32-row chunks per tensor-core Gram CTA of a
+ *                        single problem (default 8; 1..65536)
+ *   gram_max_splits      most K-splits of one Gram tile (default 32; 1..1024)
+ *   batch_gram_chunks    most 32-row chunks per Gram CTA in batched solves
+ *                        (default 128; 1..65536)
+ *   batch_step_cost      the batched sketch's cost of a step's transform in
+ *                        the units of one sampled row per thread, used to
+ *                        cut the block ranges (default 114; 1..100000) */
+typedef struct rnnls_tuning {
+  int32_t sketch_sms;
+  int32_t full_step_min_slots;
+  int32_t gram_min_chunks;
+  int32_t gram_max_splits;
+  int32_t batch_gram_chunks;
+  int32_t batch_step_cost;
+  int32_t reserved[2]; /* zero */
+} rnnls_tuning;
+
 /* Create a context on CUDA device `device` that enqueues on `stream`
  * (a cudaStream_t, borrowed, may be NULL for the legacy default stream).
  * Errors: EINVAL (ctx null), ECUDA (device unusable). */
@@ -123,6 +152,12 @@ int rnnls_set_stream(rnnls_ctx *ctx, void *stream);
  * instead of waiting for it.  Results do not depend on the cap.
  * Errors: EINVAL (ctx null or sms < 0). */
 int rnnls_set_sketch_sms(rnnls_ctx *ctx, int sms);
+
+/* Set / read the context's launch-shape choices (rnnls_tuning).  Later
+ * calls on the context use them.  Errors: EINVAL (null pointer, a field
+ * out of range, reserved not zero). */
+int rnnls_set_tuning(rnnls_ctx *ctx, const rnnls_tuning *t);
+int rnnls_get_tuning(rnnls_ctx *ctx, rnnls_tuning *t);
 
 /* Scheduling aid (not part of the method): `event` (a cudaEvent_t, borrowed;
  * NULL to stop) is recorded on the context stream by every FP32 sketch call

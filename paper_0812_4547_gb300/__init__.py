@@ -189,6 +189,14 @@ class Context:
         fn(self.handle, SA.data_ptr(), _ld(SA), Sb.data_ptr(), rr, d, x.data_ptr(), info.data_ptr())
         return x, info
 
+    def get_tuning(self) -> dict:
+        """The context's launch-shape choices (rnnls_tuning; 0 = built-in default)."""
+        return B.rnnls_get_tuning(self.handle)
+
+    def set_tuning(self, values: dict) -> None:
+        """Replace the context's launch-shape choices (missing knobs: default)."""
+        B.rnnls_set_tuning(self.handle, values)
+
     def sketch_csc(self, colptr, rowidx, val, b, n_raw: int, d: int, r: int, seed: int, instance: int = 0,
                    SA=None, Sb=None, idx=None):
         """Sketch of a sparse A in compressed columns (device int64 colptr, int32 rowidx,

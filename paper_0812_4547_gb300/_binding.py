@@ -32,7 +32,7 @@ EXPORTS = (
     "rnnls_solve_f64", "rnnls_solve_batched", "rnnls_residual", "rnnls_strerror", "rnnls_profile_begin",
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
     "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted", "rnnls_set_plan_event", "rnnls_gram",
-    "rnnls_solve_pg", "rnnls_sketch_csc",
+    "rnnls_solve_pg", "rnnls_sketch_csc", "rnnls_set_tuning", "rnnls_get_tuning",
 )
 
 
@@ -48,6 +48,22 @@ class rnnls_info(ctypes.Structure):
         ("accurate_mode", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
     ]
+
+
+class rnnls_tuning(ctypes.Structure):
+    _fields_ = [
+        ("sketch_sms", ctypes.c_int32),
+        ("full_step_min_slots", ctypes.c_int32),
+        ("gram_min_chunks", ctypes.c_int32),
+        ("gram_max_splits", ctypes.c_int32),
+        ("batch_gram_chunks", ctypes.c_int32),
+        ("batch_step_cost", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
+    ]
+
+
+#: the tuning knobs by name (rnnls_tuning's fields other than reserved)
+TUNING_KNOBS = tuple(f[0] for f in rnnls_tuning._fields_ if f[0] != "reserved")
 
 
 class rnnls_kernel_time(ctypes.Structure):
@@ -122,6 +138,8 @@ def lib() -> ctypes.CDLL:
         L.rnnls_gram.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_pg.argtypes = [P, P, I64, P, I64, I64, P, P, ctypes.c_double, I32]
         L.rnnls_sketch_csc.argtypes = [P, P, P, P, P, I64, I64, I64, U64, U64, P, I64, P, P]
+        L.rnnls_set_tuning.argtypes = [P, ctypes.POINTER(rnnls_tuning)]
+        L.rnnls_get_tuning.argtypes = [P, ctypes.POINTER(rnnls_tuning)]
         L.rnnls_sketch_batched.argtypes = [P, ctypes.POINTER(rnnls_sketch_job), I64]
         L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_boosted.argtypes = [P, P, I64, P, I64, I64, I64, U64, U64, I32, P, P, P, P]
@@ -224,6 +242,20 @@ def rnnls_sketch_batched(ctx, jobs) -> None:
 def rnnls_gram(ctx, SA, ldsa, Sb, r, d, Q, colabs) -> None:
     check(lib().rnnls_gram(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
                            ctypes.c_void_p(Q), ctypes.c_void_p(colabs)), "rnnls_gram")
+
+
+def rnnls_set_tuning(ctx, values: dict) -> None:
+    unknown = set(values) - set(TUNING_KNOBS)
+    if unknown:
+        raise ValueError(f"unknown tuning knobs: {sorted(unknown)}")
+    t = rnnls_tuning(**{k: int(v) for k, v in values.items()})
+    check(lib().rnnls_set_tuning(ctypes.c_void_p(ctx), ctypes.byref(t)), "rnnls_set_tuning")
+
+
+def rnnls_get_tuning(ctx) -> dict:
+    t = rnnls_tuning()
+    check(lib().rnnls_get_tuning(ctypes.c_void_p(ctx), ctypes.byref(t)), "rnnls_get_tuning")
+    return {k: getattr(t, k) for k in TUNING_KNOBS}
 
 
 def rnnls_sketch_csc(ctx, colptr, rowidx, val, b, n_raw, d, r, seed, instance, SA, ldsa, Sb, idx) -> None:

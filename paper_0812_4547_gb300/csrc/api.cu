@@ -305,6 +305,26 @@ int rnnls_set_plan_event(rnnls_ctx *ctx, void *event) {
 int rnnls_set_sketch_sms(rnnls_ctx *ctx, int sms) {
   if (!ctx || sms < 0) return RNNLS_EINVAL;
   ctx->sketch_sms = sms;
+  ctx->tune.sketch_sms = sms;
+  return RNNLS_OK;
+}
+
+int rnnls_set_tuning(rnnls_ctx *ctx, const rnnls_tuning *t) {
+  if (!ctx || !t) return RNNLS_EINVAL;
+  auto in = [](int v, int lo, int hi) { return v == 0 || (v >= lo && v <= hi); };
+  if (t->sketch_sms < 0 || !in(t->full_step_min_slots, 48, 1024) || !in(t->gram_min_chunks, 1, 65536) ||
+      !in(t->gram_max_splits, 1, 1024) || !in(t->batch_gram_chunks, 1, 65536) ||
+      !in(t->batch_step_cost, 1, 100000) || t->reserved[0] != 0 || t->reserved[1] != 0)
+    return RNNLS_EINVAL;
+  ctx->tune = *t;
+  ctx->sketch_sms = t->sketch_sms;
+  return RNNLS_OK;
+}
+
+int rnnls_get_tuning(rnnls_ctx *ctx, rnnls_tuning *t) {
+  if (!ctx || !t) return RNNLS_EINVAL;
+  *t = ctx->tune;
+  t->sketch_sms = ctx->sketch_sms;
   return RNNLS_OK;
 }
 

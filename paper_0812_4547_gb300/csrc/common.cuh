@@ -181,6 +181,7 @@ struct rnnls_ctx {
   cudaStream_t stream;
   int num_sms;
   int sketch_sms;     // SMs the large-n sketch may occupy (0: all)
+  rnnls_tuning tune;  // launch-shape choices (0 fields: defaults)
   int max_smem_optin;
   void *ws;          // device workspace
   size_t ws_bytes;
@@ -212,6 +213,8 @@ int ensure_aux(rnnls_ctx *ctx, size_t bytes);
 // At least `n` zeroed completion counters (kernels leave them at zero).
 int ensure_counters(rnnls_ctx *ctx, size_t n, unsigned int **out);
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+// a tuning field, or its default when 0
+inline int tune_or(int v, int def) { return v > 0 ? v : def; }
 
 // Kernels the profiler tells apart.
 enum kernel_id {

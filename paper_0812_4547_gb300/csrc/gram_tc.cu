@@ -591,7 +591,7 @@ int gram_tc_tile_count(int c, int d, int multi) {
 }
 
 gram_tc_job gram_tc_plan(const float *S, int64_t lds, const float *s, int64_t ldt, int nb, int64_t m, int d,
-                         int multi, int want_ctas, int64_t max_chunks_per_cta) {
+                         int multi, int want_ctas, int64_t max_chunks_per_cta, int min_chunks, int max_splits) {
   gram_tc_job j{};
   j.S = S;
   j.s = s;
@@ -605,9 +605,9 @@ gram_tc_job gram_tc_plan(const float *S, int64_t lds, const float *s, int64_t ld
   j.tiles = gram_tc_tile_count(j.c, d, multi);
   const int64_t chunks = std::max<int64_t>(1, (m + kKC - 1) / kKC);
   int64_t splits = std::max<int64_t>(1, ((int64_t)want_ctas + j.tiles - 1) / j.tiles);
-  // at least 8 chunks per CTA and at most 32 K-splits: the last CTA of a
-  // tile adds every split's partial tile
-  splits = std::min<int64_t>(std::min<int64_t>(splits, 32), std::max<int64_t>(1, chunks / 8));
+  // at least min_chunks chunks per CTA and at most max_splits K-splits (the
+  // last CTA of a tile adds every split's partial tile)
+  splits = std::min<int64_t>(std::min<int64_t>(splits, max_splits), std::max<int64_t>(1, chunks / min_chunks));
   splits = std::max<int64_t>(splits, (chunks + max_chunks_per_cta - 1) / max_chunks_per_cta);
   j.chunks_per_split = (chunks + splits - 1) / splits;
   j.splits = (int)((chunks + j.chunks_per_split - 1) / j.chunks_per_split);
@@ -661,7 +661,8 @@ int gram_tc_launch_batched(rnnls_ctx *ctx, const gram_tc_job *d_jobs, const int6
 
 int gram_f32(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *Q,
              double *colabs) {
-  gram_tc_job gj = gram_tc_plan(SA, ldsa, Sb, r, 1, r, (int)d, 0, ctx->num_sms, (int64_t)1 << 40);
+  gram_tc_job gj = gram_tc_plan(SA, ldsa, Sb, r, 1, r, (int)d, 0, ctx->num_sms, (int64_t)1 << 40,
+                                gram_min_chunks(ctx), gram_max_splits(ctx));
   const size_t D1 = (size_t)d + 1;
   const size_t bytes = 2 * align_up(D1 * D1 * 4, 256) + gram_tc_ws_bytes(gj) + 1024;
   int st = ensure_workspace(ctx, bytes);

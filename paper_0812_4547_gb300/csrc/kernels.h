@@ -159,9 +159,13 @@ __host__ __device__ inline void gram_tc_tile_at(int t, int c, int d, int multi, 
 }
 int gram_tc_tile_count(int c, int d, int multi);
 // Tiles and K-splits of one problem: about want_ctas CTAs, at most
-// max_chunks_per_cta chunks of 32 rows each (pointers left for gram_tc_carve).
+// max_chunks_per_cta and (if the problem allows) at least min_chunks chunks
+// of 32 rows each, at most max_splits splits (pointers left for gram_tc_carve).
 gram_tc_job gram_tc_plan(const float *S, int64_t lds, const float *s, int64_t ldt, int nb, int64_t m, int d,
-                         int multi, int want_ctas, int64_t max_chunks_per_cta);
+                         int multi, int want_ctas, int64_t max_chunks_per_cta, int min_chunks, int max_splits);
+// the context's choices of the above (rnnls_tuning), defaults 8 and 32
+inline int gram_min_chunks(const rnnls_ctx *ctx) { return tune_or(ctx->tune.gram_min_chunks, 8); }
+inline int gram_max_splits(const rnnls_ctx *ctx) { return tune_or(ctx->tune.gram_max_splits, 32); }
 size_t gram_tc_ws_bytes(const gram_tc_job &j);
 void gram_tc_carve(gram_tc_job &j, ws_carver &wc, unsigned int *counters, double *Qd, float *Qhi, float *Qlo,
                    double *colabs);

@@ -380,7 +380,8 @@ __global__ void __launch_bounds__(kPgThreads) pg_kernel(const pg_job jb) {
 
 int solve_pg_f32(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, int64_t r, int64_t d, double *x,
                  rnnls_info *info, double tol, int max_iter) {
-  gram_tc_job gj = gram_tc_plan(SA, ldsa, Sb, r, 1, r, (int)d, 0, ctx->num_sms, (int64_t)1 << 40);
+  gram_tc_job gj = gram_tc_plan(SA, ldsa, Sb, r, 1, r, (int)d, 0, ctx->num_sms, (int64_t)1 << 40,
+                                gram_min_chunks(ctx), gram_max_splits(ctx));
   const size_t D1 = (size_t)d + 1;
   int per_sm = 0;
   RNNLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pg_kernel, kPgThreads,

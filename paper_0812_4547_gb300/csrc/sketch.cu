@@ -216,6 +216,7 @@ struct srht_part {
   int64_t U;    // units
   int64_t T;    // steps = U * J
   int aligned;
+  int full_min;  // rows per thread from which a step's chunks are combined by H_4 first
 };
 
 __host__ __device__ __forceinline__ int64_t part_start(int64_t b, int64_t B, const srht_part &P) {
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t stage_u32 = (raw_u32 + 1023u) & ~1023u;
   float *stage = dyn_smem + (stage_u32 - raw_u32) / 4;
   const int64_t nrow32 = n_raw >> 5;  // whole 32-row lines of a column
-  const bool full = SLOTS > 0 ? (SLOTS >= kFullMinSlots) : (slots >= kFullMinSlots);
+  const bool full = SLOTS > 0 ? (SLOTS >= kFullMinSlots) : (slots >= P.full_min);
 
   if (tid == 0) {
     for (int q = 0; q < kStages; ++q) mbar_init(smem_u32(&mbar[q]), 1);
@@ -938,7 +939,7 @@ struct srht_job {  // 64-byte aligned through its tensor maps
   float *SA, *SB;
   int64_t lda, ldb, ldsa, ldsb, n_raw, J, U, step0, rpg;
   float scale;
-  int d, slots, vec, r;
+  int d, slots, vec, r, full_min;
 };
 
 __device__ __forceinline__ void fence_tensormap_acquire(const void *map) {
@@ -1183,7 +1184,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < 64; ++s) zw[hi | ((uint32_t)s << 5) | (lane ^ (((uint32_t)s & 7u) << 2))] = v[s];
     }
     __syncthreads();
-    const bool full = slots >= kFullMinSlots;
+    const bool full = slots >= J0.full_min;
     if (full) {
       cross_chunk_h4(stage + q * kStageFloats, tid);
       __syncthreads();
@@ -1564,8 +1565,9 @@ struct srht_geom {
   size_t plan_bytes, part_bytes, sign_bytes;
 };
 
-srht_geom plan_geometry(const sketch_args_f32 &a, int sms, bool force_aligned) {
+srht_geom plan_geometry(const sketch_args_f32 &a, int sms, bool force_aligned, int full_min = kFullMinSlots) {
   srht_geom g{};
+  g.P.full_min = full_min;
   g.plan.slots = pick_slots(a.r);
   g.plan.rows_per_group = (int64_t)kThreads * g.plan.slots;
   g.plan.kgroups = (int)((a.r + g.plan.rows_per_group - 1) / g.plan.rows_per_group);
@@ -1613,7 +1615,7 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
     return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
   }
   const int sms = (ctx->sketch_sms > 0) ? std::min(ctx->sketch_sms, num_sms) : num_sms;
-  srht_geom g = plan_geometry(a, sms, false);
+  srht_geom g = plan_geometry(a, sms, false, tune_or(ctx->tune.full_step_min_slots, kFullMinSlots));
   int st = ensure_workspace(ctx, g.part_bytes + g.plan_bytes + g.sign_bytes + 1024);
   if (st) return st;
   ws_carver wc(ctx->ws);
@@ -1677,6 +1679,7 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
     J.n_raw = jb.n_raw; J.J = (jb.n_raw + 4 * (int64_t)kM - 1) / (4 * (int64_t)kM);
     J.U = (int64_t)kgroups * (jb.d + 1); J.step0 = Ttot; J.rpg = rpg; J.scale = (float)(1.0 / sqrt((double)jb.r));
     J.d = (int)jb.d; J.slots = slots; J.r = (int)jb.r; J.SA = jb.SA; J.SB = jb.Sb;
+    J.full_min = tune_or(ctx->tune.full_step_min_slots, kFullMinSlots);
     J.vec = (((uintptr_t)jb.A % 16 == 0) && (jb.lda % 4 == 0) && ((uintptr_t)jb.b % 16 == 0)) ? 1 : 0;
     Ttot += J.U * J.J;
     rpg_max = std::max(rpg_max, rpg);
@@ -1699,9 +1702,10 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
   std::vector<int64_t> starts((size_t)B + 1);
   {
     std::vector<double> wt((size_t)nb), cum((size_t)nb + 1, 0.0);
+    const double step_cost = (double)tune_or(ctx->tune.batch_step_cost, 114);
     for (int t = 0; t < nb; ++t) {
       const srht_job &J = sj[(size_t)t];
-      wt[(size_t)t] = 114.0 + J.slots + 6.0 * (double)J.slots / (double)J.J;
+      wt[(size_t)t] = step_cost + J.slots + 6.0 * (double)J.slots / (double)J.J;
       cum[(size_t)t + 1] = cum[(size_t)t] + wt[(size_t)t] * (double)(J.U * J.J);
     }
     int t = 0;

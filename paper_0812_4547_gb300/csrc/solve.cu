@@ -523,14 +523,19 @@ __device__ __noinline__ void residual_slots(const lh_vecs &V, int np) {
 // the candidate in slot np-1 enters through v = f3 = B u and the Schur
 // value sc.  Unless `have_initial` (zs already holds an FP32 estimate), one
 // FP32 solve comes first; then `iters` float-float refinement steps, and
-// (iters > 0) more until the correction is below 2^-44 of z in every slot
-// (at most 60 more: the FP32 inverse contracts the error by about
-// cond(D Q_PP D) 2^-24 per step, so ill-conditioned blocks need more).
+// (iters > 0) more while the largest relative correction over the slots
+// still halves from one step to the next and exceeds 2^-44 (at most 60
+// more: the FP32 inverse contracts the error by about cond(D Q_PP D) 2^-24
+// per step, so ill-conditioned blocks need more; once the corrections stop
+// shrinking, float-float rounding has been reached).
 constexpr int kMaxExtraRefine = 60;
 __device__ __noinline__ void passive_solve(const lh_vecs &V, lh_shared &sh, int np, bool bordered, float sc,
                                            int iters, bool have_initial = false) {
+  __shared__ unsigned int corr_max[3];  // per step (rotating): largest |dz| / |z| as float bits
   const int pb = bordered ? np - 1 : np;
   const int cap = iters > 0 ? iters + kMaxExtraRefine : 0;
+  if (threadIdx.x == 0) corr_max[0] = corr_max[1] = corr_max[2] = 0u;
+  float prev = INFINITY;
   for (int step = have_initial ? 1 : 0; step <= cap; ++step) {
     if (step > 0) {
       residual_slots(V, np);
@@ -552,15 +557,23 @@ __device__ __noinline__ void passive_solve(const lh_vecs &V, lh_shared &sh, int 
       if (threadIdx.x == 0) V.f2[pb] = yt;
       __syncthreads();
     }
-    int big = 0;
+    float mx = 0.0f;
     for (int s = threadIdx.x; s < np; s += kLHThreads) {
       const float dz = V.f2[s] * V.Dsc[V.slotvar[s]];
       V.zs[s] = (step == 0) ? ff_make(dz) : ff_add(V.zs[s], ff_make(dz));
-      big |= (fabsf(dz) > 0x1p-44f * fabsf(V.zs[s].hi)) ? 1 : 0;
+      mx = fmaxf(mx, fabsf(dz) / fmaxf(fabsf(V.zs[s].hi), 1e-30f));
     }
-    // past the fixed steps: stop once no slot moved by more than 2^-44
-    if (__syncthreads_or(big) == 0 && step >= iters && step > 0) break;
+    // the slot two steps ahead was last read two barriers ago: clear it now
+    if (threadIdx.x == 0) corr_max[(step + 1) % 3] = 0u;
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&corr_max[step % 3], __float_as_uint(mx));
+    __syncthreads();
+    const float cm = __uint_as_float(corr_max[step % 3]);
+    // past the fixed steps: stop once converged or no longer converging
+    if (step >= iters && step > 0 && (cm <= 0x1p-44f || cm > 0.5f * prev)) break;
+    prev = cm;
   }
+  __syncthreads();  // every thread has read the last step's maximum before a later call clears it
 }
 
 // Drop slot s (Schur-complement downdate of B), then move the last slot
@@ -1061,7 +1074,7 @@ int solve_one(rnnls_ctx *ctx, const T *SA, int64_t ldsa, const T *Sb, int64_t r,
   float *Bg = nullptr;
   if (sizeof(T) == 4) {
     gram_tc_job gj = gram_tc_plan((const float *)SA, ldsa, (const float *)Sb, r, 1, r, (int)d, 0, ctx->num_sms,
-                                  (int64_t)1 << 40);
+                                  (int64_t)1 << 40, gram_min_chunks(ctx), gram_max_splits(ctx));
     const size_t bytes = align_up(D1 * D1 * 8, 256) + 2 * align_up(D1 * D1 * 4, 256) + align_up((size_t)d * 8, 256) +
                          gram_tc_ws_bytes(gj) + lh_bg_bytes(ctx, (int)d) + 1024;
     st = ensure_workspace(ctx, bytes);
@@ -1135,8 +1148,8 @@ int solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, 
   return solve_one<double>(ctx, SA, ldsa, Sb, r, d, x, info);
 }
 
-// Maximum 32-row chunks per Gram CTA in a batched launch (4096 rows), so
-// that the CTAs of a batch of uneven problems carry comparable work.
+// Default maximum of 32-row chunks per Gram CTA in a batched launch (4096
+// rows), so that the CTAs of a batch of uneven problems carry comparable work.
 constexpr int64_t kBatchChunksPerCta = 128;
 
 int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
@@ -1152,7 +1165,9 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   for (int64_t i = 0; i < count; ++i) {
     const rnnls_problem &pb = probs[i];
     const int di = (int)pb.d;
-    gjs[(size_t)i] = gram_tc_plan(pb.SA, pb.ldsa, pb.Sb, pb.r, 1, pb.r, di, 0, 1, kBatchChunksPerCta);
+    gjs[(size_t)i] = gram_tc_plan(pb.SA, pb.ldsa, pb.Sb, pb.r, 1, pb.r, di, 0, 1,
+                                  tune_or(ctx->tune.batch_gram_chunks, kBatchChunksPerCta), gram_min_chunks(ctx),
+                                  gram_max_splits(ctx));
     const size_t D1 = di + 1;
     bytes += align_up(D1 * D1 * 8, 256) + 2 * align_up(D1 * D1 * 4, 256) + align_up((size_t)di * 8, 256) +
              gram_tc_ws_bytes(gjs[(size_t)i]) + lh_bg_bytes(ctx, di) + 1024;
@@ -1224,7 +1239,8 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
   // one Gram of [SA | SB] (the target-by-target block only on its diagonal),
   // then one Lawson-Hanson block per target, all reading the same Q
   const int64_t D1 = d + nrhs;
-  gram_tc_job gj = gram_tc_plan(SA, ldsa, SB, ldsb, (int)nrhs, r, (int)d, 1, ctx->num_sms, (int64_t)1 << 40);
+  gram_tc_job gj = gram_tc_plan(SA, ldsa, SB, ldsb, (int)nrhs, r, (int)d, 1, ctx->num_sms, (int64_t)1 << 40,
+                                gram_min_chunks(ctx), gram_max_splits(ctx));
   const bool bfit = lh_b_fits(ctx, (int)d);
   const size_t bytes = align_up((size_t)(D1 * D1) * 8, 256) + 2 * align_up((size_t)(D1 * D1) * 4, 256) +
                        align_up((size_t)D1 * 8, 256) + gram_tc_ws_bytes(gj) +

@@ -51,7 +51,8 @@ def test_struct_layouts_match_header(tmp_path):
     C compiler makes of include/rnnls.h."""
     from paper_0812_4547_gb300 import _binding
 
-    structs = [_binding.rnnls_info, _binding.rnnls_problem, _binding.rnnls_sketch_job, _binding.rnnls_kernel_time]
+    structs = [_binding.rnnls_info, _binding.rnnls_problem, _binding.rnnls_sketch_job, _binding.rnnls_kernel_time,
+               _binding.rnnls_tuning]
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "rnnls.h"', "int main(void) {"]
     for st in structs:
         n = st.__name__
