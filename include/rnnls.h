@@ -372,6 +372,20 @@ int rnnls_solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float
  * EUNSUPPORTED (a d above 1024), ENOMEM, ECUDA. */
 int rnnls_solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count, uint32_t flags);
 
+/* rnnls_solve_batched with the descriptor array in DEVICE memory (count
+ * rnnls_problem entries, device pointers inside), as a scheduler that
+ * builds its batches on the GPU or inside a CUDA graph would hold it.  The
+ * host cannot read the descriptors, so it passes bounds: every problem must
+ * have 1 <= r <= max_r and 1 <= d <= max_d (max_d <= 1024).  A kernel plans
+ * the batch on the device (tiles, K-splits, offsets) and every problem gets
+ * a workspace slot of the bounds' size; a descriptor outside the bounds or
+ * with a null pointer is not solved and its info (when given) gets status
+ * RNNLS_EINVAL.  Results equal rnnls_solve_batched's.  Errors: EINVAL
+ * (null ctx, null array with count > 0, count < 0, a bound < 1, flags != 0),
+ * EUNSUPPORTED (max_d > 1024), ENOMEM, ECUDA. */
+int rnnls_solve_batched_device(rnnls_ctx *ctx, const rnnls_problem *d_probs, int64_t count, int64_t max_r,
+                               int64_t max_d, uint32_t flags);
+
 /* Repeated RandomizedNNLS (the footnote to Theorem 1 in Sec. 1: a few
  * independent repetitions raise the success probability of the (1 + eps)
  * bound from 1/2 to at least 1 - 2^-k).  Run j (j < k) is Alg. 1 exactly as

@@ -33,6 +33,7 @@ EXPORTS = (
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
     "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted", "rnnls_set_plan_event", "rnnls_gram",
     "rnnls_solve_pg", "rnnls_sketch_csc", "rnnls_set_tuning", "rnnls_get_tuning",
+    "rnnls_solve_batched_device",
 )
 
 
@@ -138,6 +139,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_gram.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_pg.argtypes = [P, P, I64, P, I64, I64, P, P, ctypes.c_double, I32]
         L.rnnls_sketch_csc.argtypes = [P, P, P, P, P, I64, I64, I64, U64, U64, P, I64, P, P]
+        L.rnnls_solve_batched_device.argtypes = [P, P, I64, I64, I64, U32]
         L.rnnls_set_tuning.argtypes = [P, ctypes.POINTER(rnnls_tuning)]
         L.rnnls_get_tuning.argtypes = [P, ctypes.POINTER(rnnls_tuning)]
         L.rnnls_sketch_batched.argtypes = [P, ctypes.POINTER(rnnls_sketch_job), I64]
@@ -242,6 +244,11 @@ def rnnls_sketch_batched(ctx, jobs) -> None:
 def rnnls_gram(ctx, SA, ldsa, Sb, r, d, Q, colabs) -> None:
     check(lib().rnnls_gram(ctypes.c_void_p(ctx), ctypes.c_void_p(SA), ldsa, ctypes.c_void_p(Sb), r, d,
                            ctypes.c_void_p(Q), ctypes.c_void_p(colabs)), "rnnls_gram")
+
+
+def rnnls_solve_batched_device(ctx, d_probs, count, max_r, max_d, flags: int = 0) -> None:
+    check(lib().rnnls_solve_batched_device(ctypes.c_void_p(ctx), ctypes.c_void_p(d_probs), count, max_r, max_d,
+                                           flags), "rnnls_solve_batched_device")
 
 
 def rnnls_set_tuning(ctx, values: dict) -> None:

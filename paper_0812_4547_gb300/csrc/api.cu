@@ -579,6 +579,15 @@ int rnnls_sketch_csc(rnnls_ctx *ctx, const int64_t *colptr, const int32_t *rowid
   return sketch_csc_f32(ctx, colptr, rowidx, val, b, n_raw, d, r, seed, instance, SA, ldsa, Sb, idx);
 }
 
+int rnnls_solve_batched_device(rnnls_ctx *ctx, const rnnls_problem *d_probs, int64_t count, int64_t max_r,
+                               int64_t max_d, uint32_t flags) {
+  if (!ctx || (!d_probs && count > 0) || count < 0 || max_r < 1 || max_d < 1 || flags != 0) return RNNLS_EINVAL;
+  if (max_d > kMaxSolveD || count > ((int64_t)1 << 31) - 1) return RNNLS_EUNSUPPORTED;
+  device_guard dg;
+  RNNLS_CUDA_TRY(dg.set(ctx->device));
+  return solve_batched_device(ctx, d_probs, count, max_r, max_d);
+}
+
 int rnnls_solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d,
                     double *x, rnnls_info *info) {
   if (!ctx || !SA || !Sb || !x || r < 1 || d < 1 || ldsa < r) return RNNLS_EINVAL;

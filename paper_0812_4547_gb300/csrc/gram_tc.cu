@@ -471,8 +471,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel_one(const gram_t
 // first[p] <= b < first[p + 1] (tiles x splits CTAs each).
 __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel_batched(const gram_tc_job *__restrict__ jobs,
                                                                         const int64_t *__restrict__ first, int count) {
-  int lo = 0, hi = count - 1;
   const int64_t bid = blockIdx.x;
+  if (bid >= first[count]) return;  // a grid sized by an upper bound
+  int lo = 0, hi = count - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (first[mid] <= bid)
@@ -566,8 +567,9 @@ __global__ void __launch_bounds__(kStatThreads) colstats_kernel_one(const gram_t
 
 __global__ void __launch_bounds__(kStatThreads) colstats_kernel_batched(const gram_tc_job *__restrict__ jobs,
                                                                         const int64_t *__restrict__ first, int count) {
-  int lo = 0, hi = count - 1;
   const int64_t bid = blockIdx.x;
+  if (bid >= first[count]) return;  // a grid sized by an upper bound
+  int lo = 0, hi = count - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (first[mid] <= bid)
@@ -583,13 +585,6 @@ smem_attr g_tc_one_attr, g_tc_batched_attr;
 
 }  // namespace
 
-int gram_tc_tile_count(int c, int d, int multi) {
-  int n = 0;
-  for (int mt = 0; mt * kTM < c; ++mt)
-    for (int nt = 0; nt * kTN < c; ++nt) n += gram_tc_tile_needed(mt, nt, c, d, multi) ? 1 : 0;
-  return n;
-}
-
 gram_tc_job gram_tc_plan(const float *S, int64_t lds, const float *s, int64_t ldt, int nb, int64_t m, int d,
                          int multi, int want_ctas, int64_t max_chunks_per_cta, int min_chunks, int max_splits) {
   gram_tc_job j{};
@@ -603,14 +598,8 @@ gram_tc_job gram_tc_plan(const float *S, int64_t lds, const float *s, int64_t ld
   j.c = d + nb;
   j.multi = multi;
   j.tiles = gram_tc_tile_count(j.c, d, multi);
-  const int64_t chunks = std::max<int64_t>(1, (m + kKC - 1) / kKC);
-  int64_t splits = std::max<int64_t>(1, ((int64_t)want_ctas + j.tiles - 1) / j.tiles);
-  // at least min_chunks chunks per CTA and at most max_splits K-splits (the
-  // last CTA of a tile adds every split's partial tile)
-  splits = std::min<int64_t>(std::min<int64_t>(splits, max_splits), std::max<int64_t>(1, chunks / min_chunks));
-  splits = std::max<int64_t>(splits, (chunks + max_chunks_per_cta - 1) / max_chunks_per_cta);
-  j.chunks_per_split = (chunks + splits - 1) / splits;
-  j.splits = (int)((chunks + j.chunks_per_split - 1) / j.chunks_per_split);
+  // the last CTA of a tile adds every split's partial tile: splits are capped
+  gram_tc_splits(m, j.tiles, want_ctas, max_chunks_per_cta, min_chunks, max_splits, j.splits, j.chunks_per_split);
   const auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
   j.vec4 = (al(S) && (lds % 4) == 0 && (nb == 0 || (al(s) && (nb == 1 || (ldt % 4) == 0)))) ? 1 : 0;
   return j;

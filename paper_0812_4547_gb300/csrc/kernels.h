@@ -157,7 +157,29 @@ __host__ __device__ inline void gram_tc_tile_at(int t, int c, int d, int multi, 
       }
   mt = nt = 0;
 }
-int gram_tc_tile_count(int c, int d, int multi);
+__host__ __device__ inline int gram_tc_tile_count(int c, int d, int multi) {
+  int n = 0;
+  for (int mt = 0; mt * kGramTileM < c; ++mt)
+    for (int nt = 0; nt * kGramTileN < c; ++nt) n += gram_tc_tile_needed(mt, nt, c, d, multi) ? 1 : 0;
+  return n;
+}
+// K-splits of a problem of m rows with `tiles` tiles (fields splits and
+// chunks_per_split of gram_tc_job): about want_ctas CTAs, at least
+// min_chunks chunks of 32 rows per CTA when the problem allows, at most
+// max_splits splits, at most max_chunks_per_cta chunks per CTA.
+__host__ __device__ inline void gram_tc_splits(int64_t m, int tiles, int want_ctas, int64_t max_chunks_per_cta,
+                                               int min_chunks, int max_splits, int &splits_out, int64_t &cps_out) {
+  const int64_t chunks = m > 32 ? (m + 31) / 32 : 1;
+  int64_t splits = ((int64_t)want_ctas + tiles - 1) / tiles;
+  if (splits < 1) splits = 1;
+  const int64_t by_min = chunks / min_chunks > 1 ? chunks / min_chunks : 1;
+  if (splits > max_splits) splits = max_splits;
+  if (splits > by_min) splits = by_min;
+  const int64_t by_max = (chunks + max_chunks_per_cta - 1) / max_chunks_per_cta;
+  if (splits < by_max) splits = by_max;
+  cps_out = (chunks + splits - 1) / splits;
+  splits_out = (int)((chunks + cps_out - 1) / cps_out);
+}
 // Tiles and K-splits of one problem: about want_ctas CTAs, at most
 // max_chunks_per_cta and (if the problem allows) at least min_chunks chunks
 // of 32 rows each, at most max_splits splits (pointers left for gram_tc_carve).
@@ -183,6 +205,8 @@ int solve_f32(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *Sb, in
 int solve_f64(rnnls_ctx *ctx, const double *SA, int64_t ldsa, const double *Sb, int64_t r, int64_t d, double *x,
               rnnls_info *info);
 int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count);
+// the same from a device-resident descriptor array (plan made on the device)
+int solve_batched_device(rnnls_ctx *ctx, const rnnls_problem *d_probs, int64_t count, int64_t max_r, int64_t max_d);
 // nrhs targets sharing one sketch SA: X (d x nrhs, leading dimension ldx), infos nrhs (nullable)
 int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, int64_t ldsb, int64_t r, int64_t d,
                 int64_t nrhs, double *X, int64_t ldx, rnnls_info *infos);

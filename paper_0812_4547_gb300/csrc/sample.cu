@@ -5,8 +5,6 @@
 //   iid       : draw k -> row (word k of stream 2) >> (64 - L)
 //   Bernoulli : row i kept iff word i of stream 1 < r * 2^(64 - L), i.e. with
 //               probability r/n (Alg. 1 step 2); all rows when r >= n.
-#include <cub/block/block_reduce.cuh>
-#include <cub/block/block_scan.cuh>
 
 #include "kernels.h"
 
@@ -53,6 +51,39 @@ __device__ __forceinline__ uint32_t bernoulli_keep4(uint64_t seed, uint64_t inst
   return bits;
 }
 
+// Block-wide sum and exclusive prefix sum over kBernThreads threads: warp
+// shuffles, then one pass over the per-warp totals in shared memory.
+constexpr int kBernWarps = kBernThreads / 32;
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_sum(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+// Exclusive prefix of v over the block (thread order); *total gets the sum.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_sum(T v, T *total) {
+  __shared__ T warp_tot[kBernWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T inc = warp_inclusive_sum(v);
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const T t = (lane < kBernWarps) ? warp_tot[lane] : (T)0;
+    const T ti = warp_inclusive_sum(t);
+    if (lane < kBernWarps) warp_tot[lane] = ti - t;  // exclusive prefix of the warp totals
+    if (lane == kBernWarps - 1) *total = ti;
+  }
+  __syncthreads();
+  const T out = warp_tot[warp] + inc - v;
+  __syncthreads();  // warp_tot reusable by the caller's next call
+  return out;
+}
+
 __global__ void __launch_bounds__(kBernThreads) bernoulli_count_kernel(uint64_t seed, uint64_t inst, int L,
                                                                        int64_t r, uint32_t *__restrict__ tile_count) {
   const int64_t n = (int64_t)1 << L;
@@ -63,25 +94,21 @@ __global__ void __launch_bounds__(kBernThreads) bernoulli_count_kernel(uint64_t 
     if (n < 4) bits &= (1u << n) - 1u;
     c = __popc(bits);
   }
-  typedef cub::BlockReduce<uint32_t, kBernThreads> reduce_t;
-  __shared__ typename reduce_t::TempStorage tmp;
-  const uint32_t tot = reduce_t(tmp).Sum(c);
+  __shared__ uint32_t tot;
+  block_exclusive_sum<uint32_t>(c, &tot);
   if (threadIdx.x == 0) tile_count[blockIdx.x] = tot;
 }
 
 __global__ void __launch_bounds__(kBernThreads) bernoulli_scan_kernel(const uint32_t *__restrict__ tile_count,
                                                                       int64_t tiles, int64_t *__restrict__ tile_off,
                                                                       int64_t *__restrict__ d_count) {
-  typedef cub::BlockScan<int64_t, kBernThreads> scan_t;
-  __shared__ typename scan_t::TempStorage tmp;
-  __shared__ int64_t carry;
+  __shared__ int64_t carry, agg;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (int64_t base = 0; base < tiles; base += kBernThreads) {
     const int64_t t = base + threadIdx.x;
-    int64_t v = (t < tiles) ? (int64_t)tile_count[t] : 0;
-    int64_t ex, agg;
-    scan_t(tmp).ExclusiveSum(v, ex, agg);
+    const int64_t v = (t < tiles) ? (int64_t)tile_count[t] : 0;
+    const int64_t ex = block_exclusive_sum<int64_t>(v, &agg);
     if (t < tiles) tile_off[t] = carry + ex;
     __syncthreads();
     if (threadIdx.x == 0) carry += agg;
@@ -100,10 +127,8 @@ __global__ void __launch_bounds__(kBernThreads) bernoulli_write_kernel(uint64_t 
     bits = bernoulli_keep4(seed, inst, L, r, j);
     if (n < 4) bits &= (1u << n) - 1u;
   }
-  typedef cub::BlockScan<uint32_t, kBernThreads> scan_t;
-  __shared__ typename scan_t::TempStorage tmp;
-  uint32_t ex;
-  scan_t(tmp).ExclusiveSum((uint32_t)__popc(bits), ex);
+  __shared__ uint32_t tot;
+  const uint32_t ex = block_exclusive_sum<uint32_t>((uint32_t)__popc(bits), &tot);
   int64_t pos = tile_off[blockIdx.x] + ex;
 #pragma unroll
   for (int w = 0; w < 4; ++w) {

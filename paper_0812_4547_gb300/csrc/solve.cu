@@ -948,6 +948,7 @@ __global__ void __launch_bounds__(kLHThreads, 2) lh_kernel(const lh_job *__restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ lh_shared sh;
   const lh_job jb = jobs[blockIdx.x];
+  if (jb.d <= 0) return;  // a problem the device-side plan refused (its info says so)
   lh_block(jb, smem_raw, sh, max_outer_mul * jb.d, max_inner_mul * jb.d);
 }
 
@@ -1232,6 +1233,194 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   st = gram_tc_launch_batched(ctx, d_gj, d_first_col, d_first_cta, (int)count, cols, ctas);
   if (st) return st;
   return lh_launch(ctx, d_jobs, count, smem);
+}
+
+// ---------------------------------------------------------------------------
+// Batched solve from a device-resident descriptor array: the plan (tiles,
+// K-splits, CTA and column offsets, workspace slots) is made on the device,
+// within host-given bounds max_r, max_d; every problem owns a workspace slot
+// of the bound's size.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct dev_plan_args {
+  const rnnls_problem *probs;
+  int64_t count, max_r;
+  int max_d;
+  int qfit_max, bfit_max;      // largest d whose Q / passive inverse fits in shared memory
+  int min_chunks, max_splits;  // the context's Gram choices
+  int64_t batch_chunks;
+  char *slots;                 // count slots of slot_bytes
+  size_t slot_bytes, off_qhi, off_qlo, off_colabs, off_cs, off_cu, off_part, off_bg;
+  unsigned int *counters;      // count x tiles_max
+  int tiles_max;
+  gram_tc_job *gjobs;
+  lh_job *ljobs;
+  int64_t *first_col, *first_cta;  // count + 1 each
+  int64_t *tmp;                    // 2 count scratch: columns and CTAs per problem
+};
+
+// One block: validate and plan every problem, then prefix sums in order.
+__global__ void __launch_bounds__(256) plan_batched_device_kernel(const dev_plan_args a) {
+  for (int64_t p = threadIdx.x; p < a.count; p += 256) {
+    const rnnls_problem pb = a.probs[p];
+    const bool ok = pb.SA && pb.Sb && pb.x && pb.r >= 1 && pb.r <= a.max_r && pb.d >= 1 && pb.d <= a.max_d &&
+                    pb.ldsa >= pb.r;
+    char *slot = a.slots + (size_t)p * a.slot_bytes;
+    const int d = ok ? (int)pb.d : 0;
+    const int c = d + 1;
+    gram_tc_job j{};
+    lh_job l{};
+    if (ok) {
+      j.S = pb.SA;
+      j.s = pb.Sb;
+      j.lds = pb.ldsa;
+      j.ldt = pb.r;
+      j.nb = 1;
+      j.m = pb.r;
+      j.d = d;
+      j.c = c;
+      j.multi = 0;
+      j.tiles = gram_tc_tile_count(c, d, 0);
+      gram_tc_splits(pb.r, j.tiles, 1, a.batch_chunks, a.min_chunks, a.max_splits, j.splits, j.chunks_per_split);
+      j.vec4 = ((((uintptr_t)pb.SA) & 15u) == 0 && (pb.ldsa % 4) == 0 && (((uintptr_t)pb.Sb) & 15u) == 0) ? 1 : 0;
+      j.Qd = (double *)slot;
+      j.Qhi = (float *)(slot + a.off_qhi);
+      j.Qlo = (float *)(slot + a.off_qlo);
+      j.colabs = (double *)(slot + a.off_colabs);
+      j.colscale = (float *)(slot + a.off_cs);
+      j.colunscale = (float *)(slot + a.off_cu);
+      j.part = j.splits > 1 ? (double *)(slot + a.off_part) : nullptr;
+      j.counters = a.counters + (size_t)p * a.tiles_max;
+      l.Qd = j.Qd;
+      l.Qhi = j.Qhi;
+      l.Qlo = j.Qlo;
+      l.ldq = c;
+      l.qcol = d;
+      l.colabs = j.colabs;
+      l.r = pb.r;
+      l.d = d;
+      l.x = pb.x;
+      l.info = pb.info;
+      l.q_smem = d <= a.qfit_max ? 1 : 0;
+      l.Bg = d > a.bfit_max ? (float *)(slot + a.off_bg) : nullptr;
+    } else if (pb.info) {
+      rnnls_info inf{};
+      inf.status = RNNLS_EINVAL;
+      *pb.info = inf;
+    }
+    a.gjobs[p] = j;
+    a.ljobs[p] = l;
+    a.tmp[p] = ok ? c : 0;
+    a.tmp[a.count + p] = ok ? (int64_t)j.tiles * j.splits : 0;
+  }
+  __syncthreads();
+  // exclusive prefix sums of columns and CTAs, in problem order
+  __shared__ int64_t carry[2];
+  __shared__ int64_t warp_tot[2][8];
+  if (threadIdx.x < 2) carry[threadIdx.x] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = 0; base < a.count; base += 256) {
+    const int64_t p = base + threadIdx.x;
+    int64_t v[2], inc[2];
+    for (int k = 0; k < 2; ++k) {
+      v[k] = p < a.count ? a.tmp[k * a.count + p] : 0;
+      inc[k] = v[k];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, inc[k], o);
+        if (lane >= o) inc[k] += u;
+      }
+      if (lane == 31) warp_tot[k][warp] = inc[k];
+    }
+    __syncthreads();
+    for (int k = 0; k < 2; ++k) {
+      int64_t before = carry[k];
+      for (int w = 0; w < warp; ++w) before += warp_tot[k][w];
+      if (p < a.count) (k == 0 ? a.first_col : a.first_cta)[p] = before + inc[k] - v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      int64_t t = 0;
+      for (int w = 0; w < 8; ++w) t += warp_tot[threadIdx.x][w];
+      carry[threadIdx.x] += t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.first_col[a.count] = carry[0];
+    a.first_cta[a.count] = carry[1];
+  }
+}
+
+}  // namespace
+
+int solve_batched_device(rnnls_ctx *ctx, const rnnls_problem *d_probs, int64_t count, int64_t max_r, int64_t max_d) {
+  if (count == 0) return RNNLS_OK;
+  const int md = (int)max_d, D1 = md + 1;
+  const int min_chunks = gram_min_chunks(ctx), max_splits = gram_max_splits(ctx);
+  const int64_t batch_chunks = tune_or(ctx->tune.batch_gram_chunks, kBatchChunksPerCta);
+  // bounds over every problem the plan may see (tiles grow with d, splits with r)
+  const int tiles_max = gram_tc_tile_count(D1, md, 0);
+  int splits_max = 1;
+  int64_t cps_unused = 0;
+  gram_tc_splits(max_r, tiles_max, 1, batch_chunks, min_chunks, max_splits, splits_max, cps_unused);
+  int qfit_max = 0, bfit_max = 0;
+  size_t smem = 0;
+  for (int dd = 1; dd <= md; ++dd) {
+    if (lh_q_fits(ctx, dd)) qfit_max = dd;
+    if (lh_b_fits(ctx, dd)) bfit_max = dd;
+    smem = std::max(smem, lh_smem_for(ctx, dd));
+  }
+  dev_plan_args a{};
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    const size_t at = o;
+    o = align_up(o + b, 256);
+    return at;
+  };
+  take((size_t)D1 * D1 * 8);  // Qd at 0
+  a.off_qhi = take((size_t)D1 * D1 * 4);
+  a.off_qlo = take((size_t)D1 * D1 * 4);
+  a.off_colabs = take((size_t)md * 8);
+  a.off_cs = take((size_t)2 * D1 * 4);
+  a.off_cu = take((size_t)D1 * 4);
+  a.off_part = take(splits_max > 1 ? (size_t)splits_max * tiles_max * kGramTileM * kGramTileN * 8 : 0);
+  a.off_bg = take(md > bfit_max ? (size_t)odd_ld(md) * md * 4 : 0);
+  a.slot_bytes = align_up(o, 256);
+  const size_t tables = align_up((size_t)count * sizeof(gram_tc_job), 256) +
+                        align_up((size_t)count * sizeof(lh_job), 256) +
+                        2 * align_up((size_t)(count + 1) * 8, 256) + align_up((size_t)2 * count * 8, 256);
+  int st = ensure_workspace(ctx, tables + (size_t)count * a.slot_bytes + 1024);
+  if (st) return st;
+  unsigned int *counters = nullptr;
+  st = ensure_counters(ctx, (size_t)count * tiles_max, &counters);
+  if (st) return st;
+  ws_carver wc(ctx->ws);
+  a.probs = d_probs;
+  a.count = count;
+  a.max_r = max_r;
+  a.max_d = md;
+  a.qfit_max = qfit_max;
+  a.bfit_max = bfit_max;
+  a.min_chunks = min_chunks;
+  a.max_splits = max_splits;
+  a.batch_chunks = batch_chunks;
+  a.gjobs = wc.take<gram_tc_job>((size_t)count);
+  a.ljobs = wc.take<lh_job>((size_t)count);
+  a.first_col = wc.take<int64_t>((size_t)count + 1);
+  a.first_cta = wc.take<int64_t>((size_t)count + 1);
+  a.tmp = wc.take<int64_t>((size_t)2 * count);
+  a.slots = wc.take<char>((size_t)count * a.slot_bytes);
+  a.counters = counters;
+  a.tiles_max = tiles_max;
+  cudaStream_t s = ctx->stream;
+  plan_batched_device_kernel<<<1, 256, 0, s>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
+  st = gram_tc_launch_batched(ctx, a.gjobs, a.first_col, a.first_cta, (int)count, count * D1,
+                              count * (int64_t)tiles_max * splits_max);
+  if (st) return st;
+  return lh_launch(ctx, a.ljobs, count, smem);
 }
 
 int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, int64_t ldsb, int64_t r, int64_t d,

@@ -127,3 +127,53 @@ def test_batched_workload_five_shapes_sampled_entries(orc):
             want = orc.sketch_entry(col, seed, inst, int(idx_o[k]), sc)
             got = host(SA)[k, j] if j < d else host(Sb)[k]
             assert abs(got - want) <= 1e-5 * sc * np.linalg.norm(col)
+
+
+def test_batched_solve_from_device_descriptors(orc):
+    """rnnls_solve_batched_device: the descriptors in device memory, the plan
+    made on the device; results equal the host-descriptor call's, and a
+    descriptor outside the bounds is refused through its own info."""
+    import ctypes
+
+    import torch
+
+    import paper_0812_4547_gb300 as P
+    from paper_0812_4547_gb300 import _binding as B
+
+    rng = np.random.default_rng(17)
+    shapes = [(4096, 20), (2000, 64), (9000, 130), (300, 7), (16384, 200)]
+    probs, outs = [], []
+    for r, d in shapes:
+        SA = dev_colmajor(rng.standard_normal((r, d)) * np.exp(rng.standard_normal(d)), np.float32)
+        Sb = dev_vec(rng.standard_normal(r), np.float32)
+        probs.append((SA, Sb, r, d))
+        outs.append((torch.empty(d, dtype=torch.float64, device="cuda"), torch.zeros(P.INFO_BYTES, dtype=torch.uint8,
+                                                                                     device="cuda"),
+                     torch.empty(d, dtype=torch.float64, device="cuda"), torch.zeros(P.INFO_BYTES, dtype=torch.uint8,
+                                                                                     device="cuda")))
+    ctx = P.Context(0)
+    try:
+        ctx.solve_batched([(SA, Sb, o[0], o[1]) for (SA, Sb, r, d), o in zip(probs, outs)])
+        descs = [B.rnnls_problem(SA.data_ptr(), SA.stride(1), Sb.data_ptr(), r, d, o[2].data_ptr(), o[3].data_ptr())
+                 for (SA, Sb, r, d), o in zip(probs, outs)]
+        # one more descriptor whose d exceeds the bound: refused, the others solved
+        bad_x = torch.full((300,), 7.0, dtype=torch.float64, device="cuda")
+        bad_info = torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device="cuda")
+        SA0, Sb0 = probs[0][0], probs[0][1]
+        descs.append(B.rnnls_problem(SA0.data_ptr(), SA0.stride(1), Sb0.data_ptr(), 4096, 300, bad_x.data_ptr(),
+                                     bad_info.data_ptr()))
+        arr = (B.rnnls_problem * len(descs))(*descs)
+        d_arr = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).cuda()
+        B.rnnls_solve_batched_device(ctx.handle, d_arr.data_ptr(), len(descs), 16384, 200)
+        torch.cuda.synchronize()
+        for (SA, Sb, r, d), o in zip(probs, outs):
+            x_host, x_dev = host(o[0]), host(o[2])
+            assert np.array_equal(x_host, x_dev)
+            assert P.info_dict(o[3])["status"] == 0
+        assert P.info_dict(bad_info)["status"] == B.RNNLS_EINVAL
+        assert np.all(host(bad_x) == 7.0)
+        assert B.lib().rnnls_solve_batched_device(ctypes.c_void_p(ctx.handle), ctypes.c_void_p(d_arr.data_ptr()), 2,
+                                                  100, 1025, 0) == B.RNNLS_EUNSUPPORTED
+        assert B.lib().rnnls_solve_batched_device(ctypes.c_void_p(ctx.handle), None, 2, 100, 10, 0) == B.RNNLS_EINVAL
+    finally:
+        ctx.close()
