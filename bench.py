@@ -80,6 +80,9 @@ def parse():
                     help="solve streams when pipelined (each solve runs in one block)")
     ap.add_argument("--no-tune", action="store_true",
                     help="workload 5: skip the autotuner (launch-shape knobs at their built-in defaults)")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x2"],
+                    help="sketch precision: fp32 (both Hadamard factors in FP32 registers) or bf16x2 (the first "
+                         "64-point factor on the tensor cores, values split into hi + lo BF16, FP32 accumulation)")
     ap.add_argument("--csc", action="store_true",
                     help="workload 2 or 3 with A held in compressed sparse columns (rnnls_sketch_csc); "
                          "one stream, sketch + solve per step")
@@ -345,6 +348,15 @@ def cpu_baseline(p, seconds: float) -> dict:
     return out
 
 
+def prec_flag(args) -> int:
+    """The library's RNNLS_PREC_* value for --prec."""
+    return 2 if getattr(args, "prec", "fp32") == "bf16x2" else 0
+
+
+def prec_dtype(args) -> str:
+    return "f32" if prec_flag(args) == 0 else "bf16x2 split (hi+lo) on tensor cores, f32 accumulation"
+
+
 def oracle_ratio(A, b, r: int, seed: int, instance: int, limit: float = 1.2e10):
     """The FP64 oracle's residual ratio of Theorem 1 on the same data and seed
     (its own sketch and Lawson-Hanson, then its exact NNLS on the full A), or
@@ -383,6 +395,8 @@ def main():
 
     dev = torch.device("cuda", local)
     base = workloads.CONFIGS[cfg]["seed"]
+    if prec_flag(args) and (cfg in (1, 4) or args.boost > 0 or args.density_sweep or args.csc):
+        raise SystemExit("--prec bf16x2 applies to workloads 2, 3 and 5 (dense FP32 sketches)")
     if cfg in (4, 5) or args.boost > 0 or args.density_sweep or args.csc:
         if args.density_sweep:
             run_density(args, ws, rank, local, dev)
@@ -400,6 +414,9 @@ def main():
     dt_np = np.float64 if f64 else np.float32
     tdt = torch.float64 if f64 else torch.float32
     elt = 8 if f64 else 4
+    if f64 and prec_flag(args):
+        raise SystemExit("--prec bf16x2 needs FP32 data (workloads 2-5)")
+    pf = prec_flag(args)
     A_host = torch.from_numpy(np.ascontiguousarray(p.A.astype(dt_np).T)).pin_memory()
     b_host = torch.from_numpy(np.asarray(p.b, dtype=dt_np)).pin_memory()
     A = A_host.to(dev).t()
@@ -479,7 +496,8 @@ def main():
         st, cs = s_sks[i % nsk], ctx_sks[i % nsk]
         if pipeline and used[k]:
             st.wait_event(solved[k])  # the buffer's previous solve has read it
-        cs.sketch(A_, b_, r, seed=i, instance=rank, SA=SAs[k], Sb=Sbs[k], idx=idxs[k], want_count=False)
+        cs.sketch(A_, b_, r, seed=i, instance=rank, SA=SAs[k], Sb=Sbs[k], idx=idxs[k], want_count=False,
+                  prec=pf)
         if after_sketch is not None:
             after_sketch.record(st)
         if pipeline:
@@ -546,7 +564,7 @@ def main():
     # e2e: pinned host inputs copied in and the solution read back every step,
     # through the same public calls (pipelined: copies overlap the previous step)
     def seq_step(i: int):
-        ctx.sketch(A, b, r, seed=i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
+        ctx.sketch(A, b, r, seed=i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False, prec=pf)
         ctx.solve(SA, Sb, r=r, x=x, info=info)
 
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, min(args.steps, 200))
@@ -618,6 +636,26 @@ def main():
     if res_t is not None:
         ratio = float(res_t.item()) / float(res_o.item())
     sketch_info = P.info_dict(info)
+    prec_report = None
+    if pf:
+        # the split-precision sketch of seed 0 against the FP32 mode's and,
+        # on rank 0, the FP64 oracle's sketch of the same FP32 bytes
+        SA_t, Sb_t = SA.double().clone(), Sb.double().clone()
+        ctx.sketch(A, b, r, seed=0, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
+        ctx.solve(SA, Sb, r=r, x=x, info=info)
+        torch.cuda.synchronize()
+        rel = lambda u, v: float(torch.linalg.vector_norm(u - v) / torch.linalg.vector_norm(v))  # noqa: E731
+        prec_report = {"SA_rel_fro_vs_fp32_mode": rel(SA_t, SA.double()), "Sb_rel_fro_vs_fp32_mode": rel(Sb_t, Sb.double()),
+                       "x_rel_vs_fp32_mode": rel(x_t, x), "bound": 5e-4}
+        if rank == 0 and not args.no_oracle_check:
+            import oracle
+
+            oracle.build()
+            SA_o, Sb_o, _ = oracle.sketch(p.A.astype(np.float32), p.b.astype(np.float32), r, seed=0, instance=rank,
+                                          nthreads=os.cpu_count() or 1)
+            SAh, Sbh = SA_t.cpu().numpy(), Sb_t.cpu().numpy()
+            prec_report["SA_rel_fro_vs_oracle"] = float(np.linalg.norm(SAh - SA_o) / np.linalg.norm(SA_o))
+            prec_report["Sb_rel_fro_vs_oracle"] = float(np.linalg.norm(Sbh - Sb_o) / np.linalg.norm(Sb_o))
 
     # roofline of the dominant kernel (the chunked sketch), timed live with
     # CUDA events on the launching stream during the timed region
@@ -629,12 +667,13 @@ def main():
     sketch_ms = sum(prof.get(k, (0, 0.0))[1] for k in ("sample_rows", "build_plan", "sketch_srht_f32",
                                                         "reduce_partials", "sketch_small", "sketch_f64"))
     wl = workload_desc(cfg, p)
+    wl["precision"] = args.prec
     wl["pipeline"] = (f"sketches on {nsk} stream(s) overlap solves on {nsolve} streams ({nbuf} sketch buffers)"
                       if pipeline else "sketch and solve back to back on one stream")
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if f64 else "f32",
+        "vs_baseline": None, "dtype": "f64" if f64 else prec_dtype(args),
         "data": "synthetic (seeded term-document-like stand-in for TechTC300)", "config": wl,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": recorded_traffic(kname, wl["workload"]), "kernel": kname,
@@ -654,6 +693,8 @@ def main():
         "solve_info": {"status": sketch_info["status"], "passive_count": sketch_info["passive_count"],
                        "outer_iters": sketch_info["outer_iters"], "accurate_mode": sketch_info["accurate_mode"]},
     }
+    if prec_report is not None:
+        out["precision"] = prec_report
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
     elif rank == 0:
@@ -1131,6 +1172,7 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
     from paper_0812_4547_gb300 import _binding as B
 
     c5 = workloads.CONFIGS[5]
+    pf = prec_flag(args)
     bseed = rank_seed(c5["seed"], rank, ws)
     shapes = workloads.batch_shapes(count=args.instances, seed=bseed)
     insts = device_batch(shapes, bseed, dev)
@@ -1157,13 +1199,14 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
     def enqueue(seed0: int, batched: bool = True):
         if batched:
             # every sketch in one batched call, then every solve in one batched call
-            ctx_sketch.sketch_batched(sketch_items(range(count), seed0))
+            ctx_sketch.sketch_batched(sketch_items(range(count), seed0), prec=pf)
             ctx_solve.solve_batched(problems)
         else:
             # the plain per-instance form: sketch and solve each instance in turn on one stream
             for i, (A, b, r) in enumerate(insts):
                 SA, Sb, idx, x, info = bufs[i]
-                ctx_plain.sketch(A, b, r, seed=seed0 + i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False)
+                ctx_plain.sketch(A, b, r, seed=seed0 + i, instance=rank, SA=SA, Sb=Sb, idx=idx, want_count=False,
+                                 prec=pf)
                 ctx_plain.solve(SA, Sb, r=r, x=x, info=info)
 
     nprof = 3
@@ -1179,7 +1222,7 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
 
             t0 = time.perf_counter()
             tuned = autotune.tune([ctx_sketch, ctx_solve], lambda: enqueue(0), "batched",
-                                  {"instances": count, "seed": bseed}, repeats=2)
+                                  {"instances": count, "seed": bseed, "prec": args.prec}, repeats=2)
             tuned["seconds"] = time.perf_counter() - t0
             torch.cuda.synchronize()
         # per-kernel times: CUDA events around every launch of `nprof` steps
@@ -1235,7 +1278,8 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
     peak, peak_src = measured_hbm_peak()
     wl = {"workload": f"c5: {count} uneven instances, n 2^U[14,20], d U{{16..200}}, r pow2 of 8(d+1)ln n",
           "instances": count, "total_input_gb": sum(4 * A.shape[0] * (A.shape[1] + 1) for A, _, _ in insts) / 1e9,
-          "sampling": "iid", "l2": "inputs larger than L2 (no flush)", "parallelism": "independent instances per GPU",
+          "sampling": "iid", "precision": args.prec, "l2": "inputs larger than L2 (no flush)",
+          "parallelism": "independent instances per GPU",
           "pipeline": "one CUDA graph per step: one rnnls_sketch_batched over all instances (rows, plans and "
                       "sketches in one launch each), then one rnnls_solve_batched; every replay redoes every "
                       "kernel with the same seeds"}
@@ -1243,7 +1287,8 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (term-document-like, generated on the device)",
+        "vs_baseline": None, "dtype": prec_dtype(args),
+        "data": "synthetic (term-document-like, generated on the device)",
         "config": wl,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
@@ -1331,7 +1376,7 @@ def e2e_batch(args, insts, bufs, dev, local: int, rank: int, ws: int, tuning=Non
             copied[g].record(copy_s)
             comp_s.wait_event(copied[g])
             ctx_sk[g].sketch_batched([(insts[i][0], insts[i][1], insts[i][2], seed0 + i, rank, bufs[i][0],
-                                       bufs[i][1], bufs[i][2]) for i in ids])
+                                       bufs[i][1], bufs[i][2]) for i in ids], prec=prec_flag(args))
             consumed[g].record(comp_s)
             used[g] = True
             ctx_sv[g].solve_batched([(bufs[i][0], bufs[i][1], bufs[i][3], bufs[i][4]) for i in ids])

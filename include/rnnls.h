@@ -74,6 +74,20 @@ extern "C" {
 #define RNNLS_SAMPLE_IID 0u       /* r uniform draws with replacement (default) */
 #define RNNLS_SAMPLE_BERNOULLI 1u /* each row kept with probability r/n (Alg. 1 step 2) */
 #define RNNLS_SAMPLE_MASK 1u
+/* Precision of the FP32 sketch's Hadamard passes (rnnls_sketch,
+ * rnnls_sketch_batched_ex).  RNNLS_PREC_FP32 (default): both 64-point
+ * factors of each 4096-row chunk's transform in FP32 registers.
+ * RNNLS_PREC_BF16X2: the first factor (row-index bits 0-4 and 11) runs on
+ * the tensor cores as a product with H_64, whose +-1 entries are exact in
+ * BF16: each value x (signs of D applied) is split into hi = bf16(x) and
+ * lo = bf16(x - hi) (|x - hi - lo| <= 2^-18 |x|), and (hi + lo) H_64 is
+ * accumulated in FP32 (Sec. 3.4's O(nd log r) preconditioning step, the
+ * split-precision form).  Relative Frobenius error vs FP64 about 1e-6
+ * (bound used by the tests: 5e-4).  Rows are the same as in FP32 mode.  For
+ * padded n <= 8192 (whole column in shared memory) the flag has no effect. */
+#define RNNLS_PREC_FP32 0u
+#define RNNLS_PREC_BF16X2 2u
+#define RNNLS_PREC_MASK 2u
 
 typedef struct rnnls_ctx rnnls_ctx;
 
@@ -184,7 +198,10 @@ int rnnls_set_plan_event(rnnls_ctx *ctx, void *event);
  * 1e-7 * sqrt(log2 n).  Errors: EINVAL (null A, b, SA or Sb; a size < 1;
  * lda < n_raw; ldsa < cap; unknown flags; cap < r in iid mode; nothing is
  * enqueued then), EUNSUPPORTED (n_raw > 2^28, d > 2^20, r > 2^30),
- * ECAPACITY, ENOMEM, ECUDA. */
+ * ECAPACITY, ENOMEM, ECUDA.  flags: one RNNLS_SAMPLE_* value, or'ed with
+ * one RNNLS_PREC_* value (in RNNLS_PREC_BF16X2 mode a sketch with more than
+ * 24,576 rows per plan group is formed in several passes over A, each for
+ * a share of the rows). */
 int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d,
                  int64_t r, uint64_t seed, uint64_t instance, uint32_t flags, float *SA, int64_t ldsa, float *Sb,
                  int32_t *idx, int64_t cap, int64_t *r_out);
@@ -251,6 +268,11 @@ typedef struct rnnls_sketch_job {
  * Errors: EINVAL (a null pointer or a bad size in any job; nothing is
  * enqueued then), EUNSUPPORTED (n_raw > 2^28), ENOMEM, ECUDA. */
 int rnnls_sketch_batched(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count);
+
+/* rnnls_sketch_batched with a precision flag (RNNLS_PREC_FP32 or
+ * RNNLS_PREC_BF16X2, see above; the same rows in both).  Errors: those of
+ * rnnls_sketch_batched, and EINVAL for any other flag bit. */
+int rnnls_sketch_batched_ex(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count, uint32_t flags);
 
 /* rnnls_sketch for a sparse A held by columns (compressed sparse column),
  * the form of the paper's term-document data (Sec. 4.1, 4.2): the same iid

@@ -13,7 +13,8 @@ import ctypes
 import math
 
 from . import _binding as B
-from ._binding import (RNNLS_SAMPLE_BERNOULLI, RNNLS_SAMPLE_IID, RNNLSError, rnnls_info,  # noqa: F401
+from ._binding import (RNNLS_PREC_BF16X2, RNNLS_PREC_FP32, RNNLS_SAMPLE_BERNOULLI, RNNLS_SAMPLE_IID,  # noqa: F401
+                       RNNLSError, rnnls_info,  # noqa: F401
                        rnnls_problem)
 
 INFO_BYTES = ctypes.sizeof(rnnls_info)
@@ -93,8 +94,9 @@ class Context:
 
     # -- sketch -------------------------------------------------------------------------
     def sketch(self, A, b, r: int, seed: int, instance: int = 0, mode: int = RNNLS_SAMPLE_IID, SA=None, Sb=None,
-               idx=None, cap: int | None = None, want_count: bool = True):
-        """SA, Sb, idx and the row count of Alg. 1's sketch (FP32 or FP64 by A's dtype)."""
+               idx=None, cap: int | None = None, want_count: bool = True, prec: int = RNNLS_PREC_FP32):
+        """SA, Sb, idx and the row count of Alg. 1's sketch (FP32 or FP64 by A's dtype; FP32 data may use
+        prec=RNNLS_PREC_BF16X2, the split-precision tensor-core pass)."""
         torch = _torch()
         A = colmajor(A)
         n_raw, d = A.shape
@@ -113,7 +115,7 @@ class Context:
             raise TypeError("A, b, SA, Sb must share dtype float32 or float64")
         if not b.is_contiguous() or not Sb.is_contiguous() or not idx.is_contiguous():
             raise ValueError("b, Sb and idx must be contiguous")
-        rows = fn(self.handle, A.data_ptr(), _ld(A), b.data_ptr(), n_raw, d, r, seed, instance, mode,
+        rows = fn(self.handle, A.data_ptr(), _ld(A), b.data_ptr(), n_raw, d, r, seed, instance, mode | prec,
                   SA.data_ptr(), _ld(SA), Sb.data_ptr(), idx.data_ptr(), cap, want_count)
         return SA, Sb, idx, rows
 
@@ -135,14 +137,14 @@ class Context:
                               instance, SA.data_ptr(), _ld(SA), SB.data_ptr(), _ld(SB), idx.data_ptr())
         return SA, SB, idx
 
-    def sketch_batched(self, items):
+    def sketch_batched(self, items, prec: int = RNNLS_PREC_FP32):
         """Sketch many FP32 instances together; items: (A, b, r, seed, instance, SA, Sb, idx), outputs preallocated."""
         jobs = []
         for A, b, r, seed, instance, SA, Sb, idx in items:
             A = colmajor(A)
             jobs.append(B.rnnls_sketch_job(A.data_ptr(), _ld(A), b.data_ptr(), A.shape[0], A.shape[1], r, seed, instance,
                                            SA.data_ptr(), _ld(SA), Sb.data_ptr(), idx.data_ptr()))
-        B.rnnls_sketch_batched(self.handle, jobs)
+        B.rnnls_sketch_batched(self.handle, jobs, prec)
 
     def sketch_shard(self, A_rows, b_rows, n_raw: int, row0: int, r: int, seed: int, instance: int = 0, SA=None,
                      Sb=None, idx=None):

@@ -25,6 +25,8 @@ RNNLS_EUNSUPPORTED = 9
 
 RNNLS_SAMPLE_IID = 0
 RNNLS_SAMPLE_BERNOULLI = 1
+RNNLS_PREC_FP32 = 0
+RNNLS_PREC_BF16X2 = 2
 
 #: every entry point declared in include/rnnls.h
 EXPORTS = (
@@ -33,7 +35,7 @@ EXPORTS = (
     "rnnls_profile_end", "rnnls_sketch_noalloc", "rnnls_set_sketch_sms", "rnnls_sketch_multi", "rnnls_sketch_shard",
     "rnnls_solve_multi", "rnnls_sketch_batched", "rnnls_solve_boosted", "rnnls_set_plan_event", "rnnls_gram",
     "rnnls_solve_pg", "rnnls_sketch_csc", "rnnls_set_tuning", "rnnls_get_tuning",
-    "rnnls_solve_batched_device",
+    "rnnls_solve_batched_device", "rnnls_sketch_batched_ex",
 )
 
 
@@ -143,6 +145,7 @@ def lib() -> ctypes.CDLL:
         L.rnnls_set_tuning.argtypes = [P, ctypes.POINTER(rnnls_tuning)]
         L.rnnls_get_tuning.argtypes = [P, ctypes.POINTER(rnnls_tuning)]
         L.rnnls_sketch_batched.argtypes = [P, ctypes.POINTER(rnnls_sketch_job), I64]
+        L.rnnls_sketch_batched_ex.argtypes = [P, ctypes.POINTER(rnnls_sketch_job), I64, U32]
         L.rnnls_residual.argtypes = [P, P, I64, P, I64, I64, P, P]
         L.rnnls_solve_boosted.argtypes = [P, P, I64, P, I64, I64, I64, U64, U64, I32, P, P, P, P]
         L.rnnls_profile_begin.argtypes = [P, I32]
@@ -236,9 +239,12 @@ def rnnls_solve_f64(ctx, SA, ldsa, Sb, r, d, x, info) -> None:
                                 ctypes.c_void_p(x), ctypes.c_void_p(info)), "rnnls_solve_f64")
 
 
-def rnnls_sketch_batched(ctx, jobs) -> None:
+def rnnls_sketch_batched(ctx, jobs, flags: int = 0) -> None:
     arr = (rnnls_sketch_job * len(jobs))(*jobs)
-    check(lib().rnnls_sketch_batched(ctypes.c_void_p(ctx), arr, len(jobs)), "rnnls_sketch_batched")
+    if flags:
+        check(lib().rnnls_sketch_batched_ex(ctypes.c_void_p(ctx), arr, len(jobs), flags), "rnnls_sketch_batched_ex")
+    else:
+        check(lib().rnnls_sketch_batched(ctypes.c_void_p(ctx), arr, len(jobs)), "rnnls_sketch_batched")
 
 
 def rnnls_gram(ctx, SA, ldsa, Sb, r, d, Q, colabs) -> None:

@@ -137,11 +137,11 @@ int get_aux(rnnls_ctx *ctx, int64_t cap, int64_t n, bool need_idx, aux_view &v) 
 
 template <typename T>
 int check_sketch_args(rnnls_ctx *ctx, const T *A, int64_t lda, const T *b, int64_t n_raw, int64_t d, int64_t r,
-                      uint32_t flags, T *SA, int64_t ldsa, T *Sb, int64_t cap) {
+                      uint32_t flags, T *SA, int64_t ldsa, T *Sb, int64_t cap, uint32_t allowed = RNNLS_SAMPLE_MASK) {
   if (!ctx || !A || !b || !SA || !Sb) return RNNLS_EINVAL;
   if (n_raw < 1 || d < 1 || r < 1 || cap < 1) return RNNLS_EINVAL;
   if (lda < n_raw || ldsa < cap) return RNNLS_EINVAL;
-  if (flags & ~RNNLS_SAMPLE_MASK) return RNNLS_EINVAL;
+  if (flags & ~allowed) return RNNLS_EINVAL;
   if ((flags & RNNLS_SAMPLE_MASK) == RNNLS_SAMPLE_IID && cap < r) return RNNLS_EINVAL;
   if (n_raw > kMaxRows || d > (1 << 20) || r > ((int64_t)1 << 30)) return RNNLS_EUNSUPPORTED;
   return RNNLS_OK;
@@ -331,7 +331,7 @@ int rnnls_get_tuning(rnnls_ctx *ctx, rnnls_tuning *t) {
 int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n_raw, int64_t d, int64_t r,
                  uint64_t seed, uint64_t instance, uint32_t flags, float *SA, int64_t ldsa, float *Sb, int32_t *idx,
                  int64_t cap, int64_t *r_out) {
-  int st = check_sketch_args(ctx, A, lda, b, n_raw, d, r, flags, SA, ldsa, Sb, cap);
+  int st = check_sketch_args(ctx, A, lda, b, n_raw, d, r, flags, SA, ldsa, Sb, cap, RNNLS_SAMPLE_MASK | RNNLS_PREC_MASK);
   if (st) return st;
   device_guard dg;
   RNNLS_CUDA_TRY(dg.set(ctx->device));
@@ -372,6 +372,7 @@ int rnnls_sketch(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, in
   a.ldsb = ldsa;
   a.chunk0 = 0;
   a.idx = rows_idx;
+  a.tc = (flags & RNNLS_PREC_MASK) == RNNLS_PREC_BF16X2 ? 1 : 0;
   st = sketch_f32(ctx, a, ctx->num_sms);
   if (st) return st;
   if (r_out) {
@@ -483,7 +484,11 @@ int rnnls_sketch_shard(rnnls_ctx *ctx, const float *A, int64_t lda, const float 
 }
 
 int rnnls_sketch_batched(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count) {
-  if (!ctx || (!jobs && count > 0) || count < 0) return RNNLS_EINVAL;
+  return rnnls_sketch_batched_ex(ctx, jobs, count, 0u);
+}
+
+int rnnls_sketch_batched_ex(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count, uint32_t flags) {
+  if (!ctx || (!jobs && count > 0) || count < 0 || (flags & ~RNNLS_PREC_MASK)) return RNNLS_EINVAL;
   for (int64_t i = 0; i < count; ++i) {
     const rnnls_sketch_job &j = jobs[i];
     if (!j.A || !j.b || !j.SA || !j.Sb || !j.idx) return RNNLS_EINVAL;
@@ -493,7 +498,7 @@ int rnnls_sketch_batched(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t c
   if (count == 0) return RNNLS_OK;
   device_guard dg;
   RNNLS_CUDA_TRY(dg.set(ctx->device));
-  return sketch_batched_f32(ctx, jobs, count);
+  return sketch_batched_f32(ctx, jobs, count, (flags & RNNLS_PREC_MASK) == RNNLS_PREC_BF16X2 ? 1 : 0);
 }
 
 int rnnls_sketch_f64(rnnls_ctx *ctx, const double *A, int64_t lda, const double *b, int64_t n_raw, int64_t d,

@@ -84,10 +84,11 @@ struct sketch_args_f32 {
   int64_t ldsb;
   int32_t *idx;
   int gen_iid;  // 1: the sketch draws the iid rows itself (idx is output only)
+  int tc = 0;   // 1: split-precision mode (pass 1 on the tensor cores, RNNLS_PREC_BF16X2)
 };
 int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms);
 // many instances (iid rows, FP32): rows, plans and sketches of all in one launch each
-int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count);
+int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count, int tc = 0);
 // sketch_f32 with caller-provided scratch (no allocation; see noalloc.cu)
 int sketch_f32_scratch(cudaStream_t s, const sketch_args_f32 &a, int num_sms, void *scratch, size_t bytes);
 

@@ -33,6 +33,7 @@
 
 #include "kernels.h"
 #include "launch_attr.h"
+#include "tcgen05.cuh"
 
 namespace rnnls {
 
@@ -207,6 +208,106 @@ __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fenc
 __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 constexpr uint32_t kTmemCols = 512;
 
+// ---- split-precision pass 1 on the tensor cores (RNNLS_PREC_BF16X2) ---------
+// H_4096 factors over position bits into H_64 (bits 0-4 and 11) (x) H_64
+// (bits 5-10).  In this mode the first factor is a matrix product on the
+// tensor cores: each value x (D applied) is carried as hi + lo with
+// hi = bf16(x), lo = bf16(x - hi), so |x - hi - lo| <= 2^-18 |x|, and
+// (hi + lo) H_64 is formed by tcgen05.mma (H_64's entries +-1 are exact in
+// BF16) with FP32 accumulation in TMEM.  The second factor stays a register
+// pass in FP32.  A pair of chunks (workers 2p, 2p + 1: 128 threads) is one
+// M = 128 tile: row m = 64 (w & 1) + wt holds the thread's 64 pass-1 values
+// in K order k = 32 h + e (position (h << 11) | (wt << 5) | e), and column
+// n of the product is the transform's output at the position with the same
+// bits.  The operands overwrite the pair's 32 KiB of the stage buffer (hi in
+// the first chunk's slot, lo in the second's), K-major core matrices of
+// 8 rows x 16 bytes, the eight core matrices of an 8-row group adjacent
+// (128 bytes apart along K, groups 1 KiB apart); H_64 has its own 8 KiB in
+// the same layout.
+constexpr int kTcRowSlots = 96;       // rows per thread kept in TMEM beside the accumulators
+constexpr uint32_t kTcAccCols = 128;  // two pairs x 64 FP32 columns
+constexpr uint32_t kTcIdesc = tc::idesc_bf16_f32(128, 64);
+
+__device__ __forceinline__ void bar_pair(int p) { asm volatile("bar.sync %0, 128;" ::"r"(p + 5) : "memory"); }
+
+// H_64 as the B operand (row n, column k: (-1)^popcount(n & k), BF16 +-1)
+__device__ __forceinline__ void init_h64(uint32_t *hm, int tid) {
+  for (int i = tid; i < 2048; i += kThreads) {
+    const int byte = 4 * i;
+    const int n = 8 * (byte >> 10) + ((byte >> 4) & 7);
+    const int k = 8 * ((byte >> 7) & 7) + ((byte & 15) >> 1);
+    const uint32_t e0 = (__popc(n & k) & 1) ? 0xBF80u : 0x3F80u;
+    const uint32_t e1 = (__popc(n & (k + 1)) & 1) ? 0xBF80u : 0x3F80u;
+    hm[i] = e0 | (e1 << 16);
+  }
+  fence_proxy_async();
+}
+
+// Pass 1 of the thread's chunk on the tensor cores.  v: its 64 values (D
+// applied) in K order; zw: its chunk's slot; pair_u32: the pair's operand
+// region (shared address); h_u32: H_64; d_tmem: the pair's accumulator
+// (lane 0); t_row: the same columns at this warp's lanes; bar / parity: the
+// pair's MMA mbarrier and the phase to wait for.  Writes the 64 outputs back
+// to the thread's pass-1 positions.  A wait that runs out sets `stalled`.
+__device__ __forceinline__ void tc_pass1(const float (&v)[64], float *zw, uint32_t pair_u32, uint32_t h_u32,
+                                         uint32_t d_tmem, uint32_t t_row, uint32_t bar, uint32_t parity, int tid,
+                                         int *stalled) {
+  const int p = tid >> 7, m = tid & 127, wt = tid & 63;
+  uint32_t hi2[32], lo2[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const float a = v[2 * i], b = v[2 * i + 1];
+    uint32_t h, l;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(b), "f"(a));
+    const float ra = a - __uint_as_float(h << 16), rb = b - __uint_as_float(h & 0xffff0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(rb), "f"(ra));
+    hi2[i] = h;
+    lo2[i] = l;
+  }
+  bar_pair(p);  // every thread of the pair holds its values: the region may be overwritten
+  const uint32_t row = pair_u32 + (uint32_t)((m >> 3) * 1024 + (m & 7) * 16);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(row + 128u * c), "r"(hi2[4 * c]),
+                 "r"(hi2[4 * c + 1]), "r"(hi2[4 * c + 2]), "r"(hi2[4 * c + 3])
+                 : "memory");
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(row + 16384u + 128u * c), "r"(lo2[4 * c]),
+                 "r"(lo2[4 * c + 1]), "r"(lo2[4 * c + 2]), "r"(lo2[4 * c + 3])
+                 : "memory");
+  }
+  fence_proxy_async();
+  bar_pair(p);
+  if (m == 0) {
+    tmem_fence_after();
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint64_t bd = tc::smem_desc(h_u32 + 256u * kk, 128, 1024);
+      tc::mma_bf16(d_tmem, tc::smem_desc(pair_u32 + 256u * kk, 128, 1024), bd, kTcIdesc, kk > 0 ? 1u : 0u);
+      tc::mma_bf16(d_tmem, tc::smem_desc(pair_u32 + 16384u + 256u * kk, 128, 1024), bd, kTcIdesc, 1u);
+    }
+    tc::mma_commit(bar);
+  }
+  {
+    const uint32_t limit = *(volatile int *)stalled ? 64u : kSpinLimit;
+    bool ok = false;
+    for (uint32_t it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, parity);
+    if (!ok) *(volatile int *)stalled = 1;
+  }
+  tmem_fence_after();
+  uint32_t o[64];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) tc::tmem_ld16(t_row + 16u * c, o + 16 * c);
+  tc::tmem_wait_ld();
+  tmem_fence_before();
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+      *reinterpret_cast<float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2))) =
+          make_float4(__uint_as_float(o[32 * h + 4 * g]), __uint_as_float(o[32 * h + 4 * g + 1]),
+                      __uint_as_float(o[32 * h + 4 * g + 2]), __uint_as_float(o[32 * h + 4 * g + 3]));
+}
+
 // Partition of the step list over the blocks.  Unit u = kg * (d + 1) + col
 // (plan group kg, column col) owns steps u*J .. u*J + J - 1.  Balanced:
 // block b takes steps [T b / B, T (b+1) / B).  Aligned: block b takes the
@@ -267,7 +368,7 @@ struct step_cursor {
 // with bits 0-4 = l and bit 11 = h.  Both passes read and write back the
 // same words, so only pass 2 has to wait for the other threads of the worker.
 // ---------------------------------------------------------------------------
-template <int SLOTS>
+template <int SLOTS, bool TC>
 __global__ void __launch_bounds__(kThreads, 1)
     sketch_srht_f32(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const float *__restrict__ A, int64_t lda, const float *__restrict__ Bm, int64_t ldb,
@@ -282,6 +383,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ unsigned int last_flag;
   __shared__ int stalled;  // a tensor copy did not land within the wait limit
   __shared__ uint32_t tmem_base_s;
+  __shared__ __align__(1024) uint32_t h64_s[TC ? 2048 : 4];  // H_64 operand (split-precision mode)
+  __shared__ __align__(8) uint64_t mma_bar[2];                // one per chunk pair (split-precision mode)
 
   const int tid = threadIdx.x;
   const int w = tid >> 6;   // worker: chunk 4j + w of a step
@@ -301,15 +404,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (tid == 0) {
     for (int q = 0; q < kStages; ++q) mbar_init(smem_u32(&mbar[q]), 1);
+    if constexpr (TC) {
+      mbar_init(smem_u32(&mma_bar[0]), 1);
+      mbar_init(smem_u32(&mma_bar[1]), 1);
+    }
     fence_mbar_init();
     stalled = 0;
   }
+  if constexpr (TC) init_h64(h64_s, tid);
   // SLOTS > 0: that many plan rows per thread, words and sums in registers;
-  // SLOTS == 0: `slots` rows (a multiple of 8, up to kMaxSlots) kept in TMEM
-  if constexpr (SLOTS == 0) {
+  // SLOTS == 0: `slots` rows (a multiple of 8, up to kMaxSlots, kTcRowSlots
+  // with TC) kept in TMEM.  TC: the pass-1 accumulators take the last
+  // kTcAccCols columns.
+  constexpr uint32_t kCols = (SLOTS == 0) ? kTmemCols : kTcAccCols;
+  constexpr int kRowCols = TC ? kTcRowSlots : kMaxSlots;
+  constexpr uint32_t kAcc0 = (SLOTS == 0) ? kTmemCols - kTcAccCols : 0u;
+  if constexpr (SLOTS == 0 || TC) {
     if (tid < 32) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
-                   "r"(kTmemCols)
+                   "r"(kCols)
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -317,8 +430,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
-  const uint32_t t_pk = tmem_base_s + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * 2 * kMaxSlots);
-  const uint32_t t_acc = t_pk + kMaxSlots;
+  const uint32_t t_pk = tmem_base_s + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * 2 * kRowCols);
+  const uint32_t t_acc = t_pk + kRowCols;
+  // TC: this pair's accumulator (lane 0) and its columns at this warp's lanes
+  const uint32_t tc_d = tmem_base_s + kAcc0 + 64u * (uint32_t)(tid >> 7);
+  const uint32_t tc_row = tc_d + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16);
+  const uint32_t tc_pair_off = (uint32_t)(2 * (tid >> 7) * kM) * 4u;  // the pair's bytes in a stage buffer
+  uint32_t tc_phase = 0;
   const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
   constexpr int RS = SLOTS > 0 ? SLOTS : 1;
   uint32_t pk_r[RS];
@@ -391,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int q = 0;
   uint32_t phase = 0;
 
-  if constexpr (SLOTS >= 24) {
+  if constexpr (SLOTS >= 24 && !TC) {
     // Pipelined order (24 or more plan rows per thread in registers): the
     // combine of step ls runs beside pass 1 of step ls + 1 (different stage
     // buffers), so each step has one block barrier and the gather's loads
@@ -704,13 +822,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         v[32 * h + 4 * g + 3] = xor_sign(t.w, (sw << (31 - (4 * g + 3))) & 0x80000000u);
       }
     }
-    fwht64(v);
+    if constexpr (TC) {
+      tc_pass1(v, zw, stage_u32 + (uint32_t)(q * kStageFloats) * 4u + tc_pair_off, smem_u32(h64_s), tc_d, tc_row,
+               smem_u32(&mma_bar[tid >> 7]), tc_phase, tid, &stalled);
+      tc_phase ^= 1u;
+    } else {
+      fwht64(v);
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int g = 0; g < 8; ++g)
-        *reinterpret_cast<float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2))) =
-            make_float4(v[32 * h + 4 * g], v[32 * h + 4 * g + 1], v[32 * h + 4 * g + 2], v[32 * h + 4 * g + 3]);
+        for (int g = 0; g < 8; ++g)
+          *reinterpret_cast<float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2))) =
+              make_float4(v[32 * h + 4 * g], v[32 * h + 4 * g + 1], v[32 * h + 4 * g + 2], v[32 * h + 4 * g + 3]);
+    }
     bar_worker(w);
     // pass 2 (bits 5-10): v[s] <- position ((wt>>5)<<11) | (s<<5) | (wt & 31)
     {
@@ -908,13 +1032,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   }
-  if constexpr (SLOTS == 0) {
+  if constexpr (SLOTS == 0 || TC) {
     tmem_wait_st();
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
     if (tid < 32)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(kTmemCols)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(kCols)
                    : "memory");
   }
 }
@@ -1005,6 +1129,7 @@ struct batch_cursor {
   }
 };
 
+template <bool TC>
 __global__ void __launch_bounds__(kThreads, 1)
     sketch_srht_batch_f32(const srht_job *__restrict__ jobs, int njobs, const int64_t *__restrict__ starts,
                           float *__restrict__ part, int maxseg, int64_t rpg_max, unsigned int *__restrict__ counters) {
@@ -1014,6 +1139,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ unsigned int last_flag;
   __shared__ int stalled;
   __shared__ uint32_t tmem_base_s;
+  __shared__ __align__(1024) uint32_t h64_s[TC ? 2048 : 4];  // H_64 operand (split-precision mode)
+  __shared__ __align__(8) uint64_t mma_bar[2];
 
   const int tid = threadIdx.x;
   const int w = tid >> 6;
@@ -1029,9 +1156,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (tid == 0) {
     for (int q = 0; q < kStages; ++q) mbar_init(smem_u32(&mbar[q]), 1);
+    if constexpr (TC) {
+      mbar_init(smem_u32(&mma_bar[0]), 1);
+      mbar_init(smem_u32(&mma_bar[1]), 1);
+    }
     fence_mbar_init();
     stalled = 0;
   }
+  if constexpr (TC) init_h64(h64_s, tid);
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                  "r"(kTmemCols)
@@ -1041,8 +1173,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
-  const uint32_t t_pk = tmem_base_s + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * 2 * kMaxSlots);
-  const uint32_t t_acc = t_pk + kMaxSlots;
+  constexpr int kRowCols = TC ? kTcRowSlots : kMaxSlots;  // TC: the last kTcAccCols columns hold pass 1's products
+  const uint32_t t_pk = tmem_base_s + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * 2 * kRowCols);
+  const uint32_t t_acc = t_pk + kRowCols;
+  const uint32_t tc_d = tmem_base_s + (kTmemCols - kTcAccCols) + 64u * (uint32_t)(tid >> 7);
+  const uint32_t tc_row = tc_d + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16);
+  const uint32_t tc_pair_off = (uint32_t)(2 * (tid >> 7) * kM) * 4u;
+  uint32_t tc_phase = 0;
   const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 
   // thread 0: copies of a step (four chunks and their sign words)
@@ -1167,13 +1304,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         v[32 * h + 4 * g + 3] = xor_sign(t.w, (sw << (31 - (4 * g + 3))) & 0x80000000u);
       }
     }
-    fwht64(v);
+    if constexpr (TC) {
+      tc_pass1(v, zw, step_u32 + tc_pair_off, smem_u32(h64_s), tc_d, tc_row, smem_u32(&mma_bar[tid >> 7]), tc_phase,
+               tid, &stalled);
+      tc_phase ^= 1u;
+    } else {
+      fwht64(v);
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int g = 0; g < 8; ++g)
-        *reinterpret_cast<float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2))) =
-            make_float4(v[32 * h + 4 * g], v[32 * h + 4 * g + 1], v[32 * h + 4 * g + 2], v[32 * h + 4 * g + 3]);
+        for (int g = 0; g < 8; ++g)
+          *reinterpret_cast<float4 *>(zw + ((h << 11) | (wt << 5) | ((g ^ (wt & 7)) << 2))) =
+              make_float4(v[32 * h + 4 * g], v[32 * h + 4 * g + 1], v[32 * h + 4 * g + 2], v[32 * h + 4 * g + 3]);
+    }
     bar_worker(w);
     {
       const uint32_t lane = (uint32_t)(wt & 31), hi = (uint32_t)(wt >> 5) << 11;
@@ -1470,6 +1613,14 @@ int pick_slots(int64_t rows) {
   const int64_t need = (rows + kThreads - 1) / kThreads;
   return (int)std::min<int64_t>(kMaxSlots, std::max<int64_t>(8, (need + 7) / 8 * 8));
 }
+// the same with the split-precision mode's smaller TMEM share (kTcRowSlots):
+// the fewest plan groups, rows spread evenly over them
+int pick_slots_tc(int64_t rows) {
+  const int64_t need = (rows + kThreads - 1) / kThreads;
+  const int64_t groups = std::max<int64_t>(1, (need + kTcRowSlots - 1) / kTcRowSlots);
+  const int64_t per = (need + groups - 1) / groups;
+  return (int)std::min<int64_t>(kTcRowSlots, std::max<int64_t>(8, (per + 7) / 8 * 8));
+}
 
 typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                     const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -1511,8 +1662,10 @@ int launch_srht(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, co
                 const uint64_t *signs, float *part, unsigned int *counters) {
   static once_per_device attrs;
   if (attrs.run([] {
-        for (auto kern : {sketch_srht_f32<0>, sketch_srht_f32<8>, sketch_srht_f32<16>, sketch_srht_f32<24>,
-                          sketch_srht_f32<32>, sketch_srht_f32<40>}) {
+        for (auto kern : {sketch_srht_f32<0, false>, sketch_srht_f32<8, false>, sketch_srht_f32<16, false>,
+                          sketch_srht_f32<24, false>, sketch_srht_f32<32, false>, sketch_srht_f32<40, false>,
+                          sketch_srht_f32<0, true>, sketch_srht_f32<8, true>, sketch_srht_f32<16, true>,
+                          sketch_srht_f32<24, true>, sketch_srht_f32<32, true>, sketch_srht_f32<40, true>}) {
           const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                      (int)kSketchSmem);
           if (e != cudaSuccess) return e;
@@ -1529,12 +1682,18 @@ int launch_srht(cudaStream_t s, const sketch_args_f32 &a, const plan_t &plan, co
     if (st) return st;
   }
   // up to 40 rows per thread in registers, beyond that in TMEM
-  auto kern = plan.slots == 8    ? sketch_srht_f32<8>
-              : plan.slots == 16 ? sketch_srht_f32<16>
-              : plan.slots == 24 ? sketch_srht_f32<24>
-              : plan.slots == 32 ? sketch_srht_f32<32>
-              : plan.slots == 40 ? sketch_srht_f32<40>
-                                 : sketch_srht_f32<0>;
+  auto kern = a.tc ? (plan.slots == 8    ? sketch_srht_f32<8, true>
+                      : plan.slots == 16 ? sketch_srht_f32<16, true>
+                      : plan.slots == 24 ? sketch_srht_f32<24, true>
+                      : plan.slots == 32 ? sketch_srht_f32<32, true>
+                      : plan.slots == 40 ? sketch_srht_f32<40, true>
+                                         : sketch_srht_f32<0, true>)
+                   : (plan.slots == 8    ? sketch_srht_f32<8, false>
+                      : plan.slots == 16 ? sketch_srht_f32<16, false>
+                      : plan.slots == 24 ? sketch_srht_f32<24, false>
+                      : plan.slots == 32 ? sketch_srht_f32<32, false>
+                      : plan.slots == 40 ? sketch_srht_f32<40, false>
+                                         : sketch_srht_f32<0, false>);
   // programmatic dependent of the plan launch before it (the kernel waits for
   // that launch before it reads anything the launch writes)
   cudaLaunchConfig_t cfg = {};
@@ -1568,7 +1727,7 @@ struct srht_geom {
 srht_geom plan_geometry(const sketch_args_f32 &a, int sms, bool force_aligned, int full_min = kFullMinSlots) {
   srht_geom g{};
   g.P.full_min = full_min;
-  g.plan.slots = pick_slots(a.r);
+  g.plan.slots = a.tc ? pick_slots_tc(a.r) : pick_slots(a.r);
   g.plan.rows_per_group = (int64_t)kThreads * g.plan.slots;
   g.plan.kgroups = (int)((a.r + g.plan.rows_per_group - 1) / g.plan.rows_per_group);
   g.vec = (((uintptr_t)a.A % 16 == 0) && (a.lda % 4 == 0) && ((uintptr_t)a.b % 16 == 0) &&
@@ -1640,7 +1799,7 @@ int sketch_f32(rnnls_ctx *ctx, const sketch_args_f32 &a, int num_sms) {
   return launch_srht(s, a, g.plan, g.P, g.blocks, g.vec, signs, part, counters);
 }
 
-int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count) {
+int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t count, int tc) {
   cudaStream_t s = ctx->stream;
   const int num_sms = ctx->num_sms;
   // instances too small for the chunked path go one by one
@@ -1655,7 +1814,7 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
     a.A = jb.A; a.lda = jb.lda; a.b = jb.b; a.ldb = jb.n_raw; a.nb = 1; a.n_raw = jb.n_raw; a.d = (int)jb.d;
     a.L = log2_ceil64(jb.n_raw); a.chunk0 = 0; a.r = jb.r; a.d_count = nullptr; a.seed = jb.seed;
     a.inst = jb.instance; a.scale = (float)(1.0 / sqrt((double)jb.r)); a.SA = jb.SA; a.ldsa = jb.ldsa; a.Sb = jb.Sb;
-    a.ldsb = jb.ldsa; a.idx = jb.idx; a.gen_iid = 0;
+    a.ldsb = jb.ldsa; a.idx = jb.idx; a.gen_iid = 0; a.tc = tc;
     int st = launch_sample_iid(s, jb.seed, jb.instance, a.L, jb.r, jb.idx);
     if (!st) st = sketch_f32(ctx, a, num_sms);
     if (st) return st;
@@ -1672,7 +1831,7 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
     const rnnls_sketch_job &jb = jobs[big[(size_t)t]];
     srht_job &J = sj[(size_t)t];
     memset(&J, 0, sizeof(J));
-    const int slots = pick_slots(jb.r);
+    const int slots = tc ? pick_slots_tc(jb.r) : pick_slots(jb.r);
     const int64_t rpg = (int64_t)kThreads * slots;
     const int kgroups = (int)((jb.r + rpg - 1) / rpg);
     J.A = jb.A; J.B = jb.b; J.lda = jb.lda; J.ldb = jb.n_raw; J.ldsa = jb.ldsa; J.ldsb = jb.ldsa;
@@ -1796,11 +1955,12 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
                              (const int64_t *)(d_tables + off_fp), nb, samp_tot, plan_tot);
   }
   if (st) return st;
-  static smem_attr batch_attr;
-  RNNLS_CUDA_TRY(batch_attr.ensure((const void *)sketch_srht_batch_f32, kSketchSmem));
+  static smem_attr batch_attr, batch_attr_tc;
+  auto kern = tc ? sketch_srht_batch_f32<true> : sketch_srht_batch_f32<false>;
+  RNNLS_CUDA_TRY((tc ? batch_attr_tc : batch_attr).ensure((const void *)kern, kSketchSmem));
   prof_scope ps_main(ctx, K_SKETCH);
-  sketch_srht_batch_f32<<<(unsigned)B, kThreads, kSketchSmem, s>>>(
-      (const srht_job *)d_tables, nb, (const int64_t *)(d_tables + off_st), part, maxseg, rpg_max, counters);
+  kern<<<(unsigned)B, kThreads, kSketchSmem, s>>>((const srht_job *)d_tables, nb, (const int64_t *)(d_tables + off_st),
+                                                  part, maxseg, rpg_max, counters);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 
