@@ -144,7 +144,9 @@ typedef struct rnnls_tuning {
   int32_t gram_max_splits;
   int32_t batch_gram_chunks;
   int32_t batch_step_cost;
-  int32_t reserved[2]; /* zero */
+  int32_t lh_warp_max_d;  /* Lawson-Hanson problems with d up to this run as one-warp
+                             blocks, larger ones as 256-thread blocks (0: 64; -1: never) */
+  int32_t reserved;       /* zero */
 } rnnls_tuning;
 
 /* Create a context on CUDA device `device` that enqueues on `stream`

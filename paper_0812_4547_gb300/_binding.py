@@ -61,7 +61,8 @@ class rnnls_tuning(ctypes.Structure):
         ("gram_max_splits", ctypes.c_int32),
         ("batch_gram_chunks", ctypes.c_int32),
         ("batch_step_cost", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("lh_warp_max_d", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

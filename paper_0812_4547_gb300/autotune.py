@@ -2,7 +2,8 @@
 
 The knobs are the fields of ``rnnls_tuning`` (see include/rnnls.h): the
 sketch's SM cap and full-step threshold, the tensor-core Gram's K-split
-limits, the batched Gram's chunks per CTA and the batched sketch's step cost.
+limits, the batched Gram's chunks per CTA, the batched sketch's step cost
+and the largest Lawson-Hanson problem that runs as a one-warp block.
 None changes what is computed beyond FP32 summation order.  The tuner
 times a caller-supplied step (CUDA events on the context's stream) for each
 candidate value of one knob at a time, keeping the others at their best so
@@ -30,12 +31,13 @@ CANDIDATES = {
     "gram_max_splits": [0, 8, 16, 64],
     "batch_gram_chunks": [0, 32, 64, 256],
     "batch_step_cost": [0, 60, 180, 300],
+    "lh_warp_max_d": [0, -1, 32, 128],
 }
 
 #: the knobs that act on each kind of workload
 KNOBS_FOR = {
-    "single": ["full_step_min_slots", "gram_min_chunks", "gram_max_splits"],
-    "batched": ["full_step_min_slots", "batch_step_cost", "batch_gram_chunks"],
+    "single": ["full_step_min_slots", "gram_min_chunks", "gram_max_splits", "lh_warp_max_d"],
+    "batched": ["full_step_min_slots", "batch_step_cost", "batch_gram_chunks", "lh_warp_max_d"],
 }
 
 

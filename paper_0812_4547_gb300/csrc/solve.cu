@@ -15,6 +15,7 @@
 //     (argmax of w, tolerance, sign of z, interpolation step) use these
 //     refined values and the same rules as the FP64 reference algorithm.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <vector>
 
@@ -194,6 +195,7 @@ struct lh_shared {
 };
 
 // block sum of floats (all threads get the result)
+template <int NT>
 __device__ float block_sum_f(float v, lh_shared &sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -202,10 +204,11 @@ __device__ float block_sum_f(float v, lh_shared &sh) {
   __syncthreads();
   float t = 0.0f;
 #pragma unroll
-  for (int q = 0; q < kLHThreads / 32; ++q) t += sh.fred[q];
+  for (int q = 0; q < NT / 32; ++q) t += sh.fred[q];
   return t;
 }
 
+template <int NT>
 __device__ ff block_sum_ff(ff v, lh_shared &sh) {
   for (int o = 16; o > 0; o >>= 1) {
     ff u{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
@@ -217,11 +220,12 @@ __device__ ff block_sum_ff(ff v, lh_shared &sh) {
   __syncthreads();
   ff t{0.0f, 0.0f};
 #pragma unroll
-  for (int q = 0; q < kLHThreads / 32; ++q) t = ff_add(t, sh.vred[q]);
+  for (int q = 0; q < NT / 32; ++q) t = ff_add(t, sh.vred[q]);
   return t;
 }
 
 // argmax of (valid, value) with ties to the smallest index; returns -1 if none
+template <int NT>
 __device__ int block_argmax_ff(bool valid, ff v, int idx, lh_shared &sh, ff &best) {
   int bi = valid ? idx : -1;
   ff bv = v;
@@ -242,7 +246,7 @@ __device__ int block_argmax_ff(bool valid, ff v, int idx, lh_shared &sh, ff &bes
   __syncthreads();
   bi = -1;
 #pragma unroll
-  for (int q = 0; q < kLHThreads / 32; ++q) {
+  for (int q = 0; q < NT / 32; ++q) {
     const int oi = sh.ired[q];
     const ff ov = sh.vred[q];
     if (oi >= 0 && (bi < 0 || ff_gt(ov, bv) || (!ff_gt(bv, ov) && oi < bi))) {
@@ -303,10 +307,11 @@ __device__ __forceinline__ int lanes_per_row(int rows) {
 
 // y[s] = sum_q B[s][q] g[q] for s < p (B symmetric: lanes of row s read
 // column s, rows of B at odd stride, so a warp touches distinct banks)
+template <int NT>
 __device__ __forceinline__ void apply_B(const lh_vecs &V, int p, const float *g, float *y) {
   const int tpr = lanes_per_row(p);
   const int part = threadIdx.x & (tpr - 1);
-  for (int base = 0; base < p; base += kLHThreads / tpr) {
+  for (int base = 0; base < p; base += NT / tpr) {
     const int s = base + threadIdx.x / tpr;
     const bool ok = s < p;
     float a0 = 0.0f, a1 = 0.0f;
@@ -325,10 +330,11 @@ __device__ __forceinline__ void apply_B(const lh_vecs &V, int p, const float *g,
 }
 
 // w_j = q_j - sum_s Q[j][slotvar[s]] x_s for every j (float-float)
+template <int NT>
 __device__ __noinline__ void compute_w(const lh_vecs &V, int d, int p) {
   const int tpj = lanes_per_row(d);
   const int part = threadIdx.x & (tpj - 1);
-  for (int base = 0; base < d; base += kLHThreads / tpj) {
+  for (int base = 0; base < d; base += NT / tpj) {
     const int j = base + threadIdx.x / tpj;
     const bool ok = j < d;
     dotff a0;
@@ -350,12 +356,13 @@ __device__ __noinline__ void compute_w(const lh_vecs &V, int d, int p) {
 
 // Fast path, phase 1: FP32 dual for every j and each warp's best candidate
 // (largest w_j outside P, ties to the smallest j) into sh.wkey / sh.widx.
+template <int NT>
 __device__ __forceinline__ void dual_and_warp_best(const lh_vecs &V, int d, int p, lh_shared &sh) {
   const int tpj = lanes_per_row(d);
   const int part = threadIdx.x & (tpj - 1);
   uint32_t bkey = 0u;
   uint32_t bidx = 0xffffffffu;
-  for (int base = 0; base < d; base += kLHThreads / tpj) {
+  for (int base = 0; base < d; base += NT / tpj) {
     const int j = base + threadIdx.x / tpj;
     const bool ok = j < d;
     float a0 = 0.0f, a1 = 0.0f;
@@ -390,10 +397,11 @@ __device__ __forceinline__ void dual_and_warp_best(const lh_vecs &V, int d, int 
 }
 
 // After the barrier: the block's candidate from the per-warp winners.
+template <int NT>
 __device__ __forceinline__ int merge_warp_best(const lh_shared &sh) {
   uint32_t bk = 0u;
   int bi = -1;
-  for (int q = 0; q < kLHThreads / 32; ++q) {
+  for (int q = 0; q < NT / 32; ++q) {
     const int i = sh.widx[q];
     if (i < 0) continue;
     const uint32_t k = sh.wkey[q];
@@ -407,12 +415,13 @@ __device__ __forceinline__ int merge_warp_best(const lh_shared &sh) {
 
 // Fast path, phase 2: v = B u with u_s = D_s Q[v_s][t] D_t made on the fly,
 // v into f3, per-warp partial sums of u'v into sh.wsum.
+template <int NT>
 __device__ __forceinline__ void bordered_v(const lh_vecs &V, int p, int t, float dt, lh_shared &sh) {
   const int tpr = lanes_per_row(p);
   const int part = threadIdx.x & (tpr - 1);
   const float *qt = V.Qh + t * V.ldQ;
   float uv = 0.0f;
-  for (int base = 0; base < p; base += kLHThreads / tpr) {
+  for (int base = 0; base < p; base += NT / tpr) {
     const int s = base + threadIdx.x / tpr;
     const bool ok = s < p;
     float a0 = 0.0f, a1 = 0.0f;
@@ -442,6 +451,7 @@ __device__ __forceinline__ void bordered_v(const lh_vecs &V, int p, int t, float
 
 // The entering candidate: argmax of w over j outside P and not rejected
 // (ties to the smallest j).  Warp 0 decides; everyone gets the result.
+template <int NT>
 __device__ __noinline__ int select_candidate(const lh_vecs &V, int d, lh_shared &sh, ff &best) {
   if (threadIdx.x < 32) {
     ff bv{0.0f, 0.0f};
@@ -469,6 +479,7 @@ __device__ __noinline__ int select_candidate(const lh_vecs &V, int d, lh_shared 
 
 // The interpolation step: over slots with z <= 0, the minimum of
 // x/(x - z) (ties to the smallest variable).  Warp 0 decides.
+template <int NT>
 __device__ __noinline__ int select_alpha(const lh_vecs &V, int p, lh_shared &sh, ff &amin) {
   if (threadIdx.x < 32) {
     ff bv{0.0f, 0.0f};
@@ -497,8 +508,9 @@ __device__ __noinline__ int select_alpha(const lh_vecs &V, int p, lh_shared &sh,
 }
 
 // res_i = q_{v_i} - sum_q Q[v_i][v_q] z_q for slots i < np (float-float)
+template <int NT>
 __device__ __noinline__ void residual_slots(const lh_vecs &V, int np) {
-  for (int i = threadIdx.x; i < np; i += kLHThreads) {
+  for (int i = threadIdx.x; i < np; i += NT) {
     const int vi = V.slotvar[i];
     const float *rh = V.Qh + vi * V.ldQ;
     const float *rl = V.Ql + vi * V.ldQ;
@@ -529,6 +541,7 @@ __device__ __noinline__ void residual_slots(const lh_vecs &V, int np) {
 // per step, so ill-conditioned blocks need more; once the corrections stop
 // shrinking, float-float rounding has been reached).
 constexpr int kMaxExtraRefine = 60;
+template <int NT>
 __device__ __noinline__ void passive_solve(const lh_vecs &V, lh_shared &sh, int np, bool bordered, float sc,
                                            int iters, bool have_initial = false) {
   __shared__ unsigned int corr_max[3];  // per step (rotating): largest |dz| / |z| as float bits
@@ -538,27 +551,27 @@ __device__ __noinline__ void passive_solve(const lh_vecs &V, lh_shared &sh, int 
   float prev = INFINITY;
   for (int step = have_initial ? 1 : 0; step <= cap; ++step) {
     if (step > 0) {
-      residual_slots(V, np);
+      residual_slots<NT>(V, np);
       __syncthreads();
     }
-    for (int s = threadIdx.x; s < np; s += kLHThreads) {
+    for (int s = threadIdx.x; s < np; s += NT) {
       const int v = V.slotvar[s];
       V.f1[s] = (step == 0) ? V.qh[v] : V.res[s].hi * V.Dsc[v];
     }
     __syncthreads();
-    apply_B(V, pb, V.f1, V.f2);
+    apply_B<NT>(V, pb, V.f1, V.f2);
     __syncthreads();
     if (bordered) {
       float part = 0.0f;
-      for (int s = threadIdx.x; s < pb; s += kLHThreads) part = fmaf(V.f3[s], V.f1[s], part);
-      const float vg = block_sum_f(part, sh);
+      for (int s = threadIdx.x; s < pb; s += NT) part = fmaf(V.f3[s], V.f1[s], part);
+      const float vg = block_sum_f<NT>(part, sh);
       const float yt = (V.f1[pb] - vg) / sc;
-      for (int s = threadIdx.x; s < pb; s += kLHThreads) V.f2[s] = fmaf(-V.f3[s], yt, V.f2[s]);
+      for (int s = threadIdx.x; s < pb; s += NT) V.f2[s] = fmaf(-V.f3[s], yt, V.f2[s]);
       if (threadIdx.x == 0) V.f2[pb] = yt;
       __syncthreads();
     }
     float mx = 0.0f;
-    for (int s = threadIdx.x; s < np; s += kLHThreads) {
+    for (int s = threadIdx.x; s < np; s += NT) {
       const float dz = V.f2[s] * V.Dsc[V.slotvar[s]];
       V.zs[s] = (step == 0) ? ff_make(dz) : ff_add(V.zs[s], ff_make(dz));
       mx = fmaxf(mx, fabsf(dz) / fmaxf(fabsf(V.zs[s].hi), 1e-30f));
@@ -578,14 +591,15 @@ __device__ __noinline__ void passive_solve(const lh_vecs &V, lh_shared &sh, int 
 
 // Drop slot s (Schur-complement downdate of B), then move the last slot
 // into s (B row/column, Q row, x, slot maps).  p = count before the drop.
+template <int NT>
 __device__ __noinline__ void drop_slot(const lh_vecs &V, int d, int s, int p) {
   const float bss = V.B[(int64_t)s * V.ldB + s];
-  for (int q = threadIdx.x; q < p; q += kLHThreads) V.f1[q] = V.B[(int64_t)q * V.ldB + s];
+  for (int q = threadIdx.x; q < p; q += NT) V.f1[q] = V.B[(int64_t)q * V.ldB + s];
   __syncthreads();
   const float ibss = 1.0f / bss;
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int a = warp; a < p; a += kLHThreads / 32) {
+    for (int a = warp; a < p; a += NT / 32) {
       const float fa = V.f1[a] * ibss;
       for (int c = lane; c < p; c += 32) V.B[a * V.ldB + c] = fmaf(-fa, V.f1[c], V.B[a * V.ldB + c]);
     }
@@ -593,9 +607,9 @@ __device__ __noinline__ void drop_slot(const lh_vecs &V, int d, int s, int p) {
   __syncthreads();
   const int last = p - 1;
   if (s != last) {
-    for (int q = threadIdx.x; q < p; q += kLHThreads) V.f1[q] = V.B[(int64_t)last * V.ldB + q];
+    for (int q = threadIdx.x; q < p; q += NT) V.f1[q] = V.B[(int64_t)last * V.ldB + q];
     __syncthreads();
-    for (int q = threadIdx.x; q < p; q += kLHThreads) {
+    for (int q = threadIdx.x; q < p; q += NT) {
       if (q == s) continue;
       const float val = V.f1[q];
       const int qq = (q == last) ? s : q;
@@ -647,6 +661,7 @@ __host__ __device__ inline lh_layout lh_make_layout(int d, bool q_smem, bool b_s
   return L;
 }
 
+template <int NT>
 __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &sh, int max_outer, int max_inner) {
   const int d = jb.d;
   const int D1 = d + 1;
@@ -660,7 +675,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
     float *qh = (float *)(smem_raw + L.off_Qh);
     float *ql = (float *)(smem_raw + L.off_Ql);
     const int ld = odd_ld(D1);
-    for (int e = tid; e < D1 * D1; e += kLHThreads) {
+    for (int e = tid; e < D1 * D1; e += NT) {
       const int i = e / D1, j = e - i * D1;
       const int64_t src = (int64_t)(i < d ? i : jb.qcol) * jb.ldq + (j < d ? j : jb.qcol);
       qh[i * ld + j] = jb.Qhi[src];
@@ -702,12 +717,12 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
   const ff tol = ff_from_double(tol_d);
   {
     int bad = 0;
-    for (int64_t e = tid; e < (int64_t)D1 * D1; e += kLHThreads) {
+    for (int64_t e = tid; e < (int64_t)D1 * D1; e += NT) {
       const int64_t i = e / D1, j = e - i * D1;
       bad |= !isfinite(jb.Qd[(i < d ? i : jb.qcol) * jb.ldq + (j < d ? j : jb.qcol)]);
     }
     if (__syncthreads_or(bad)) {
-      for (int j = tid; j < d; j += kLHThreads) jb.x[j] = 0.0;
+      for (int j = tid; j < d; j += NT) jb.x[j] = 0.0;
       if (tid == 0 && jb.info) {
         rnnls_info inf;
         inf.status = RNNLS_ENONFINITE;
@@ -722,7 +737,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
       return;
     }
   }
-  for (int j = tid; j < d; j += kLHThreads) {
+  for (int j = tid; j < d; j += NT) {
     const double qjj = jb.Qd[(int64_t)j * jb.ldq + j];
     const float dj = (qjj > 0.0) ? (float)(1.0 / sqrt(qjj)) : 0.0f;
     V.Dsc[j] = dj;
@@ -750,15 +765,15 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
       int t = -1;
       ff best{0.0f, 0.0f};
       if (accurate) {
-        compute_w(V, d, sh.p);
-        for (int j = tid; j < d; j += kLHThreads) V.rej[j] = 0;
+        compute_w<NT>(V, d, sh.p);
+        for (int j = tid; j < d; j += NT) V.rej[j] = 0;
         __syncthreads();
-        t = select_candidate(V, d, sh, best);
+        t = select_candidate<NT>(V, d, sh, best);
       } else {
-        dual_and_warp_best(V, d, sh.p, sh);
-        for (int j = tid; j < d; j += kLHThreads) V.rej[j] = 0;
+        dual_and_warp_best<NT>(V, d, sh.p, sh);
+        for (int j = tid; j < d; j += NT) V.rej[j] = 0;
         __syncthreads();
-        t = merge_warp_best(sh);
+        t = merge_warp_best<NT>(sh);
         if (t >= 0) best = V.w[t];
       }
       for (;;) {
@@ -766,15 +781,15 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
         const int p = sh.p;
         const float dt = V.Dsc[t];
         // v = B u and the Schur value sc = 1 - u'v (fixed summation order)
-        bordered_v(V, p, t, dt, sh);
+        bordered_v<NT>(V, p, t, dt, sh);
         __syncthreads();
         float uv = 0.0f;
-        for (int q = 0; q < kLHThreads / 32; ++q) uv += sh.wsum[q];
+        for (int q = 0; q < NT / 32; ++q) uv += sh.wsum[q];
         const float sc = 1.0f - uv;
         if (!(sc > 1e-13f) || dt == 0.0f) {
           if (tid == 0) V.rej[t] = 1;
           __syncthreads();
-          t = select_candidate(V, d, sh, best);
+          t = select_candidate<NT>(V, d, sh, best);
           continue;
         }
         // x_P solves the current passive set, so the bordered solution is
@@ -782,7 +797,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
         const float yt = dt * best.hi / sc;
         const float isc = 1.0f / sc;
         int neg = 0;
-        for (int s2 = tid; s2 < p; s2 += kLHThreads) {
+        for (int s2 = tid; s2 < p; s2 += NT) {
           const float zf = fmaf(-V.Dsc[V.slotvar[s2]] * V.f3[s2], yt, V.xs[s2].hi);
           V.zs[s2] = ff_make(zf);
           neg |= (zf <= 0.0f) ? 1 : 0;
@@ -793,25 +808,25 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
         }
         if (accurate) {
           __syncthreads();
-          passive_solve(V, sh, p + 1, true, sc, 2, true);
+          passive_solve<NT>(V, sh, p + 1, true, sc, 2, true);
           if (!ff_gt0(V.zs[p])) {
             if (tid == 0) V.rej[t] = 1;
             __syncthreads();
-            t = select_candidate(V, d, sh, best);
+            t = select_candidate<NT>(V, d, sh, best);
             continue;
           }
           neg = 0;
-          for (int s2 = tid; s2 < p; s2 += kLHThreads) neg |= ff_le0(V.zs[s2]) ? 1 : 0;
+          for (int s2 = tid; s2 < p; s2 += NT) neg |= ff_le0(V.zs[s2]) ? 1 : 0;
         }
         // commit the bordered inverse: B += v v'/sc, new row/col -v/sc, corner 1/sc
         {
           const int warp = tid >> 5, lane = tid & 31;
-          for (int a = warp; a < p; a += kLHThreads / 32) {
+          for (int a = warp; a < p; a += NT / 32) {
             const float fa = V.f3[a] * isc;
             for (int c = lane; c < p; c += 32) V.B[a * V.ldB + c] = fmaf(fa, V.f3[c], V.B[a * V.ldB + c]);
           }
         }
-        for (int s2 = tid; s2 < p; s2 += kLHThreads) {
+        for (int s2 = tid; s2 < p; s2 += NT) {
           V.B[s2 * V.ldB + p] = -V.f3[s2] * isc;
           V.B[p * V.ldB + s2] = -V.f3[s2] * isc;
         }
@@ -836,21 +851,21 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
         if (accurate) break;
         // verify the FP32 end point
         const int p = sh.p;
-        if (p > 0) passive_solve(V, sh, p, false, 0.0f, 3);
+        if (p > 0) passive_solve<NT>(V, sh, p, false, 0.0f, 3);
         int neg = 0;
-        for (int s = tid; s < p; s += kLHThreads) neg |= ff_le0(V.zs[s]) ? 1 : 0;
+        for (int s = tid; s < p; s += NT) neg |= ff_le0(V.zs[s]) ? 1 : 0;
         if (__syncthreads_or(neg)) {
           accurate = true;
           accurate_mode = 1;
           go_inner = true;
           continue;
         }
-        for (int s = tid; s < p; s += kLHThreads) V.xs[s] = V.zs[s];
+        for (int s = tid; s < p; s += NT) V.xs[s] = V.zs[s];
         __syncthreads();
-        compute_w(V, d, p);
+        compute_w<NT>(V, d, p);
         __syncthreads();
         int up = 0;
-        for (int j = tid; j < d; j += kLHThreads) up |= (V.varslot[j] < 0 && ff_gt(V.w[j], tol)) ? 1 : 0;
+        for (int j = tid; j < d; j += NT) up |= (V.varslot[j] < 0 && ff_gt(V.w[j], tol)) ? 1 : 0;
         if (__syncthreads_or(up)) {
           accurate = true;
           accurate_mode = 2;
@@ -874,9 +889,9 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
       ++inner;
       const int p = sh.p;
       ff amin;
-      const int jmin = select_alpha(V, p, sh, amin);
+      const int jmin = select_alpha<NT>(V, p, sh, amin);
       if (jmin < 0) {
-        for (int s = tid; s < p; s += kLHThreads) V.xs[s] = V.zs[s];
+        for (int s = tid; s < p; s += NT) V.xs[s] = V.zs[s];
         __syncthreads();
         break;
       }
@@ -885,7 +900,7 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
         __syncthreads();
         break;
       }
-      for (int s = tid; s < p; s += kLHThreads) V.xs[s] = ff_add(V.xs[s], ff_mul(amin, ff_sub(V.zs[s], V.xs[s])));
+      for (int s = tid; s < p; s += NT) V.xs[s] = ff_add(V.xs[s], ff_mul(amin, ff_sub(V.zs[s], V.xs[s])));
       __syncthreads();
       if (tid == 0) V.xs[V.varslot[jmin]] = ff{0.0f, 0.0f};
       __syncthreads();
@@ -894,40 +909,40 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
           const int v = V.slotvar[s];
           __syncthreads();
           if (tid == 0) V.varslot[v] = -1;
-          drop_slot(V, d, s, sh.p);
+          drop_slot<NT>(V, d, s, sh.p);
           if (tid == 0) sh.p = sh.p - 1;
           __syncthreads();
         }
       }
       if (sh.p == 0) break;
-      passive_solve(V, sh, sh.p, false, 0.0f, accurate ? 2 : 0);
+      passive_solve<NT>(V, sh, sh.p, false, 0.0f, accurate ? 2 : 0);
     }
     if (sh.status != RNNLS_OK) break;
   }
 
   // outputs: x, dual maximum over the active set, objective
-  compute_w(V, d, sh.p);
+  compute_w<NT>(V, d, sh.p);
   __syncthreads();
-  for (int j = tid; j < d; j += kLHThreads) {
+  for (int j = tid; j < d; j += NT) {
     const int s = V.varslot[j];
     jb.x[j] = (s >= 0) ? ff_to_double(V.xs[s]) : 0.0;
   }
   ff dmax{0.0f, 0.0f};
   int dj = -1;
-  for (int j = tid; j < d; j += kLHThreads)
+  for (int j = tid; j < d; j += NT)
     if (V.varslot[j] < 0 && (dj < 0 || ff_gt(V.w[j], dmax))) {
       dmax = V.w[j];
       dj = j;
     }
   ff dbest;
-  const int dbi = block_argmax_ff(dj >= 0, dmax, dj, sh, dbest);
+  const int dbi = block_argmax_ff<NT>(dj >= 0, dmax, dj, sh, dbest);
   // objective = s's - sum over P of x_j (q_j + w_j)   (w = q - Qx)
   ff part{0.0f, 0.0f};
-  for (int s = tid; s < sh.p; s += kLHThreads) {
+  for (int s = tid; s < sh.p; s += NT) {
     const int v = V.slotvar[s];
     part = ff_add(part, ff_mul(V.xs[s], ff_add(V.qv[v], V.w[v])));
   }
-  const ff qxpxw = block_sum_ff(part, sh);
+  const ff qxpxw = block_sum_ff<NT>(part, sh);
   if (tid == 0 && jb.info) {
     rnnls_info inf;
     inf.status = sh.status;
@@ -943,20 +958,24 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
   }
 }
 
-__global__ void __launch_bounds__(kLHThreads, 2) lh_kernel(const lh_job *__restrict__ jobs, int max_outer_mul,
-                                                           int max_inner_mul) {
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 32 ? 16 : 2) lh_kernel(const lh_job *__restrict__ jobs, int max_outer_mul,
+                                                                  int max_inner_mul, int warp_max_d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ lh_shared sh;
   const lh_job jb = jobs[blockIdx.x];
   if (jb.d <= 0) return;  // a problem the device-side plan refused (its info says so)
-  lh_block(jb, smem_raw, sh, max_outer_mul * jb.d, max_inner_mul * jb.d);
+  // problems up to warp_max_d unknowns run as one-warp blocks, the others as
+  // 256-thread blocks: each launch skips the other kind
+  if ((NT == 32) != (jb.d <= warp_max_d)) return;
+  lh_block<NT>(jb, smem_raw, sh, max_outer_mul * jb.d, max_inner_mul * jb.d);
 }
 
-__global__ void __launch_bounds__(kLHThreads, 1) lh_kernel_one(const lh_job jb, int max_outer_mul,
-                                                               int max_inner_mul) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) lh_kernel_one(const lh_job jb, int max_outer_mul, int max_inner_mul) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ lh_shared sh;
-  lh_block(jb, smem_raw, sh, max_outer_mul * jb.d, max_inner_mul * jb.d);
+  lh_block<NT>(jb, smem_raw, sh, max_outer_mul * jb.d, max_inner_mul * jb.d);
 }
 
 // ||A x - b||^2 in FP64 (evaluation of Definition 1's objective)
@@ -1043,12 +1062,34 @@ size_t lh_bg_bytes(rnnls_ctx *ctx, int d) {
   return lh_b_fits(ctx, d) ? 0 : align_up((size_t)odd_ld(d) * d * sizeof(float), 256);
 }
 
-int lh_launch(rnnls_ctx *ctx, const lh_job *d_jobs, int64_t count, size_t smem) {
+// Problems with few unknowns run as one-warp blocks (one warp per problem:
+// the block's barriers and reductions stay inside the warp, and many
+// problems share an SM); the others as 256-thread blocks.
+constexpr int kLHWarpMaxD = 64;
+int lh_warp_max_d(const rnnls_ctx *ctx) {
+  const int v = ctx->tune.lh_warp_max_d;
+  return v == 0 ? kLHWarpMaxD : (v < 0 ? 0 : v);
+}
+
+// d_jobs: `count` jobs with d in [min_d, max_d] (bounds; device-made job
+// tables pass 1 and their bound), smem: the largest block's shared memory.
+int lh_launch(rnnls_ctx *ctx, const lh_job *d_jobs, int64_t count, size_t smem, int min_d, int max_d) {
   prof_scope ps(ctx, K_LH);
   if (smem + kLHStaticSmem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
-  static smem_attr lh_attr;
-  RNNLS_CUDA_TRY(lh_attr.ensure((const void *)lh_kernel, smem));
-  lh_kernel<<<(unsigned)count, kLHThreads, smem, ctx->stream>>>(d_jobs, 3, 30);
+  const int wmd = lh_warp_max_d(ctx);
+  if (min_d <= wmd) {
+    // the one-warp blocks' problems have d <= wmd: their shared memory is at most that of d = wmd
+    const size_t s32 = std::min(smem, lh_make_layout(std::min(wmd, max_d), true, true).bytes);
+    static smem_attr lh_attr32;
+    RNNLS_CUDA_TRY(lh_attr32.ensure((const void *)lh_kernel<32>, s32));
+    lh_kernel<32><<<(unsigned)count, 32, s32, ctx->stream>>>(d_jobs, 3, 30, wmd);
+    if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
+  }
+  if (max_d > wmd) {
+    static smem_attr lh_attr;
+    RNNLS_CUDA_TRY(lh_attr.ensure((const void *)lh_kernel<kLHThreads>, smem));
+    lh_kernel<kLHThreads><<<(unsigned)count, kLHThreads, smem, ctx->stream>>>(d_jobs, 3, 30, wmd);
+  }
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 
@@ -1056,9 +1097,15 @@ int lh_launch_one(rnnls_ctx *ctx, const lh_job &jb) {
   prof_scope ps(ctx, K_LH);
   const size_t smem = lh_make_layout(jb.d, jb.q_smem != 0, jb.Bg == nullptr).bytes;
   if (smem + kLHStaticSmem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
-  static smem_attr one_attr;
-  RNNLS_CUDA_TRY(one_attr.ensure((const void *)lh_kernel_one, smem));
-  lh_kernel_one<<<1, kLHThreads, smem, ctx->stream>>>(jb, 3, 30);
+  if (jb.d <= lh_warp_max_d(ctx)) {
+    static smem_attr one_attr32;
+    RNNLS_CUDA_TRY(one_attr32.ensure((const void *)lh_kernel_one<32>, smem));
+    lh_kernel_one<32><<<1, 32, smem, ctx->stream>>>(jb, 3, 30);
+  } else {
+    static smem_attr one_attr;
+    RNNLS_CUDA_TRY(one_attr.ensure((const void *)lh_kernel_one<kLHThreads>, smem));
+    lh_kernel_one<kLHThreads><<<1, kLHThreads, smem, ctx->stream>>>(jb, 3, 30);
+  }
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
 
@@ -1163,9 +1210,12 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   size_t bytes = tbytes + 256;
   size_t smem = 0;
   int64_t tiles = 0;
+  int min_d = INT_MAX, max_d = 0;
   for (int64_t i = 0; i < count; ++i) {
     const rnnls_problem &pb = probs[i];
     const int di = (int)pb.d;
+    min_d = std::min(min_d, di);
+    max_d = std::max(max_d, di);
     gjs[(size_t)i] = gram_tc_plan(pb.SA, pb.ldsa, pb.Sb, pb.r, 1, pb.r, di, 0, 1,
                                   tune_or(ctx->tune.batch_gram_chunks, kBatchChunksPerCta), gram_min_chunks(ctx),
                                   gram_max_splits(ctx));
@@ -1232,7 +1282,7 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   const lh_job *d_jobs = (const lh_job *)(d_tables + tab_jobs + 2 * tab_first);
   st = gram_tc_launch_batched(ctx, d_gj, d_first_col, d_first_cta, (int)count, cols, ctas);
   if (st) return st;
-  return lh_launch(ctx, d_jobs, count, smem);
+  return lh_launch(ctx, d_jobs, count, smem, min_d, max_d);
 }
 
 // ---------------------------------------------------------------------------
@@ -1420,7 +1470,7 @@ int solve_batched_device(rnnls_ctx *ctx, const rnnls_problem *d_probs, int64_t c
   st = gram_tc_launch_batched(ctx, a.gjobs, a.first_col, a.first_cta, (int)count, count * D1,
                               count * (int64_t)tiles_max * splits_max);
   if (st) return st;
-  return lh_launch(ctx, a.ljobs, count, smem);
+  return lh_launch(ctx, a.ljobs, count, smem, 1, md);
 }
 
 int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, int64_t ldsb, int64_t r, int64_t d,
@@ -1472,7 +1522,7 @@ int solve_multi(rnnls_ctx *ctx, const float *SA, int64_t ldsa, const float *SB, 
   memcpy(ctx->pinned, jobs.data(), jbytes);
   RNNLS_CUDA_TRY(cudaMemcpyAsync(d_jobs, ctx->pinned, jbytes, cudaMemcpyHostToDevice, s));
   RNNLS_CUDA_TRY(cudaEventRecord(ctx->pinned_ready, s));
-  return lh_launch(ctx, d_jobs, nrhs, lh_make_layout((int)d, false, bfit).bytes);
+  return lh_launch(ctx, d_jobs, nrhs, lh_make_layout((int)d, false, bfit).bytes, (int)d, (int)d);
 }
 
 int residual_f32(rnnls_ctx *ctx, const float *A, int64_t lda, const float *b, int64_t n, int64_t d,

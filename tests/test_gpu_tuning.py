@@ -17,11 +17,11 @@ def test_tuning_round_trip_and_validation():
     try:
         assert all(v == 0 for v in ctx.get_tuning().values())
         t = {"sketch_sms": 100, "full_step_min_slots": 64, "gram_min_chunks": 4, "gram_max_splits": 16,
-             "batch_gram_chunks": 64, "batch_step_cost": 200}
+             "batch_gram_chunks": 64, "batch_step_cost": 200, "lh_warp_max_d": 96}
         ctx.set_tuning(t)
         assert ctx.get_tuning() == t
         for bad in ({"full_step_min_slots": 47}, {"gram_max_splits": 1025}, {"sketch_sms": -1},
-                    {"batch_step_cost": 100001}):
+                    {"batch_step_cost": 100001}, {"lh_warp_max_d": -2}, {"lh_warp_max_d": 1025}):
             with pytest.raises(B.RNNLSError) as e:
                 ctx.set_tuning(bad)
             assert e.value.status == B.RNNLS_EINVAL
@@ -143,5 +143,37 @@ def test_autotuner_end_to_end(tmp_path):
         e2 = T.tune(ctx, step, "single", {"n": n, "d": d, "r": r}, path=path, candidates=cands)
         assert e2["cached"] and e2["tuning"] == e1["tuning"]
         assert e1["key"] in T.load_cache(path)["entries"]
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("d", [8, 40, 64, 100])
+def test_lh_team_size_gives_the_same_solve(orc, d):
+    """Lawson-Hanson as one-warp blocks or as 256-thread blocks: the same
+    active set and x within 1e-6 of the oracle's (one problem and a batch)."""
+    import torch
+
+    import paper_0812_4547_gb300 as P
+
+    rng = np.random.default_rng(d)
+    r = 2048
+    SAh = (rng.standard_normal((r, d)) * np.exp(rng.standard_normal(d))).astype(np.float32)
+    x0 = np.abs(rng.standard_normal(d)) * (rng.random(d) < 0.5)
+    Sbh = (SAh.astype(np.float64) @ x0 + rng.standard_normal(r)).astype(np.float32)
+    x_ref, _ = orc.nnls(SAh, Sbh)
+    SA, Sb = dev_colmajor(SAh), dev_vec(Sbh)
+    ctx = P.Context(0)
+    try:
+        for wmd in (-1, 0, 1024):
+            ctx.set_tuning({"lh_warp_max_d": wmd})
+            x, info = ctx.solve(SA, Sb)
+            xs = torch.empty(d, dtype=torch.float64, device="cuda")
+            infos = torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device="cuda")
+            ctx.solve_batched([(SA, Sb, xs, infos)])
+            torch.cuda.synchronize()
+            for xg, inf in ((host(x), info), (host(xs), infos)):
+                assert P.info_dict(inf)["status"] == 0
+                assert np.array_equal(xg > 0, x_ref > 0), wmd
+                assert np.max(np.abs(xg - x_ref)) <= 1e-6 * np.max(np.abs(x_ref)), wmd
     finally:
         ctx.close()
