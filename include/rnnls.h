@@ -145,7 +145,7 @@ typedef struct rnnls_tuning {
   int32_t batch_gram_chunks;
   int32_t batch_step_cost;
   int32_t lh_warp_max_d;  /* Lawson-Hanson problems with d up to this run as one-warp
-                             blocks, larger ones as 256-thread blocks (0: 64; -1: never) */
+                             blocks, larger ones as 256-thread blocks (0: none) */
   int32_t reserved;       /* zero */
 } rnnls_tuning;
 

@@ -31,7 +31,7 @@ CANDIDATES = {
     "gram_max_splits": [0, 8, 16, 64],
     "batch_gram_chunks": [0, 32, 64, 256],
     "batch_step_cost": [0, 60, 180, 300],
-    "lh_warp_max_d": [0, -1, 32, 128],
+    "lh_warp_max_d": [0, 32, 64],
 }
 
 #: the knobs that act on each kind of workload
@@ -85,7 +85,7 @@ def coordinate_search(time_fn, knobs: list, candidates: dict | None = None, base
     t_best = t_base
     for _ in range(rounds):
         for k in knobs:
-            for v in candidates[k]:
+            for v in candidates.get(k, ()):
                 if best.get(k, 0) == v:
                     continue
                 trial = dict(best)

@@ -314,7 +314,7 @@ int rnnls_set_tuning(rnnls_ctx *ctx, const rnnls_tuning *t) {
   auto in = [](int v, int lo, int hi) { return v == 0 || (v >= lo && v <= hi); };
   if (t->sketch_sms < 0 || !in(t->full_step_min_slots, 48, 1024) || !in(t->gram_min_chunks, 1, 65536) ||
       !in(t->gram_max_splits, 1, 1024) || !in(t->batch_gram_chunks, 1, 65536) ||
-      !in(t->batch_step_cost, 1, 100000) || !(t->lh_warp_max_d == -1 || in(t->lh_warp_max_d, 1, 1024)) ||
+      !in(t->batch_step_cost, 1, 100000) || !in(t->lh_warp_max_d, 1, 1024) ||
       t->reserved != 0)
     return RNNLS_EINVAL;
   ctx->tune = *t;

@@ -1062,14 +1062,15 @@ size_t lh_bg_bytes(rnnls_ctx *ctx, int d) {
   return lh_b_fits(ctx, d) ? 0 : align_up((size_t)odd_ld(d) * d * sizeof(float), 256);
 }
 
-// Problems with few unknowns run as one-warp blocks (one warp per problem:
-// the block's barriers and reductions stay inside the warp, and many
-// problems share an SM); the others as 256-thread blocks.
-constexpr int kLHWarpMaxD = 64;
-int lh_warp_max_d(const rnnls_ctx *ctx) {
-  const int v = ctx->tune.lh_warp_max_d;
-  return v == 0 ? kLHWarpMaxD : (v < 0 ? 0 : v);
-}
+// Problems with up to lh_warp_max_d unknowns can run as one-warp blocks (one
+// warp per problem: the block's barriers and reductions stay inside the
+// warp, and many problems share an SM); by default every problem runs as a
+// 256-thread block.  Measured on GB300 (term-document sketches, one solve):
+// d = 16: 88 vs 55 us, d = 64: 482 vs 148 us, d = 128: 1982 vs 451 us for
+// one warp vs 256 threads; the per-iteration dot products and inverse
+// updates, not the block barriers, set a solve's time, so eight times the
+// work per thread costs more than the barriers save.
+int lh_warp_max_d(const rnnls_ctx *ctx) { return ctx->tune.lh_warp_max_d; }
 
 // d_jobs: `count` jobs with d in [min_d, max_d] (bounds; device-made job
 // tables pass 1 and their bound), smem: the largest block's shared memory.
