@@ -53,6 +53,13 @@ constexpr uint32_t kSpinLimit = 1u << 22;                    // bounded wait on 
 #define RNNLS_FULL_MIN_SLOTS 48
 #endif
 constexpr int kFullMinSlots = RNNLS_FULL_MIN_SLOTS;
+// From this many plan rows per thread on (in the full-step mode), the
+// batched kernel combines steps in pairs (each row reads one word per two
+// steps).
+#ifndef RNNLS_PAIR_MIN_SLOTS
+#define RNNLS_PAIR_MIN_SLOTS 48
+#endif
+constexpr int kPairMinSlots = RNNLS_PAIR_MIN_SLOTS;
 
 __device__ __forceinline__ void bar_worker(int w) {
   asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
@@ -184,6 +191,40 @@ __device__ __forceinline__ void cross_chunk_h4(float *__restrict__ st, int tid) 
     *reinterpret_cast<float4 *>(st + kM + o) = z1;
     *reinterpret_cast<float4 *>(st + 2 * kM + o) = z2;
     *reinterpret_cast<float4 *>(st + 3 * kM + o) = z3;
+  }
+}
+
+// cross_chunk_h4 on a pair's second step (buffer `sb`), then the butterfly
+// with the first step's already transformed buffer `fb`, word by word:
+// fb <- fb + sb, sb <- fb - sb.
+__device__ __forceinline__ void cross_chunk_h4_pair(float *__restrict__ fb, float *__restrict__ sb, int tid) {
+#pragma unroll 2
+  for (int k = 0; k < kM / (4 * kThreads); ++k) {
+    const int o = 4 * (tid + kThreads * k);
+    float4 z0 = *reinterpret_cast<const float4 *>(sb + o);
+    float4 z1 = *reinterpret_cast<const float4 *>(sb + kM + o);
+    float4 z2 = *reinterpret_cast<const float4 *>(sb + 2 * kM + o);
+    float4 z3 = *reinterpret_cast<const float4 *>(sb + 3 * kM + o);
+    float4 f0 = *reinterpret_cast<const float4 *>(fb + o);
+    float4 f1 = *reinterpret_cast<const float4 *>(fb + kM + o);
+    float4 f2 = *reinterpret_cast<const float4 *>(fb + 2 * kM + o);
+    float4 f3 = *reinterpret_cast<const float4 *>(fb + 3 * kM + o);
+    bfly4(z0, z1);
+    bfly4(z2, z3);
+    bfly4(z0, z2);
+    bfly4(z1, z3);
+    bfly4(f0, z0);
+    bfly4(f1, z1);
+    bfly4(f2, z2);
+    bfly4(f3, z3);
+    *reinterpret_cast<float4 *>(fb + o) = f0;
+    *reinterpret_cast<float4 *>(fb + kM + o) = f1;
+    *reinterpret_cast<float4 *>(fb + 2 * kM + o) = f2;
+    *reinterpret_cast<float4 *>(fb + 3 * kM + o) = f3;
+    *reinterpret_cast<float4 *>(sb + o) = z0;
+    *reinterpret_cast<float4 *>(sb + kM + o) = z1;
+    *reinterpret_cast<float4 *>(sb + 2 * kM + o) = z2;
+    *reinterpret_cast<float4 *>(sb + 3 * kM + o) = z3;
   }
 }
 
@@ -1210,9 +1251,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     ic.next(jobs, njobs);
     iq = (iq + 1 == kStages) ? 0 : iq + 1;
   };
+  // thread 0 keeps up to kStages steps loaded or in flight ahead of the
+  // last step whose buffer is free (`consumed`; a pair's first step is freed
+  // with its second)
+  int64_t n_issued = 0, consumed = 0;
   if (tid == 0) {
     issue();
-    if (nsteps > 1) issue();
+    n_issued = 1;
+    if (nsteps > 1) {
+      issue();
+      n_issued = 2;
+    }
   }
 
   batch_cursor cur;
@@ -1221,6 +1270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int64_t loaded_kg = -1;
   int q = 0;
   uint32_t phase = 0;
+  int pair_q = -1;  // buffer of the pending first step of a step pair, or -1
   for (int64_t ls = 0; ls < nsteps; ++ls) {
     const int ji = cur.ji;
     const int64_t j = cur.j, u = cur.u, kg = cur.kg;
@@ -1242,10 +1292,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       loaded_ji = ji;
       loaded_kg = kg;
     }
-    __syncthreads();  // step ls-1 is done with its buffer
-    if (tid == 0 && ls + 2 < nsteps) {
+    __syncthreads();  // the steps before `consumed` are done with their buffers
+    if (tid == 0 && n_issued < nsteps && n_issued < consumed + kStages) {
       fence_proxy_async();
-      issue();
+      do {
+        issue();
+        ++n_issued;
+      } while (n_issued < nsteps && n_issued < consumed + kStages);
     }
     {
       const uint32_t bar = smem_u32(&mbar[q]);
@@ -1328,12 +1381,37 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     const bool full = slots >= J0.full_min;
+    // Step pairs (full-step mode, kPairMinSlots or more rows per thread):
+    // steps j (even) and j + 1 of a unit are combined together.  After both
+    // are transformed, buffer of j holds z_j + z_(j+1) and buffer of j + 1
+    // z_j - z_(j+1), word by word; a row with chunk-group bits h' = h >> 2
+    // adds (-1)^popcount(h' & j) times the word of the first buffer if h' is
+    // even, of the second if odd (the signs of j and j + 1 differ exactly by
+    // h' & 1).  Each row then reads one word per two steps.
+    const bool pair_second = pair_q >= 0;
+    const bool pair_first = !pair_second && full && slots >= kPairMinSlots && (j & 1) == 0 && j + 1 < J0.J &&
+                            ls + 1 < nsteps;
     if (full) {
-      cross_chunk_h4(stage + q * kStageFloats, tid);
+      if (pair_second)
+        cross_chunk_h4_pair(stage + pair_q * kStageFloats, stage + q * kStageFloats, tid);
+      else
+        cross_chunk_h4(stage + q * kStageFloats, tid);
       __syncthreads();
     }
+    if (pair_first) {
+      pair_q = q;
+      cur.next(jobs, njobs);
+      if (++q == kStages) {
+        q = 0;
+        phase ^= 1u;
+      }
+      continue;
+    }
 
-    const uint32_t jm = (uint32_t)j << 16;
+    const uint32_t jm = (uint32_t)(pair_second ? j - 1 : j) << 16;
+    // the first buffer of a pair (or this step's), and the offset of the second
+    const uint32_t cb_u32 = pair_second ? stage_u32 + (uint32_t)(pair_q * kStageFloats) * 4u : step_u32;
+    const uint32_t cb_delta = pair_second ? step_u32 - cb_u32 : 0u;
     {
       uint32_t pk[8], acc[8], pkn[8], accn[8];
       tmem_wait_st();
@@ -1346,7 +1424,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld8(t_pk + s8 + 8, pkn);
           tmem_ld8(t_acc + s8 + 8, accn);
         }
-        if (full) {
+        if (pair_second) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const uint32_t p = pk[e];
+            const float y = lds_1(cb_u32 + (p & 0xfffcu) + ((p >> 16) & 1u) * cb_delta);
+            acc[e] = __float_as_uint(__uint_as_float(acc[e]) + xor_sign(y, (uint32_t)__popc(p & jm) << 31));
+          }
+        } else if (full) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const uint32_t p = pk[e];
@@ -1382,6 +1467,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       q = 0;
       phase ^= 1u;
     }
+    consumed = ls + 1;
+    pair_q = -1;
 
     // end of this block's part of (instance ji, unit u)
     if (j == J0.J - 1 || ls == nsteps - 1) {
