@@ -1468,6 +1468,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       phase ^= 1u;
     }
     consumed = ls + 1;
+    const int qpair = pair_q;  // a finished pair's first buffer (free now), or -1
     pair_q = -1;
 
     // end of this block's part of (instance ji, unit u)
@@ -1482,14 +1483,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       tmem_wait_st();
       if (nseg == 1) {
         // Whole unit in this block: its rows k0 .. k0 + nk - 1 (a plan group
-        // holds consecutive rows) go through this step's buffer, 16384 at a
-        // time, so that the sketch column is written with coalesced stores.
-        // The buffer is refilled only after the next step's first barrier.
+        // holds consecutive rows) go through this step's buffer (and, after a
+        // step pair, the pair's first buffer too), 16384 (32768) at a time,
+        // so that the sketch column is written with coalesced stores.  The
+        // buffers are refilled only after the next step's first barrier.
         float *ost = stage + qs * kStageFloats;
+        float *ost2 = stage + (qpair >= 0 ? qpair : qs) * kStageFloats;
+        const int64_t span = (qpair >= 0 ? 2 : 1) * (int64_t)kStageFloats;
         const int64_t k0 = kg * J0.rpg;
         const int64_t nk = min(J0.rpg, (int64_t)J0.r - k0);
         float *dst = ((col < d) ? J0.SA + (int64_t)col * J0.ldsa : J0.SB) + k0;
-        for (int64_t h0 = 0; h0 < nk; h0 += kStageFloats) {
+        for (int64_t h0 = 0; h0 < nk; h0 += span) {
           __syncthreads();  // the combine (or the previous copy) is done with the buffer
           for (int s32 = 0; s32 < slots; s32 += 32) {
             const int n8 = min(4, (slots - s32) >> 3);
@@ -1505,13 +1509,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
               const int64_t o = (int64_t)kk[e] - k0 - h0;
-              if (kk[e] < 0 || o < 0 || o >= kStageFloats) continue;
-              ost[o] = poisoned ? __int_as_float(0x7fc00000) : J0.scale * __uint_as_float(acc[e]);
+              if (kk[e] < 0 || o < 0 || o >= span) continue;
+              (o < kStageFloats ? ost : ost2)[o & (kStageFloats - 1)] =
+                  poisoned ? __int_as_float(0x7fc00000) : J0.scale * __uint_as_float(acc[e]);
             }
           }
           __syncthreads();
-          const int64_t cnt = min((int64_t)kStageFloats, nk - h0);
-          for (int64_t i = tid; i < cnt; i += kThreads) dst[h0 + i] = ost[i];
+          const int64_t cnt = min(span, nk - h0);
+          for (int64_t i = tid; i < cnt; i += kThreads) dst[h0 + i] = (i < kStageFloats ? ost : ost2)[i & (kStageFloats - 1)];
         }
         for (int s8 = 0; s8 < slots; s8 += 8) tmem_st8(t_acc + s8, zero8);
       } else {
@@ -1951,7 +1956,10 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
     const double step_cost = (double)tune_or(ctx->tune.batch_step_cost, 114);
     for (int t = 0; t < nb; ++t) {
       const srht_job &J = sj[(size_t)t];
-      wt[(size_t)t] = step_cost + J.slots + 6.0 * (double)J.slots / (double)J.J;
+      // steps combined in pairs (full-step mode) read each row once per two
+      // steps: about half the rows' cost, plus the pair's extra butterfly pass
+      const bool pairs = J.slots >= J.full_min && J.slots >= kPairMinSlots && J.J >= 2;
+      wt[(size_t)t] = step_cost + (pairs ? 16.0 + 0.55 * J.slots : (double)J.slots) + 6.0 * (double)J.slots / (double)J.J;
       cum[(size_t)t + 1] = cum[(size_t)t] + wt[(size_t)t] * (double)(J.U * J.J);
     }
     int t = 0;
