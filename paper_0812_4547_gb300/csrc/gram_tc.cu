@@ -29,8 +29,9 @@
 // Work split: a CTA owns one tile of Q (128 rows i x 64 columns j; tiles
 // wholly below the diagonal are skipped) and a range of 32-row chunks of X.
 // Eight warps slice their share of the tile's columns into shared memory
-// (K-major core matrices, two buffers; the next chunk's values are loaded
-// into registers ahead) and drain the accumulators; a ninth warp issues, per
+// (K-major core matrices, two buffers; the values of the next three chunks
+// are copied ahead into a ring in shared memory with cp.async) and drain the
+// accumulators; a ninth warp issues, per
 // chunk, 21 x 2 tcgen05.mma (M = 128, N = 64, K = 16) into the four
 // accumulators and commits them to an mbarrier.  The warps meet only at
 // mbarriers: "full" (a buffer is sliced), "mma_done" (the tensor cores are
@@ -63,12 +64,17 @@ constexpr uint32_t kStride = (kKC / 8) * 128;  // bytes between core matrices ad
 constexpr uint32_t kASlice = kTM * kKC * 2;    // bytes of one slice of the 128-row operand
 constexpr uint32_t kBSlice = kTN * kKC * 2;    // bytes of one slice of the 64-row operand
 constexpr uint32_t kBufBytes = kSl * (kASlice + kBSlice);
-constexpr size_t kTcSmem = 2 * (size_t)kBufBytes;
+// raw FP32 values of a chunk, copied ahead: per slicing thread 16 rows of its
+// A feature and 8 of its B feature, stored as 16-byte units [unit][thread]
+constexpr int kRawDepth = 3;                       // chunks copied ahead of the one being sliced
+constexpr uint32_t kRawA = kSliceThreads * 64;     // bytes of a chunk's A values
+constexpr uint32_t kRawBytes = kRawA + kSliceThreads * 32;
+constexpr size_t kTcSmem = 2 * (size_t)kBufBytes + (size_t)kRawDepth * kRawBytes;
 constexpr uint32_t kWaitLimit = 1u << 22;      // mbarrier polls before a wait gives up
 constexpr uint32_t kShortWait = 64;            // polls once some wait has given up
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTM, kTN);
 
-static_assert(kTcSmem <= 200 * 1024, "tile buffers exceed shared memory");
+static_assert(kTcSmem <= 220 * 1024, "tile buffers exceed shared memory");
 static_assert(kColLo + kTN <= kTmemCols, "accumulators exceed the TMEM allocation");
 
 // Accumulator a (0, 1, 2: the exact groups G_0, G_1, G_2; 3: G_3 + G_4 + G_5)
@@ -96,6 +102,49 @@ __device__ __forceinline__ void load_rows(const float *col, int64_t k, int64_t m
 #pragma unroll
     for (int e = 0; e < n; ++e) x[e] = (col && k + e < m) ? __ldg(col + k + e) : 0.0f;
   }
+}
+
+// Rows k..k+n-1 of column `col` copied to shared memory at dst, dst + ustride,
+// ... (16 bytes each): cp.async when the rows are 16-byte aligned and inside
+// the column, else plain loads (zero past m or for a missing column) stored
+// by the thread itself.
+template <int n>
+__device__ __forceinline__ void copy_rows(const float *col, int64_t k, int64_t m, int vec4, uint32_t dst,
+                                          uint32_t ustride) {
+  if (col && vec4 && k + n <= m) {
+#pragma unroll
+    for (int e = 0; e < n; e += 4)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)(e / 4) * ustride),
+                   "l"(col + k + e)
+                   : "memory");
+  } else {
+    float x[n];
+    load_rows<n>(col, k, m, 0, x);
+#pragma unroll
+    for (int e = 0; e < n; e += 4)
+      asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(dst + (uint32_t)(e / 4) * ustride), "f"(x[e]),
+                   "f"(x[e + 1]), "f"(x[e + 2]), "f"(x[e + 3])
+                   : "memory");
+  }
+}
+template <int n>
+__device__ __forceinline__ void read_rows(uint32_t src, uint32_t ustride, float *x) {
+#pragma unroll
+  for (int e = 0; e < n; e += 4)
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(x[e]), "=f"(x[e + 1]), "=f"(x[e + 2]), "=f"(x[e + 3])
+                 : "r"(src + (uint32_t)(e / 4) * ustride)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most `pending` (0, 1 or 2) of this thread's copy groups are still in flight
+__device__ __forceinline__ void cp_async_wait(int pending) {
+  if (pending >= 2)
+    asm volatile("cp.async.wait_group 2;" ::: "memory");
+  else if (pending == 1)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
@@ -240,13 +289,19 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
         kSl * kASlice + (uint32_t)(fb >> 3) * kStride + (uint32_t)(fb & 7) * 16 + (uint32_t)kb * kLead;
     const float row_un = (i0 + drow < jb.c) ? jb.colunscale[i0 + drow] : 0.0f;
 
-    // two register sets: chunk t is sliced from set t % 2 while the values of
-    // chunk t + 1 are in flight in the other set
-    float xa0[16], xb0[8], xa1[16], xb1[8];
-    auto load_chunk = [&](int64_t ch, float *xa, float *xb) {
-      const int64_t k0 = ch * kKC;
-      load_rows<16>(colA, k0 + 16 * ha, jb.m, jb.vec4, xa);
-      if (colB) load_rows<8>(colB, k0 + 8 * kb, jb.m, jb.vec4, xb);
+    // the values of chunk t are copied into ring slot t % kRawDepth, kRawDepth
+    // chunks ahead (one copy group per chunk); this thread reads back only
+    // what it copied itself
+    const uint32_t rawbase = sbase + 2 * kBufBytes + (uint32_t)tid * 16;
+    constexpr uint32_t kUnit = kSliceThreads * 16;  // between a thread's 16-byte units
+    auto issue_chunk = [&](int64_t t) {
+      if (t < nch) {
+        const int64_t k0 = (ch0 + t) * kKC;
+        const uint32_t slot = rawbase + (uint32_t)(t % kRawDepth) * kRawBytes;
+        if (colA) copy_rows<16>(colA, k0 + 16 * ha, jb.m, jb.vec4, slot, kUnit);
+        if (colB) copy_rows<8>(colB, k0 + 8 * kb, jb.m, jb.vec4, slot + kRawA, kUnit);
+      }
+      cp_async_commit();  // an empty group past the last chunk keeps the counting uniform
     };
     // columns past c slice to zero: written once into both buffers
 #pragma unroll
@@ -296,10 +351,15 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       tc::tmem_wait_st();
     };
 
-    // one chunk: slice it from (xa, xb), refill (xa, xb) with chunk t + 2,
-    // then drain what is due after chunk t - 1
-    auto step = [&](int64_t t, float *xa, float *xb) {
+    // one chunk: slice it from its ring slot, copy chunk t + kRawDepth into
+    // that slot, then drain what is due after chunk t - 1
+    auto step = [&](int64_t t) {
       const int b = (int)(t & 1);
+      cp_async_wait(kRawDepth - 1);  // chunk t's group has landed (later groups may be in flight)
+      float xa[16], xb[8];
+      const uint32_t slot = rawbase + (uint32_t)(t % kRawDepth) * kRawBytes;
+      if (colA) read_rows<16>(slot, kUnit, xa);
+      if (colB) read_rows<8>(slot + kRawA, kUnit, xb);
       if (t >= 2) wait(done_bar(b), (uint32_t)(((t - 2) >> 1) & 1));  // the MMAs of chunk t - 2 read this buffer
       const uint32_t base = sbase + (uint32_t)b * kBufBytes;
       if (colA) {
@@ -310,7 +370,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       tc::fence_proxy_async();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(full_bar(b));
-      if (t + 2 < nch) load_chunk(ch0 + t + 2, xa, xb);
+      issue_chunk(t + kRawDepth);
       if (t >= 1) {
         const uint32_t due = due_after(t - 1, nch);
         if (due) {
@@ -323,12 +383,9 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
         }
       }
     };
-    if (nch > 0) load_chunk(ch0, xa0, xb0);
-    if (nch > 1) load_chunk(ch0 + 1, xa1, xb1);
-    for (int64_t t = 0; t < nch; t += 2) {
-      step(t, xa0, xb0);
-      if (t + 1 < nch) step(t + 1, xa1, xb1);
-    }
+    for (int q = 0; q < kRawDepth; ++q) issue_chunk(q);
+    for (int64_t t = 0; t < nch; ++t) step(t);
+    cp_async_wait(0);
     if (nch > 0) {
       const int64_t t = nch - 1;
       wait(done_bar((int)(t & 1)), (uint32_t)((t >> 1) & 1));
