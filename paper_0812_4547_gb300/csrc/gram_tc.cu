@@ -233,17 +233,16 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float y) {
 // k-th due group (in group order) moves to spare k, and its drained slot
 // becomes spare k.
 struct acc_slots {
-  uint32_t g = 0u | (1u << 3) | (2u << 6) | (3u << 9);  // slot of group a in bits 3a .. 3a + 2
-  uint32_t spare = 4u | (5u << 3);                       // spare k in bits 3k .. 3k + 2
-  __device__ __forceinline__ int slot(int a) const { return (int)((g >> (3 * a)) & 7u); }
+  int g[4] = {0, 1, 2, 3};
+  int spare[2] = {4, 5};
   __device__ __forceinline__ void swap_due(uint32_t due) {
     int k = 0;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       if (!((due >> a) & 1u)) continue;
-      const uint32_t old = (g >> (3 * a)) & 7u, sp = (spare >> (3 * k)) & 7u;
-      g = (g & ~(7u << (3 * a))) | (sp << (3 * a));
-      spare = (spare & ~(7u << (3 * k))) | (old << (3 * k));
+      const int old = g[a];
+      g[a] = spare[k];
+      spare[k] = old;
       ++k;
     }
   }
@@ -372,7 +371,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
         for (int a = 0; a < 4; ++a) {
           if (!((due >> a) & 1u)) continue;
           uint32_t r[16];
-          tc::tmem_ld16(tlane + acc_col(amap.slot(a)) + (uint32_t)hh, r);
+          tc::tmem_ld16(tlane + acc_col(amap.g[a]) + (uint32_t)hh, r);
           tc::tmem_wait_ld();
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
@@ -465,7 +464,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
             const uint64_t ad = dA + (uint64_t)((p * kASlice + kk * 2 * kLead) >> 4);
             const uint64_t bd = dB + (uint64_t)(((uint32_t)(w - p) * bSl + (uint32_t)kk * 2 * kLead) >> 4);
             const bool first = (p == 0 && kk == 0 && (a < 3 || w == 3));
-            tc::mma_bf16(tbase + acc_col(amap.slot(a)), ad, bd, kIdesc, (first && ((fresh >> a) & 1u)) ? 0u : 1u);
+            tc::mma_bf16(tbase + acc_col(amap.g[a]), ad, bd, kIdesc, (first && ((fresh >> a) & 1u)) ? 0u : 1u);
           }
         }
       }
