@@ -36,10 +36,7 @@
 // accumulators and commits them to an mbarrier.  The warps meet only at
 // mbarriers: "full" (a buffer is sliced), "mma_done" (the tensor cores are
 // through a buffer) and "drained" (the due accumulators were read back), so
-// slicing of chunk t + 1 runs while the tensor cores work on chunk t.  Two
-// spare accumulators let the tensor cores go on while due ones are drained:
-// a group that is due continues in a spare, and the drained one becomes the
-// next spare.
+// slicing of chunk t + 1 runs while the tensor cores work on chunk t.
 // K-splits of one tile add their FP64 partials in a fixed order in the last
 // CTA to finish (a counter per tile, reset by that CTA).
 #include <cuda_bf16.h>
@@ -80,19 +77,10 @@ constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTM, kTN);
 static_assert(kTcSmem <= 220 * 1024, "tile buffers exceed shared memory");
 static_assert(kColLo + kTN <= kTmemCols, "accumulators exceed the TMEM allocation");
 
-// Physical accumulators: slots 0-3 at columns 0-255, the running sums at
-// 256-383, the two spare slots 4 and 5 at 384-511.
-__device__ __forceinline__ uint32_t acc_col(int slot) { return (uint32_t)(slot * kTN + (slot >= 4 ? 2 * kTN : 0)); }
-static_assert(6 * kTN + 2 * kTN <= (int)kTmemCols, "spare accumulators exceed the TMEM allocation");
-
-// Group a (0, 1, 2: the exact groups G_0, G_1, G_2; 3: G_3 + G_4 + G_5) is
-// drained after chunk t when t % drain_period(a) == drain_offset(a) (and
-// after the last chunk): never more than drain_period(a) chunks apart, and
-// (w + 1) * 32 * period * 2^14 stays within 2^23 for the exact ones.  The
-// offsets keep at most two groups due after any chunk but the last, so two
-// spare accumulators suffice.
+// Accumulator a (0, 1, 2: the exact groups G_0, G_1, G_2; 3: G_3 + G_4 + G_5)
+// is drained after every drain_period(a) chunks: (w + 1) * 32 * period *
+// 2^14 stays within 2^23 for the exact ones.
 __host__ __device__ constexpr int drain_period(int a) { return a == 0 ? 16 : 8; }
-__host__ __device__ constexpr int drain_offset(int a) { return a == 0 ? 15 : (a == 1 ? 3 : (a == 2 ? 5 : 7)); }
 __device__ __forceinline__ constexpr int acc_of(int w) { return w < 3 ? w : 3; }
 
 __device__ __forceinline__ const float *tc_col(const gram_tc_job &j, int g) {
@@ -227,38 +215,18 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float y) {
   lo = __fadd_rn(lo, e);
 }
 
-// Groups drained after chunk t (relative to the CTA's first chunk).
-// The slot map of the four groups and the two spares, updated identically by
-// the MMA warp and the draining warps at every drain event but the last: the
-// k-th due group (in group order) moves to spare k, and its drained slot
-// becomes spare k.
-struct acc_slots {
-  int g[4] = {0, 1, 2, 3};
-  int spare[2] = {4, 5};
-  __device__ __forceinline__ void swap_due(uint32_t due) {
-    int k = 0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      if (!((due >> a) & 1u)) continue;
-      const int old = g[a];
-      g[a] = spare[k];
-      spare[k] = old;
-      ++k;
-    }
-  }
-};
-
+// Accumulators drained after chunk t (relative to the CTA's first chunk).
 __device__ __forceinline__ uint32_t due_after(int64_t t, int64_t nch) {
   uint32_t due = 0;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
-    if (t + 1 == nch || (t % drain_period(a)) == drain_offset(a)) due |= 1u << a;
+    if (t + 1 == nch || ((t + 1) % drain_period(a)) == 0) due |= 1u << a;
   return due;
 }
 
 __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t local) {
   extern __shared__ __align__(128) unsigned char tc_smem[];
-  __shared__ __align__(8) uint64_t mbar[6];  // full[2], mma_done[2], drained[2] (by event parity)
+  __shared__ __align__(8) uint64_t mbar[5];  // full[2], mma_done[2], drained
   __shared__ uint32_t tmem_base_s;
   __shared__ float colun_s[kTN];
   __shared__ int last_s;  // this CTA finished the tile's last K-split
@@ -277,8 +245,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
 
   const uint32_t sbase = tc::smem_addr(tc_smem);
   const uint32_t full0 = tc::smem_addr(&mbar[0]), done0 = tc::smem_addr(&mbar[2]);
-  const uint32_t drained0 = tc::smem_addr(&mbar[4]);
-  auto drained_bar = [&](uint32_t e) { return drained0 + 8u * (e & 1u); };
+  const uint32_t drained = tc::smem_addr(&mbar[4]);
   auto full_bar = [&](int b) { return full0 + 8u * (uint32_t)b; };
   auto done_bar = [&](int b) { return done0 + 8u * (uint32_t)b; };
   if (tid == 0) {
@@ -286,8 +253,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
     tc::mbar_init(full_bar(1), kSliceThreads / 32);
     tc::mbar_init(done_bar(0), 1);
     tc::mbar_init(done_bar(1), 1);
-    tc::mbar_init(drained_bar(0), kSliceThreads / 32);
-    tc::mbar_init(drained_bar(1), kSliceThreads / 32);
+    tc::mbar_init(drained, kSliceThreads / 32);
     tc::fence_mbar_init();
     last_s = 0;
   }
@@ -359,8 +325,6 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
       tc::tmem_wait_st();
     }
     // due accumulators into the running sums, 16 of the thread's 32 columns at a time
-    acc_slots amap;    // where each group accumulates (the MMA warp keeps the same map)
-    uint32_t ev = 0;   // drain events signalled
     auto drain = [&](uint32_t due) {
 #pragma unroll 1
       for (int hh = 0; hh < 32; hh += 16) {
@@ -371,7 +335,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
         for (int a = 0; a < 4; ++a) {
           if (!((due >> a) & 1u)) continue;
           uint32_t r[16];
-          tc::tmem_ld16(tlane + acc_col(amap.g[a]) + (uint32_t)hh, r);
+          tc::tmem_ld16(tlane + (uint32_t)(a * kTN + hh), r);
           tc::tmem_wait_ld();
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
@@ -415,9 +379,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
           drain(due);
           tc::tmem_fence_before();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(drained_bar(ev));
-          amap.swap_due(due);  // chunk t - 1 is not the last: the MMAs of chunk t use the spares
-          ++ev;
+          if (lane == 0) tc::mbar_arrive(drained);
         }
       }
     };
@@ -432,19 +394,16 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
     }
   } else if (lane == 0) {
     // ---- the MMA warp (one issuing thread) ---------------------------------
-    uint32_t fresh = 0xFu;  // groups whose next MMA overwrites its slot
-    acc_slots amap;
-    uint32_t ev = 0;        // drain events passed
+    uint32_t fresh = 0xFu;  // accumulators whose next MMA overwrites
+    uint32_t events = 0;    // drain events waited for
     for (int64_t t = 0; t < nch; ++t) {
       const int b = (int)(t & 1);
       wait(full_bar(b), (uint32_t)((t >> 1) & 1));
       if (t >= 1) {
         const uint32_t due = due_after(t - 1, nch);
         if (due) {
-          // the previous event's drained slots are this event's spares
-          if (ev >= 1) wait(drained_bar(ev - 1), ((ev - 1) >> 1) & 1u);
-          amap.swap_due(due);
-          ++ev;
+          wait(drained, events & 1u);
+          ++events;
           fresh |= due;
         }
       }
@@ -464,7 +423,7 @@ __device__ __forceinline__ void gram_tc_block(const gram_tc_job &jb, int64_t loc
             const uint64_t ad = dA + (uint64_t)((p * kASlice + kk * 2 * kLead) >> 4);
             const uint64_t bd = dB + (uint64_t)(((uint32_t)(w - p) * bSl + (uint32_t)kk * 2 * kLead) >> 4);
             const bool first = (p == 0 && kk == 0 && (a < 3 || w == 3));
-            tc::mma_bf16(tbase + acc_col(amap.g[a]), ad, bd, kIdesc, (first && ((fresh >> a) & 1u)) ? 0u : 1u);
+            tc::mma_bf16(tbase + (uint32_t)(a * kTN), ad, bd, kIdesc, (first && ((fresh >> a) & 1u)) ? 0u : 1u);
           }
         }
       }
