@@ -2031,6 +2031,26 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
   char *h = (char *)ctx->pinned;
   memcpy(h, sj.data(), (size_t)nb * sizeof(srht_job));
   size_t off = align_up((size_t)nb * sizeof(srht_job), 256);
+  // plan blocks start with the instances of most rows (a plan block's work
+  // grows with r): the last blocks to start are short ones
+  {
+    std::vector<int> order((size_t)nb);
+    for (int t = 0; t < nb; ++t) order[(size_t)t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pj[(size_t)a].r > pj[(size_t)b].r; });
+    std::vector<plan_job> pj2((size_t)nb);
+    samp_tot = 0;
+    plan_tot = 0;
+    for (int k = 0; k < nb; ++k) {
+      pj2[(size_t)k] = pj[(size_t)order[(size_t)k]];
+      first_s[(size_t)k] = samp_tot;
+      first_p[(size_t)k] = plan_tot;
+      samp_tot += sample_blocks(pj2[(size_t)k].r);
+      plan_tot += plan_blocks(pj2[(size_t)k]);
+    }
+    first_s[(size_t)nb] = samp_tot;
+    first_p[(size_t)nb] = plan_tot;
+    pj.swap(pj2);
+  }
   memcpy(h + off, pj.data(), (size_t)nb * sizeof(plan_job));
   const size_t off_p = off;
   off += align_up((size_t)nb * sizeof(plan_job), 256);

@@ -1240,6 +1240,15 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   int64_t *first_col = (int64_t *)(h_tables + tab_jobs);
   int64_t *first_cta = (int64_t *)(h_tables + tab_jobs + tab_first);
   lh_job *jobs = (lh_job *)(h_tables + tab_jobs + 2 * tab_first);
+  // Lawson-Hanson blocks start in order of decreasing d (longest first: the
+  // blocks of the last wave are the short ones, so the launch ends sooner)
+  std::vector<int64_t> lh_pos((size_t)count);
+  {
+    std::vector<int64_t> order((size_t)count);
+    for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return probs[a].d > probs[b].d; });
+    for (int64_t k = 0; k < count; ++k) lh_pos[(size_t)order[(size_t)k]] = k;
+  }
   int64_t ctas = 0, cols = 0;
   for (int64_t i = 0; i < count; ++i) {
     const rnnls_problem &pb = probs[i];
@@ -1256,7 +1265,7 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
     cols += q.c;
     first_cta[i] = ctas;
     ctas += (int64_t)q.tiles * q.splits;
-    lh_job &jb = jobs[i];
+    lh_job &jb = jobs[lh_pos[(size_t)i]];
     jb.Qd = Qd;
     jb.Qhi = Qhi;
     jb.Qlo = Qlo;
