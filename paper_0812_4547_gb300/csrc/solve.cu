@@ -1281,6 +1281,23 @@ int solve_batched(rnnls_ctx *ctx, const rnnls_problem *probs, int64_t count) {
   }
   first_col[count] = cols;
   first_cta[count] = ctas;
+  {
+    // the Gram CTAs of the problems with most rows (the longest K-splits)
+    // start first; a job's CTAs and columns stay contiguous
+    std::vector<int64_t> order((size_t)count);
+    for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return probs[a].r > probs[b].r; });
+    std::vector<gram_tc_job> g2((size_t)count);
+    for (int64_t k = 0; k < count; ++k) g2[(size_t)k] = gj[order[(size_t)k]];
+    int64_t c2 = 0, t2 = 0;
+    for (int64_t k = 0; k < count; ++k) {
+      gj[k] = g2[(size_t)k];
+      first_col[k] = c2;
+      first_cta[k] = t2;
+      c2 += gj[k].c;
+      t2 += (int64_t)gj[k].tiles * gj[k].splits;
+    }
+  }
   cudaStream_t s = ctx->stream;
   // tables staged through the context's pinned buffer (ensure_pinned waited
   // for the previous call's copy out of it)
