@@ -1493,15 +1493,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t k0 = kg * J0.rpg;
         const int64_t nk = min(J0.rpg, (int64_t)J0.r - k0);
         float *dst = ((col < d) ? J0.SA + (int64_t)col * J0.ldsa : J0.SB) + k0;
+        // the row indices of 32 rows at a time, the next 32 loaded while
+        // these are placed (their latency is then paid once per pass)
+        const int32_t *kk_src = J0.pkk + (size_t)kg * slots * kThreads + tid;
+        auto load_kk = [&](int s32, int32_t *kk) {
+          const int n8 = min(4, (slots - s32) >> 3);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) kk[e] = (e < 8 * n8) ? __ldg(kk_src + (size_t)(s32 + e) * kThreads) : -1;
+        };
         for (int64_t h0 = 0; h0 < nk; h0 += span) {
           __syncthreads();  // the combine (or the previous copy) is done with the buffer
+          int32_t kk[32], kn[32];
+          load_kk(0, kk);
           for (int s32 = 0; s32 < slots; s32 += 32) {
             const int n8 = min(4, (slots - s32) >> 3);
-            int32_t kk[32];
             uint32_t acc[32];
-#pragma unroll
-            for (int e = 0; e < 32; ++e)
-              kk[e] = (e < 8 * n8) ? J0.pkk[((size_t)kg * slots + s32 + e) * kThreads + tid] : -1;
+            if (s32 + 32 < slots) load_kk(s32 + 32, kn);
 #pragma unroll
             for (int b8 = 0; b8 < 4; ++b8)
               if (b8 < n8) tmem_ld8(t_acc + s32 + 8 * b8, acc + 8 * b8);
@@ -1513,6 +1520,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               (o < kStageFloats ? ost : ost2)[o & (kStageFloats - 1)] =
                   poisoned ? __int_as_float(0x7fc00000) : J0.scale * __uint_as_float(acc[e]);
             }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) kk[e] = kn[e];
           }
           __syncthreads();
           const int64_t cnt = min(span, nk - h0);
