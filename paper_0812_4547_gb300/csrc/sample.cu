@@ -191,36 +191,42 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v) {
   return v;
 }
 
-// One block per (plan group g, bank q), plus the sign-table blocks.  Every
-// plan block reads the rows of its group (drawn before), counts all 32
-// banks itself and writes only what belongs to bank q: its rows with rank
-// below 8 * slots (lane q), the spilled ones (into other lanes' free
-// positions, in bank order) and lane q's free positions no spilled row
-// takes.  No block reads another block's output.
+// One block per plan group g, plus the sign-table blocks.  The block ranks
+// the group's rows within their banks in one pass: 1024 rows at a time (one
+// per thread), a row's rank is the count of its bank's rows in earlier
+// passes, in earlier warps of this pass (a per-warp bank histogram, scanned
+// over the warps) and in earlier lanes of its warp (__match_any_sync).  Rows
+// with rank below 8 * slots go to lane q of successive (warp, slot) pairs;
+// the others (a bank's overflow) are kept per bank in shared memory and,
+// once every bank's count is known, take the free positions of the other
+// lanes in bank order; free positions left over become empty entries.  If
+// a bank overflows by more than the kept number, a second pass places the
+// rest.  Which position a row takes does not change any sum (each row adds
+// its steps in step order wherever it sits); only the shared-memory banks
+// its gathers hit.
 // gen_L > 0: the block draws the iid rows itself (draw k = word k of stream
-// 2 shifted right by 64 - gen_L, as sample_iid_kernel does) and the bank-0
-// block of each plan group writes them to idx; gen_L = 0: rows read from idx.
+// 2 shifted right by 64 - gen_L, as sample_iid_kernel does) and writes them
+// to idx; gen_L = 0: rows read from idx.
+constexpr int kPlanWarps = kPlanThreads / 32;
+constexpr uint32_t kSpillPerBank = 96;  // overflow rows kept per bank
+
 __device__ __forceinline__ void plan_block(int blk, int32_t *__restrict__ idx, int64_t r,
                                            const int64_t *__restrict__ d_count, uint32_t *__restrict__ plan_pk,
                                            int32_t *__restrict__ plan_k, int slots, int64_t rows_per_group,
                                            int kgroups, uint64_t seed, uint64_t inst,
                                            uint64_t *__restrict__ sign_table, int64_t sign_words,
                                            int64_t sign_block0, int gen_L) {
+  __shared__ uint32_t wcnt[kPlanWarps][33];  // this pass: rows of bank b in warp w (padded)
+  __shared__ uint32_t base[32];              // rows of bank b in earlier passes
   __shared__ uint32_t cnt[32], ov_start[32], free_start[32];
-  __shared__ uint32_t wsum[kPlanThreads / 32];
-  __shared__ uint32_t whist[kPlanThreads / 32][32];  // per-warp bank counts (no contention)
-  __shared__ uint32_t round_total, total_ov;
-  // this bank's spilled rows, kept from the first scan (a second scan only
-  // if more than kSpillKeep spill)
-  constexpr uint32_t kSpillKeep = 768;
-  __shared__ uint32_t spill_row[kSpillKeep];
-  __shared__ int32_t spill_k[kSpillKeep];
+  __shared__ uint32_t total_ov, redo;
+  __shared__ uint32_t spill_row[32][kSpillPerBank];
+  __shared__ int32_t spill_k[32][kSpillPerBank];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nplan = 32 * kgroups;
-  if (blk >= nplan) {
+  if (blk >= kgroups) {
     // sign words of D: word W (counted from the table's first chunk) is word
     // W % 4 of Philox block sign_block0 + W / 4 of stream 0
-    const int64_t pb = (int64_t)(blk - nplan) * kPlanThreads + tid;
+    const int64_t pb = (int64_t)(blk - kgroups) * kPlanThreads + tid;
     if (4 * pb < sign_words) {
       const u64x4 u = philox4x64_10((uint64_t)(sign_block0 + pb), kStreamSigns, seed, inst);
 #pragma unroll
@@ -228,8 +234,7 @@ __device__ __forceinline__ void plan_block(int blk, int32_t *__restrict__ idx, i
     }
     return;
   }
-  const int g = blk >> 5;
-  const uint32_t q = blk & 31;
+  const int g = blk;
   int64_t rr = r;
   if (d_count) rr = min(r, *d_count);
   const int64_t k0 = (int64_t)g * rows_per_group;
@@ -237,125 +242,124 @@ __device__ __forceinline__ void plan_block(int blk, int32_t *__restrict__ idx, i
   uint32_t *pk_out = plan_pk + (size_t)g * slots * kThreads;
   int32_t *k_out = plan_k + (size_t)g * slots * kThreads;
   const uint32_t cap = 8u * (uint32_t)slots;  // rows per bank without spilling
-  whist[warp][lane] = 0;
-  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  if (tid < 32) base[tid] = 0;
 
-  auto place = [&](uint32_t pos, uint32_t ln, uint32_t row, int64_t k) {
+  auto entry = [&](uint32_t pos, uint32_t ln) { return (size_t)(pos >> 3) * kThreads + (pos & 7u) * 32u + ln; };
+  auto encode = [&](uint32_t row) {
     const uint32_t l = row & (kM - 1), h = row >> kLogM;
-    const size_t e = (size_t)(pos >> 3) * kThreads + (pos & 7u) * 32u + ln;
-    pk_out[e] = (swz128(l) << 2) | ((h & 3u) << 14) | ((h >> 2) << 16) | ((h & 1u) << 31) | (((h >> 1) & 1u) << 30);
-    k_out[e] = (int32_t)k;
+    return (swz128(l) << 2) | ((h & 3u) << 14) | ((h >> 2) << 16) | ((h & 1u) << 31) | (((h >> 1) & 1u) << 30);
   };
-  // rows k = t0 + 4 tid .. + 3 of this round, in draw order (thread, then e)
-  auto scan = [&](bool count_all, bool place_spilled) {
-    uint32_t qbase = 0;
-    for (int64_t t0 = k0; t0 < k1; t0 += 4 * kPlanThreads) {
-      const int64_t kb = t0 + 4 * tid;
-      uint32_t rows[4], bank[4];
-      if (gen_L > 0) {
-        // kb is a multiple of 4: one Philox block gives draws kb .. kb + 3
-        const u64x4 u = philox4x64_10((uint64_t)(kb >> 2), kStreamIid, seed, inst);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) rows[e] = (kb + e < k1) ? (uint32_t)(u.w[e] >> (64 - gen_L)) : 0u;
-        if (count_all && q == 0) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (kb + e < k1) idx[kb + e] = (int32_t)rows[e];
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) rows[e] = (kb + e < k1) ? (uint32_t)idx[kb + e] : 0u;
-      }
-      uint32_t mine = 0;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const bool valid = kb + e < k1;
-        bank[e] = valid ? (swz128(rows[e] & (kM - 1)) & 31u) : 32u;
-        mine += (bank[e] == q) ? 1u : 0u;
-        if (count_all) {
-          const uint32_t same = __match_any_sync(0xffffffffu, bank[e]);
-          if (valid && (same & ((1u << lane) - 1u)) == 0) whist[warp][bank[e]] += __popc(same);
-        }
-      }
-      // ranks of bank-q rows: exclusive scan of `mine` over the block
-      const uint32_t incl = warp_inclusive_sum(mine);
-      if (lane == 31) wsum[warp] = incl;
+  // the row of draw k (k < k1), drawing or reading it
+  auto row_of = [&](int64_t k, bool write_idx) -> uint32_t {
+    if (gen_L > 0) {
+      const u64x4 u = philox4x64_10((uint64_t)(k >> 2), kStreamIid, seed, inst);
+      const uint32_t v = (uint32_t)(u.w[k & 3] >> (64 - gen_L));
+      if (write_idx) idx[k] = (int32_t)v;
+      return v;
+    }
+    return (uint32_t)idx[k];
+  };
+  // One pass: rows k0 + 1024 i + tid; rank each within its bank.  place = 0:
+  // place ranks below cap and keep the overflow; place = 1 (the rare second
+  // pass): place only overflow rows the first pass could not keep.
+  auto pass = [&](int place) {
+    for (int64_t t0 = k0; t0 < k1; t0 += kPlanThreads) {
+      const int64_t k = t0 + tid;
+      const bool valid = k < k1;
+      const uint32_t row = valid ? row_of(k, place == 0) : 0u;
+      const uint32_t bank = valid ? (swz128(row & (kM - 1)) & 31u) : 32u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, bank);
+      for (int i = tid; i < kPlanWarps * 33; i += kPlanThreads) (&wcnt[0][0])[i] = 0;
       __syncthreads();
-      if (warp == 0) {
-        const uint32_t v = (lane < kPlanThreads / 32) ? wsum[lane] : 0u;
+      if (valid && (peers & lt) == 0) wcnt[warp][bank] = __popc(peers);
+      __syncthreads();
+      // warp b scans bank b's counts over the warps
+      if (warp < 32) {
+        const uint32_t v = (lane < kPlanWarps) ? wcnt[lane][warp] : 0u;
         const uint32_t vi = warp_inclusive_sum(v);
-        if (lane < kPlanThreads / 32) wsum[lane] = vi - v;
-        if (lane == 31) round_total = vi;
+        if (lane < kPlanWarps) wcnt[lane][warp] = base[warp] + vi - v;  // exclusive offset, earlier passes included
+        __syncwarp();
+        if (lane == 31) base[warp] += vi;
       }
       __syncthreads();
-      uint32_t rank = qbase + wsum[warp] + incl - mine;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (bank[e] != q) continue;
+      if (valid) {
+        const uint32_t rank = wcnt[warp][bank] + __popc(peers & lt);
         if (rank < cap) {
-          if (!place_spilled) place(rank, q, rows[e], kb + e);
-        } else if (!place_spilled) {
-          if (rank - cap < kSpillKeep) {
-            spill_row[rank - cap] = rows[e];
-            spill_k[rank - cap] = (int32_t)(kb + e);
+          if (place == 0) {
+            const size_t e = entry(rank, bank);
+            pk_out[e] = encode(row);
+            k_out[e] = (int32_t)k;
           }
         } else {
-          // spilled row: the e-th overall spilled row takes the e-th free position (bank order)
-          const uint32_t ev = ov_start[q] + (rank - cap);
-          for (uint32_t b2 = 0; b2 < 32; ++b2) {
-            const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
-            if (ev >= free_start[b2] && ev < free_start[b2] + f) place(cnt[b2] + (ev - free_start[b2]), b2, rows[e], kb + e);
+          const uint32_t o = rank - cap;
+          if (place == 0) {
+            if (o < kSpillPerBank) {
+              spill_row[bank][o] = row;
+              spill_k[bank][o] = (int32_t)k;
+            }
+          } else if (o >= kSpillPerBank) {
+            // the e-th overflow row overall takes the e-th free position (bank order)
+            const uint32_t ev = ov_start[bank] + o;
+            for (uint32_t b2 = 0; b2 < 32; ++b2) {
+              const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
+              if (ev >= free_start[b2] && ev < free_start[b2] + f) {
+                const size_t e = entry(cnt[b2] + (ev - free_start[b2]), b2);
+                pk_out[e] = encode(row);
+                k_out[e] = (int32_t)k;
+              }
+            }
           }
         }
-        ++rank;
       }
-      qbase += round_total;
-      __syncthreads();  // wsum and round_total are reused
+      __syncthreads();  // wcnt is reused
     }
   };
-  scan(true, false);
-  if (tid < 32) {
-    uint32_t c = 0;
-    for (int w = 0; w < kPlanThreads / 32; ++w) c += whist[w][tid];
-    cnt[tid] = c;
-  }
+  pass(0);
+  if (tid < 32) cnt[tid] = base[tid];
   __syncthreads();
   if (tid == 0) {
-    uint32_t ov = 0, fr = 0;
+    uint32_t ov = 0, fr = 0, big = 0;
     for (int b2 = 0; b2 < 32; ++b2) {
       ov_start[b2] = ov;
       free_start[b2] = fr;
       ov += cnt[b2] > cap ? cnt[b2] - cap : 0u;
       fr += cnt[b2] < cap ? cap - cnt[b2] : 0u;
+      big |= (cnt[b2] > cap + kSpillPerBank) ? 1u : 0u;
     }
     total_ov = ov;
+    redo = big;
   }
   __syncthreads();
-  // lane q's free positions that no spilled row takes: empty entries (read a
-  // word of bank q, write nothing)
-  if (cnt[q] < cap) {
-    const uint32_t nfree = cap - cnt[q];
-    for (uint32_t f = tid; f < nfree; f += kPlanThreads) {
-      if (free_start[q] + f < total_ov) continue;
-      const uint32_t pos = cnt[q] + f;
-      const size_t e = (size_t)(pos >> 3) * kThreads + (pos & 7u) * 32u + q;
-      pk_out[e] = q << 2;
-      k_out[e] = -1;
+  // kept overflow rows into free positions, in bank order
+  for (uint32_t i = tid; i < 32 * kSpillPerBank; i += kPlanThreads) {
+    const uint32_t bank = i / kSpillPerBank, o = i % kSpillPerBank;
+    if (cnt[bank] <= cap || o >= cnt[bank] - cap) continue;
+    const uint32_t ev = ov_start[bank] + o;
+    for (uint32_t b2 = 0; b2 < 32; ++b2) {
+      const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
+      if (ev >= free_start[b2] && ev < free_start[b2] + f) {
+        const size_t e = entry(cnt[b2] + (ev - free_start[b2]), b2);
+        pk_out[e] = encode(spill_row[bank][o]);
+        k_out[e] = spill_k[bank][o];
+      }
     }
   }
-  if (cnt[q] > cap) {
-    const uint32_t nsp = cnt[q] - cap;
-    if (nsp <= kSpillKeep) {
-      for (uint32_t t = tid; t < nsp; t += kPlanThreads) {
-        const uint32_t ev = ov_start[q] + t;
-        for (uint32_t b2 = 0; b2 < 32; ++b2) {
-          const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
-          if (ev >= free_start[b2] && ev < free_start[b2] + f) place(cnt[b2] + (ev - free_start[b2]), b2, spill_row[t], spill_k[t]);
-        }
-      }
-    } else {
-      scan(false, true);
-    }
+  // free positions no overflow row takes: empty entries (read a word of the
+  // lane's own bank, write nothing)
+  for (uint32_t i = tid; i < 32 * cap; i += kPlanThreads) {
+    const uint32_t q = i / cap, pos = i % cap;
+    if (pos < cnt[q]) continue;
+    if (free_start[q] + (pos - cnt[q]) < total_ov) continue;
+    const size_t e = entry(pos, q);
+    pk_out[e] = q << 2;
+    k_out[e] = -1;
+  }
+  if (redo) {
+    __syncthreads();
+    if (tid < 32) base[tid] = 0;
+    __syncthreads();
+    pass(1);
   }
 }
 
@@ -413,7 +417,7 @@ __global__ void __launch_bounds__(kPlanThreads) build_plan_batched_kernel(const 
 
 int64_t sample_blocks(int64_t r) { return ((r + 3) / 4 + 255) / 256; }
 int64_t plan_blocks(const plan_job &j) {
-  return 32 * (int64_t)j.kgroups + (j.sign_words / 4 + kPlanThreads - 1) / kPlanThreads;
+  return (int64_t)j.kgroups + (j.sign_words / 4 + kPlanThreads - 1) / kPlanThreads;
 }
 
 int launch_plan_batched(cudaStream_t s, const plan_job *d_jobs, const int64_t *d_first_sample,
@@ -435,7 +439,7 @@ int launch_build_plan(cudaStream_t s, int32_t *idx, int64_t r, const int64_t *d_
     return RNNLS_EUNSUPPORTED;
   if (!sign_table) sign_words = 0;
   const int64_t sign_blocks = (sign_words / 4 + kPlanThreads - 1) / kPlanThreads;
-  build_plan_kernel<<<(unsigned)(32 * plan.kgroups + sign_blocks), kPlanThreads, 0, s>>>(
+  build_plan_kernel<<<(unsigned)(plan.kgroups + sign_blocks), kPlanThreads, 0, s>>>(
       idx, r, d_count, plan.pk, plan.k, plan.slots, plan.rows_per_group, plan.kgroups, seed, inst, sign_table,
       sign_words, sign_block0, gen_L);
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
