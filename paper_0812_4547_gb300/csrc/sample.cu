@@ -194,8 +194,8 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v) {
 // One block per plan group g, plus the sign-table blocks.  The block ranks
 // the group's rows within their banks in one pass: 1024 rows at a time (one
 // per thread), a row's rank is the count of its bank's rows in earlier
-// passes, in earlier warps of this pass (a per-warp bank histogram, scanned
-// over the warps) and in earlier lanes of its warp (__match_any_sync).  Rows
+// sub-passes, in earlier warps of this one (a per-warp bank histogram,
+// scanned over the warps) and in earlier lanes of its warp (__match_any_sync).  Rows
 // with rank below 8 * slots go to lane q of successive (warp, slot) pairs;
 // the others (a bank's overflow) are kept per bank in shared memory and,
 // once every bank's count is known, take the free positions of the other
@@ -204,9 +204,9 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v) {
 // rest.  Which position a row takes does not change any sum (each row adds
 // its steps in step order wherever it sits); only the shared-memory banks
 // its gathers hit.
-// gen_L > 0: the block draws the iid rows itself (draw k = word k of stream
-// 2 shifted right by 64 - gen_L, as sample_iid_kernel does) and writes them
-// to idx; gen_L = 0: rows read from idx.
+// gen_L > 0: the block draws the iid rows itself (draw k = word k % 4 of
+// Philox block k / 4 of stream 2, shifted right by 64 - gen_L, as
+// sample_iid_kernel does) and writes them to idx; gen_L = 0: rows read from idx.
 constexpr int kPlanWarps = kPlanThreads / 32;
 constexpr uint32_t kSpillPerBank = 96;  // overflow rows kept per bank
 
@@ -250,69 +250,79 @@ __device__ __forceinline__ void plan_block(int blk, int32_t *__restrict__ idx, i
     const uint32_t l = row & (kM - 1), h = row >> kLogM;
     return (swz128(l) << 2) | ((h & 3u) << 14) | ((h >> 2) << 16) | ((h & 1u) << 31) | (((h >> 1) & 1u) << 30);
   };
-  // the row of draw k (k < k1), drawing or reading it
-  auto row_of = [&](int64_t k, bool write_idx) -> uint32_t {
-    if (gen_L > 0) {
-      const u64x4 u = philox4x64_10((uint64_t)(k >> 2), kStreamIid, seed, inst);
-      const uint32_t v = (uint32_t)(u.w[k & 3] >> (64 - gen_L));
-      if (write_idx) idx[k] = (int32_t)v;
-      return v;
-    }
-    return (uint32_t)idx[k];
-  };
-  // One pass: rows k0 + 1024 i + tid; rank each within its bank.  place = 0:
-  // place ranks below cap and keep the overflow; place = 1 (the rare second
-  // pass): place only overflow rows the first pass could not keep.
+  // One pass over the group's rows, 4096 at a time (draws t0 + 4 tid + e, one
+  // Philox block per thread), ranked in sub-passes e = 0..3 of 1024 rows each:
+  // a row's rank within its bank counts the bank's rows of earlier sub-passes,
+  // of earlier warps of its sub-pass and of earlier lanes of its warp.
+  // place = 0: place ranks below cap and keep the overflow; place = 1 (the
+  // rare second pass): place only overflow rows the first pass could not keep.
   auto pass = [&](int place) {
-    for (int64_t t0 = k0; t0 < k1; t0 += kPlanThreads) {
-      const int64_t k = t0 + tid;
-      const bool valid = k < k1;
-      const uint32_t row = valid ? row_of(k, place == 0) : 0u;
-      const uint32_t bank = valid ? (swz128(row & (kM - 1)) & 31u) : 32u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, bank);
-      for (int i = tid; i < kPlanWarps * 33; i += kPlanThreads) (&wcnt[0][0])[i] = 0;
-      __syncthreads();
-      if (valid && (peers & lt) == 0) wcnt[warp][bank] = __popc(peers);
-      __syncthreads();
-      // warp b scans bank b's counts over the warps
-      if (warp < 32) {
-        const uint32_t v = (lane < kPlanWarps) ? wcnt[lane][warp] : 0u;
-        const uint32_t vi = warp_inclusive_sum(v);
-        if (lane < kPlanWarps) wcnt[lane][warp] = base[warp] + vi - v;  // exclusive offset, earlier passes included
-        __syncwarp();
-        if (lane == 31) base[warp] += vi;
+    for (int64_t t0 = k0; t0 < k1; t0 += 4 * kPlanThreads) {
+      const int64_t kb = t0 + 4 * tid;
+      uint32_t rows[4];
+      if (gen_L > 0) {
+        // kb is a multiple of 4: one Philox block gives draws kb .. kb + 3
+        const u64x4 u = philox4x64_10((uint64_t)(kb >> 2), kStreamIid, seed, inst);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          rows[e] = (uint32_t)(u.w[e] >> (64 - gen_L));
+          if (place == 0 && kb + e < k1) idx[kb + e] = (int32_t)rows[e];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) rows[e] = (kb + e < k1) ? (uint32_t)idx[kb + e] : 0u;
       }
-      __syncthreads();
-      if (valid) {
-        const uint32_t rank = wcnt[warp][bank] + __popc(peers & lt);
-        if (rank < cap) {
-          if (place == 0) {
-            const size_t e = entry(rank, bank);
-            pk_out[e] = encode(row);
-            k_out[e] = (int32_t)k;
-          }
-        } else {
-          const uint32_t o = rank - cap;
-          if (place == 0) {
-            if (o < kSpillPerBank) {
-              spill_row[bank][o] = row;
-              spill_k[bank][o] = (int32_t)k;
+#pragma unroll 1
+      for (int e = 0; e < 4; ++e) {
+        const int64_t k = kb + e;
+        const bool valid = k < k1;
+        const uint32_t row = rows[e];
+        const uint32_t bank = valid ? (swz128(row & (kM - 1)) & 31u) : 32u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, bank);
+        for (int i = tid; i < kPlanWarps * 33; i += kPlanThreads) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        if (valid && (peers & lt) == 0) wcnt[warp][bank] = __popc(peers);
+        __syncthreads();
+        // warp b scans bank b's counts over the warps
+        {
+          const uint32_t v = (lane < kPlanWarps) ? wcnt[lane][warp] : 0u;
+          const uint32_t vi = warp_inclusive_sum(v);
+          if (lane < kPlanWarps) wcnt[lane][warp] = base[warp] + vi - v;  // exclusive, earlier sub-passes included
+          __syncwarp();
+          if (lane == 31) base[warp] += vi;
+        }
+        __syncthreads();
+        if (valid) {
+          const uint32_t rank = wcnt[warp][bank] + __popc(peers & lt);
+          if (rank < cap) {
+            if (place == 0) {
+              const size_t en = entry(rank, bank);
+              pk_out[en] = encode(row);
+              k_out[en] = (int32_t)k;
             }
-          } else if (o >= kSpillPerBank) {
-            // the e-th overflow row overall takes the e-th free position (bank order)
-            const uint32_t ev = ov_start[bank] + o;
-            for (uint32_t b2 = 0; b2 < 32; ++b2) {
-              const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
-              if (ev >= free_start[b2] && ev < free_start[b2] + f) {
-                const size_t e = entry(cnt[b2] + (ev - free_start[b2]), b2);
-                pk_out[e] = encode(row);
-                k_out[e] = (int32_t)k;
+          } else {
+            const uint32_t o = rank - cap;
+            if (place == 0) {
+              if (o < kSpillPerBank) {
+                spill_row[bank][o] = row;
+                spill_k[bank][o] = (int32_t)k;
+              }
+            } else if (o >= kSpillPerBank) {
+              // the e-th overflow row overall takes the e-th free position (bank order)
+              const uint32_t ev = ov_start[bank] + o;
+              for (uint32_t b2 = 0; b2 < 32; ++b2) {
+                const uint32_t f = cnt[b2] < cap ? cap - cnt[b2] : 0u;
+                if (ev >= free_start[b2] && ev < free_start[b2] + f) {
+                  const size_t en = entry(cnt[b2] + (ev - free_start[b2]), b2);
+                  pk_out[en] = encode(row);
+                  k_out[en] = (int32_t)k;
+                }
               }
             }
           }
         }
+        __syncthreads();  // wcnt is reused
       }
-      __syncthreads();  // wcnt is reused
     }
   };
   pass(0);
