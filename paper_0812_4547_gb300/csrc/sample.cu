@@ -216,7 +216,7 @@ __device__ __forceinline__ void plan_block(int blk, int32_t *__restrict__ idx, i
                                            int kgroups, uint64_t seed, uint64_t inst,
                                            uint64_t *__restrict__ sign_table, int64_t sign_words,
                                            int64_t sign_block0, int gen_L) {
-  __shared__ uint32_t wcnt[kPlanWarps][33];  // this pass: rows of bank b in warp w (padded)
+  __shared__ uint32_t wcnt[2][kPlanWarps][33];  // per sub-pass (alternating): rows of bank b in warp w
   __shared__ uint32_t base[32];              // rows of bank b in earlier passes
   __shared__ uint32_t cnt[32], ov_start[32], free_start[32];
   __shared__ uint32_t total_ov, redo;
@@ -244,6 +244,7 @@ __device__ __forceinline__ void plan_block(int blk, int32_t *__restrict__ idx, i
   const uint32_t cap = 8u * (uint32_t)slots;  // rows per bank without spilling
   const uint32_t lt = (1u << lane) - 1u;
   if (tid < 32) base[tid] = 0;
+  uint32_t sub = 0;  // sub-passes done (selects the count table)
 
   auto entry = [&](uint32_t pos, uint32_t ln) { return (size_t)(pos >> 3) * kThreads + (pos & 7u) * 32u + ln; };
   auto encode = [&](uint32_t row) {
@@ -279,21 +280,29 @@ __device__ __forceinline__ void plan_block(int blk, int32_t *__restrict__ idx, i
         const uint32_t row = rows[e];
         const uint32_t bank = valid ? (swz128(row & (kM - 1)) & 31u) : 32u;
         const uint32_t peers = __match_any_sync(0xffffffffu, bank);
-        for (int i = tid; i < kPlanWarps * 33; i += kPlanThreads) (&wcnt[0][0])[i] = 0;
-        __syncthreads();
-        if (valid && (peers & lt) == 0) wcnt[warp][bank] = __popc(peers);
+        // lane b counts the warp's rows of bank b from five bit-slice ballots
+        uint32_t same = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const uint32_t bj = __ballot_sync(0xffffffffu, (bank >> j) & 1u);
+          same &= ((lane >> j) & 1) ? bj : ~bj;
+        }
+        // two tables in turn: the one written here was last read two sub-passes ago
+        uint32_t(&wc)[kPlanWarps][33] = wcnt[sub & 1];
+        ++sub;
+        wc[warp][lane] = __popc(same);
         __syncthreads();
         // warp b scans bank b's counts over the warps
         {
-          const uint32_t v = (lane < kPlanWarps) ? wcnt[lane][warp] : 0u;
+          const uint32_t v = (lane < kPlanWarps) ? wc[lane][warp] : 0u;
           const uint32_t vi = warp_inclusive_sum(v);
-          if (lane < kPlanWarps) wcnt[lane][warp] = base[warp] + vi - v;  // exclusive, earlier sub-passes included
+          if (lane < kPlanWarps) wc[lane][warp] = base[warp] + vi - v;  // exclusive, earlier sub-passes included
           __syncwarp();
           if (lane == 31) base[warp] += vi;
         }
         __syncthreads();
         if (valid) {
-          const uint32_t rank = wcnt[warp][bank] + __popc(peers & lt);
+          const uint32_t rank = wc[warp][bank] + __popc(peers & lt);
           if (rank < cap) {
             if (place == 0) {
               const size_t en = entry(rank, bank);
@@ -321,9 +330,9 @@ __device__ __forceinline__ void plan_block(int blk, int32_t *__restrict__ idx, i
             }
           }
         }
-        __syncthreads();  // wcnt is reused
       }
     }
+    __syncthreads();  // the last sub-pass's ranks are read
   };
   pass(0);
   if (tid < 32) cnt[tid] = base[tid];
