@@ -146,7 +146,7 @@ typedef struct rnnls_tuning {
   int32_t batch_step_cost;
   int32_t lh_warp_max_d;  /* Lawson-Hanson problems with d up to this run as one-warp
                              blocks, larger ones as 256-thread blocks (0: none) */
-  int32_t lh_wide_min_d;  /* ... and from this d on as 512-thread blocks (0: 129) */
+  int32_t reserved;       /* zero */
 } rnnls_tuning;
 
 /* Create a context on CUDA device `device` that enqueues on `stream`

@@ -62,7 +62,7 @@ class rnnls_tuning(ctypes.Structure):
         ("batch_gram_chunks", ctypes.c_int32),
         ("batch_step_cost", ctypes.c_int32),
         ("lh_warp_max_d", ctypes.c_int32),
-        ("lh_wide_min_d", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -32,13 +32,12 @@ CANDIDATES = {
     "batch_gram_chunks": [0, 32, 64, 256],
     "batch_step_cost": [0, 60, 180, 300],
     "lh_warp_max_d": [0, 32, 64],
-    "lh_wide_min_d": [0, 65, 1025],
 }
 
 #: the knobs that act on each kind of workload
 KNOBS_FOR = {
-    "single": ["full_step_min_slots", "gram_min_chunks", "gram_max_splits", "lh_warp_max_d", "lh_wide_min_d"],
-    "batched": ["full_step_min_slots", "batch_step_cost", "batch_gram_chunks", "lh_warp_max_d", "lh_wide_min_d"],
+    "single": ["full_step_min_slots", "gram_min_chunks", "gram_max_splits", "lh_warp_max_d"],
+    "batched": ["full_step_min_slots", "batch_step_cost", "batch_gram_chunks", "lh_warp_max_d"],
 }
 
 

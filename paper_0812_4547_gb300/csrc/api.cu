@@ -315,7 +315,7 @@ int rnnls_set_tuning(rnnls_ctx *ctx, const rnnls_tuning *t) {
   if (t->sketch_sms < 0 || !in(t->full_step_min_slots, 48, 1024) || !in(t->gram_min_chunks, 1, 65536) ||
       !in(t->gram_max_splits, 1, 1024) || !in(t->batch_gram_chunks, 1, 65536) ||
       !in(t->batch_step_cost, 1, 100000) || !in(t->lh_warp_max_d, 1, 1024) ||
-      !in(t->lh_wide_min_d, 1, 1025))
+      t->reserved != 0)
     return RNNLS_EINVAL;
   ctx->tune = *t;
   ctx->sketch_sms = t->sketch_sms;

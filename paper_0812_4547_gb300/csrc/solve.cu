@@ -32,8 +32,6 @@ constexpr int kGT = 32;         // Gram tile
 #define RNNLS_LH_THREADS 256
 #endif
 constexpr int kLHThreads = RNNLS_LH_THREADS;  // Lawson-Hanson block
-constexpr int kLHWide = 512;                  // block size for problems with many unknowns
-constexpr int kLHMaxWarps = kLHWide / 32;
 
 // ---------------------------------------------------------------------------
 // FP64 Gram of X = [S | s] (m x (d+1)) in tiles of 32 x 32, split over rows
@@ -182,18 +180,18 @@ struct dotff {
 };
 
 struct lh_shared {
-  uint32_t wkey[kLHMaxWarps];  // per-warp candidate keys / partial sums (fast path)
-  int widx[kLHMaxWarps];
-  float wsum[kLHMaxWarps];
+  uint32_t wkey[kLHThreads / 32];  // per-warp candidate keys / partial sums (fast path)
+  int widx[kLHThreads / 32];
+  float wsum[kLHThreads / 32];
   int p;       // passive count
   int t;       // candidate / chosen index
   int status;
   int flag;
   float fscal;
   ff ffscal;
-  int ired[kLHMaxWarps];
-  ff vred[kLHMaxWarps];
-  float fred[kLHMaxWarps];
+  int ired[kLHThreads / 32];
+  ff vred[kLHThreads / 32];
+  float fred[kLHThreads / 32];
 };
 
 // block sum of floats (all threads get the result)
@@ -961,17 +959,15 @@ __device__ void lh_block(const lh_job &jb, unsigned char *smem_raw, lh_shared &s
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, NT == 32 ? 16 : (NT == kLHWide ? 1 : 2))
-    lh_kernel(const lh_job *__restrict__ jobs, int max_outer_mul, int max_inner_mul, int warp_max_d, int wide_min_d) {
+__global__ void __launch_bounds__(NT, NT == 32 ? 16 : 2) lh_kernel(const lh_job *__restrict__ jobs, int max_outer_mul,
+                                                                  int max_inner_mul, int warp_max_d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ lh_shared sh;
   const lh_job jb = jobs[blockIdx.x];
   if (jb.d <= 0) return;  // a problem the device-side plan refused (its info says so)
-  // problems up to warp_max_d unknowns run as one-warp blocks, from
-  // wide_min_d on as 512-thread blocks, the others as 256-thread blocks: each
-  // launch skips the other kinds
-  const int want = jb.d <= warp_max_d ? 32 : (jb.d >= wide_min_d ? kLHWide : kLHThreads);
-  if (want != NT) return;
+  // problems up to warp_max_d unknowns run as one-warp blocks, the others as
+  // 256-thread blocks: each launch skips the other kind
+  if ((NT == 32) != (jb.d <= warp_max_d)) return;
   lh_block<NT>(jb, smem_raw, sh, max_outer_mul * jb.d, max_inner_mul * jb.d);
 }
 
@@ -1075,36 +1071,25 @@ size_t lh_bg_bytes(rnnls_ctx *ctx, int d) {
 // updates, not the block barriers, set a solve's time, so eight times the
 // work per thread costs more than the barriers save.
 int lh_warp_max_d(const rnnls_ctx *ctx) { return ctx->tune.lh_warp_max_d; }
-// From this many unknowns on, a problem runs as a 512-thread block (its dot
-// products and inverse updates spread over twice the threads).
-constexpr int kLHWideMinD = 129;
-int lh_wide_min_d(const rnnls_ctx *ctx) { return tune_or(ctx->tune.lh_wide_min_d, kLHWideMinD); }
 
 // d_jobs: `count` jobs with d in [min_d, max_d] (bounds; device-made job
 // tables pass 1 and their bound), smem: the largest block's shared memory.
 int lh_launch(rnnls_ctx *ctx, const lh_job *d_jobs, int64_t count, size_t smem, int min_d, int max_d) {
   prof_scope ps(ctx, K_LH);
   if (smem + kLHStaticSmem > (size_t)ctx->max_smem_optin) return RNNLS_EUNSUPPORTED;
-  const int wmd = lh_warp_max_d(ctx), wide = std::max(lh_wide_min_d(ctx), wmd + 1);
+  const int wmd = lh_warp_max_d(ctx);
   if (min_d <= wmd) {
     // the one-warp blocks' problems have d <= wmd: their shared memory is at most that of d = wmd
     const size_t s32 = std::min(smem, lh_make_layout(std::min(wmd, max_d), true, true).bytes);
     static smem_attr lh_attr32;
     RNNLS_CUDA_TRY(lh_attr32.ensure((const void *)lh_kernel<32>, s32));
-    lh_kernel<32><<<(unsigned)count, 32, s32, ctx->stream>>>(d_jobs, 3, 30, wmd, wide);
+    lh_kernel<32><<<(unsigned)count, 32, s32, ctx->stream>>>(d_jobs, 3, 30, wmd);
     if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
   }
-  // the wide blocks (the longest solves) first
-  if (max_d >= wide && max_d > wmd) {
-    static smem_attr lh_attr_w;
-    RNNLS_CUDA_TRY(lh_attr_w.ensure((const void *)lh_kernel<kLHWide>, smem));
-    lh_kernel<kLHWide><<<(unsigned)count, kLHWide, smem, ctx->stream>>>(d_jobs, 3, 30, wmd, wide);
-    if (cudaGetLastError() != cudaSuccess) return RNNLS_ECUDA;
-  }
-  if (max_d > wmd && min_d < wide) {
+  if (max_d > wmd) {
     static smem_attr lh_attr;
     RNNLS_CUDA_TRY(lh_attr.ensure((const void *)lh_kernel<kLHThreads>, smem));
-    lh_kernel<kLHThreads><<<(unsigned)count, kLHThreads, smem, ctx->stream>>>(d_jobs, 3, 30, wmd, wide);
+    lh_kernel<kLHThreads><<<(unsigned)count, kLHThreads, smem, ctx->stream>>>(d_jobs, 3, 30, wmd);
   }
   return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
 }
@@ -1117,10 +1102,6 @@ int lh_launch_one(rnnls_ctx *ctx, const lh_job &jb) {
     static smem_attr one_attr32;
     RNNLS_CUDA_TRY(one_attr32.ensure((const void *)lh_kernel_one<32>, smem));
     lh_kernel_one<32><<<1, 32, smem, ctx->stream>>>(jb, 3, 30);
-  } else if (jb.d >= lh_wide_min_d(ctx)) {
-    static smem_attr one_attr_w;
-    RNNLS_CUDA_TRY(one_attr_w.ensure((const void *)lh_kernel_one<kLHWide>, smem));
-    lh_kernel_one<kLHWide><<<1, kLHWide, smem, ctx->stream>>>(jb, 3, 30);
   } else {
     static smem_attr one_attr;
     RNNLS_CUDA_TRY(one_attr.ensure((const void *)lh_kernel_one<kLHThreads>, smem));

@@ -17,11 +17,11 @@ def test_tuning_round_trip_and_validation():
     try:
         assert all(v == 0 for v in ctx.get_tuning().values())
         t = {"sketch_sms": 100, "full_step_min_slots": 64, "gram_min_chunks": 4, "gram_max_splits": 16,
-             "batch_gram_chunks": 64, "batch_step_cost": 200, "lh_warp_max_d": 96, "lh_wide_min_d": 300}
+             "batch_gram_chunks": 64, "batch_step_cost": 200, "lh_warp_max_d": 96}
         ctx.set_tuning(t)
         assert ctx.get_tuning() == t
         for bad in ({"full_step_min_slots": 47}, {"gram_max_splits": 1025}, {"sketch_sms": -1},
-                    {"batch_step_cost": 100001}, {"lh_warp_max_d": -1}, {"lh_warp_max_d": 1025}, {"lh_wide_min_d": 1026}):
+                    {"batch_step_cost": 100001}, {"lh_warp_max_d": -1}, {"lh_warp_max_d": 1025}):
             with pytest.raises(B.RNNLSError) as e:
                 ctx.set_tuning(bad)
             assert e.value.status == B.RNNLS_EINVAL
@@ -149,7 +149,7 @@ def test_autotuner_end_to_end(tmp_path):
 
 @pytest.mark.parametrize("d", [8, 40, 64, 100])
 def test_lh_team_size_gives_the_same_solve(orc, d):
-    """Lawson-Hanson as one-warp, 256-thread or 512-thread blocks: the same
+    """Lawson-Hanson as one-warp blocks or as 256-thread blocks: the same
     active set and x within 1e-6 of the oracle's (one problem and a batch)."""
     import torch
 
@@ -164,8 +164,8 @@ def test_lh_team_size_gives_the_same_solve(orc, d):
     SA, Sb = dev_colmajor(SAh), dev_vec(Sbh)
     ctx = P.Context(0)
     try:
-        for wmd, wide in ((0, 0), (64, 0), (1024, 0), (0, 1), (0, 1025)):
-            ctx.set_tuning({"lh_warp_max_d": wmd, "lh_wide_min_d": wide})
+        for wmd in (0, 64, 1024):
+            ctx.set_tuning({"lh_warp_max_d": wmd})
             x, info = ctx.solve(SA, Sb)
             xs = torch.empty(d, dtype=torch.float64, device="cuda")
             infos = torch.zeros(P.INFO_BYTES, dtype=torch.uint8, device="cuda")
