@@ -1292,10 +1292,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       loaded_ji = ji;
       loaded_kg = kg;
     }
-    // No block barrier here: a warp that has finished the previous step may
-    // transform this one (its own copy wait, its own worker's barriers) while
-    // others still gather; the copies into freed buffers are issued after the
-    // barrier that follows the transform.
+    __syncthreads();  // the steps before `consumed` are done with their buffers
+    if (tid == 0 && n_issued < nsteps && n_issued < consumed + kStages) {
+      fence_proxy_async();
+      do {
+        issue();
+        ++n_issued;
+      } while (n_issued < nsteps && n_issued < consumed + kStages);
+    }
     {
       const uint32_t bar = smem_u32(&mbar[q]);
       const uint32_t limit = *(volatile int *)&stalled ? 64u : kSpinLimit;
@@ -1375,14 +1379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int s = 0; s < 64; ++s) zw[hi | ((uint32_t)s << 5) | (lane ^ (((uint32_t)s & 7u) << 2))] = v[s];
     }
-    __syncthreads();  // this step is transformed; every thread is done with the steps before `consumed`
-    if (tid == 0 && n_issued < nsteps && n_issued < consumed + kStages) {
-      fence_proxy_async();
-      do {
-        issue();
-        ++n_issued;
-      } while (n_issued < nsteps && n_issued < consumed + kStages);
-    }
+    __syncthreads();
     const bool full = slots >= J0.full_min;
     // Step pairs (full-step mode, kPairMinSlots or more rows per thread):
     // steps j (even) and j + 1 of a unit are combined together.  After both
