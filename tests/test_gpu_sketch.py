@@ -94,7 +94,10 @@ def test_unaligned_and_strided_inputs(ctx, orc):
     assert rel_fro(host(Sb), Sb_o) <= TOL_F32
 
 
-@pytest.mark.parametrize("n,d,r", [(4096, 20, 512), (100, 3, 50), (20000, 3, 300)])
+@pytest.mark.parametrize("n,d,r", [(4096, 20, 512), (100, 3, 50), (20000, 3, 300),
+                                   (300000, 4, 5000),   # one pass, four chunk groups per column
+                                   (70000, 2, 16384),   # one pass, the largest r it keeps in shared memory
+                                   (50000, 3, 20000)])  # larger r: the two-pass path
 def test_fp64_path(ctx, orc, n, d, r):
     p = workloads.problem(1, n=n, d=d, r=r)
     run_case(ctx, orc, p.A, p.b, r, seed=0, inst=0, mode=0, dtype=np.float64, tol=TOL_F64)
