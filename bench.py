@@ -87,7 +87,7 @@ def parse():
                     help="workload 2 or 3 with A held in compressed sparse columns (rnnls_sketch_csc); "
                          "one stream, sketch + solve per step")
     ap.add_argument("--free-sms", type=int, default=None,
-                    help="pipelined mode: SMs the sketch leaves to the solves (default: 8 + one per solve stream; "
+                    help="pipelined mode: SMs the sketch leaves to the solves (default: 5 + one per solve stream; "
                          "a Gram CTA needs a whole SM's shared memory)")
     args = ap.parse_args()
     if args.config is None:
@@ -450,7 +450,7 @@ def main():
     if pipeline:
         # SMs free of sketch blocks: one per concurrent Lawson-Hanson solve,
         # plus room for the tensor-core Gram CTAs of the solves
-        free = args.free_sms if args.free_sms is not None else 8 + nsolve
+        free = args.free_sms if args.free_sms is not None else 5 + nsolve
         for cs in ctx_sks:
             cs.set_sketch_sms(torch.cuda.get_device_properties(local).multi_processor_count - free)
     nbuf = nsolve + nsk if pipeline else 1

@@ -1658,7 +1658,10 @@ __global__ void __launch_bounds__(256) sketch_small(const T *__restrict__ A, int
 // (n / 2^17) * r * 8 bytes per column, written and read once.
 // ---------------------------------------------------------------------------
 constexpr int kF64Group = 32;          // chunks per block
-constexpr int64_t kF64MaxRows = 16384;  // rows whose sums and (h, l) fit in shared memory
+#ifndef RNNLS_F64_MAX_ROWS
+#define RNNLS_F64_MAX_ROWS 16384
+#endif
+constexpr int64_t kF64MaxRows = RNNLS_F64_MAX_ROWS;  // rows whose sums and (h, l) fit in shared memory
 
 __global__ void __launch_bounds__(256) sketch_f64_group(const double *__restrict__ A, int64_t lda,
                                                         const double *__restrict__ b, int64_t n_raw, int d, int64_t n,
@@ -2219,8 +2222,7 @@ int sketch_f64(rnnls_ctx *ctx, const sketch_args_f64 &a) {
     double *part = (double *)ctx->ws;
     const size_t smem = (size_t)kM * sizeof(double) + (size_t)a.r * (sizeof(double) + sizeof(uint32_t));
     static smem_attr group_attr;
-    RNNLS_CUDA_TRY(group_attr.ensure((const void *)sketch_f64_group,
-                                     (size_t)kM * sizeof(double) + (size_t)kF64MaxRows * (sizeof(double) + 4)));
+    RNNLS_CUDA_TRY(group_attr.ensure((const void *)sketch_f64_group, smem));
     sketch_f64_group<<<dim3((unsigned)nblk, (unsigned)(a.d + 1)), 256, smem, s>>>(
         a.A, a.lda, a.b, a.n_raw, a.d, n, a.seed, a.inst, a.idx, a.r, a.d_count, part);
     dim3 grid((unsigned)std::min<int64_t>((a.r + 255) / 256, 64), (unsigned)(a.d + 1));
