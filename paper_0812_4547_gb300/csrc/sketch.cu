@@ -1649,91 +1649,8 @@ __global__ void __launch_bounds__(256) sketch_small(const T *__restrict__ A, int
 }
 
 // ---------------------------------------------------------------------------
-// FP64, n > 2^13, r <= kF64MaxRows: one pass over X.  Block (column col,
-// chunks c0 .. c0 + kF64Group - 1) transforms its chunks one at a time in
-// shared memory (D applied) and adds, for every sampled row i = h 2^12 + l,
-// (-1)^popcount(h & c) times word l of chunk c into the row's partial sum,
-// kept in shared memory; a second launch adds a column's partials in block
-// order and scales them.  HBM reads X once; the partials are
-// (n / 2^17) * r * 8 bytes per column, written and read once.
-// ---------------------------------------------------------------------------
-constexpr int kF64Group = 32;          // chunks per block
-#ifndef RNNLS_F64_MAX_ROWS
-#define RNNLS_F64_MAX_ROWS 16384
-#endif
-constexpr int64_t kF64MaxRows = RNNLS_F64_MAX_ROWS;  // rows whose sums and (h, l) fit in shared memory
-
-__global__ void __launch_bounds__(256) sketch_f64_group(const double *__restrict__ A, int64_t lda,
-                                                        const double *__restrict__ b, int64_t n_raw, int d, int64_t n,
-                                                        uint64_t seed, uint64_t inst, const int32_t *__restrict__ idx,
-                                                        int64_t r, const int64_t *__restrict__ d_count,
-                                                        double *__restrict__ part) {
-  extern __shared__ double f64_smem[];  // chunk (kM), row sums (r), rows (r, u32)
-  __shared__ uint64_t words[kM / 64];
-  double *buf = f64_smem;
-  double *sums = f64_smem + kM;
-  uint32_t *rows = reinterpret_cast<uint32_t *>(sums + r);
-  const int col = blockIdx.y;
-  const int64_t C = n / kM;
-  const int64_t c0 = (int64_t)blockIdx.x * kF64Group, c1 = min(C, c0 + kF64Group);
-  int64_t rr = r;
-  if (d_count) rr = min(r, *d_count);
-  const double *__restrict__ x = (col < d) ? A + (int64_t)col * lda : b;
-  for (int64_t k = threadIdx.x; k < rr; k += blockDim.x) {
-    sums[k] = 0.0;
-    rows[k] = (uint32_t)idx[k];
-  }
-  for (int64_t c = c0; c < c1; ++c) {
-    if (threadIdx.x < kM / 256) {
-      const u64x4 u = philox4x64_10((uint64_t)c * (kM / 256) + threadIdx.x, kStreamSigns, seed, inst);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) words[4 * threadIdx.x + q] = u.w[q];
-    }
-    __syncthreads();  // the signs are visible; the previous chunk's gathers are done
-    for (int i = threadIdx.x; i < kM; i += blockDim.x) {
-      const int64_t row = c * kM + i;
-      const double v = (row < n_raw) ? x[row] : 0.0;
-      buf[i] = ((words[i >> 6] >> (i & 63)) & 1ull) ? -v : v;
-    }
-    __syncthreads();
-    for (int h = 1; h < kM; h <<= 1) {
-      for (int t = threadIdx.x; t < kM / 2; t += blockDim.x) {
-        const int i = ((t & ~(h - 1)) << 1) | (t & (h - 1));
-        const double a = buf[i], e = buf[i + h];
-        buf[i] = a + e;
-        buf[i + h] = a - e;
-      }
-      __syncthreads();
-    }
-    for (int64_t k = threadIdx.x; k < rr; k += blockDim.x) {
-      const uint32_t i = rows[k];
-      const double v = buf[i & (kM - 1)];
-      sums[k] += (__popc((i >> kLogM) & (uint32_t)c) & 1) ? -v : v;
-    }
-  }
-  double *out = part + ((int64_t)col * gridDim.x + blockIdx.x) * r;
-  for (int64_t k = threadIdx.x; k < rr; k += blockDim.x) out[k] = sums[k];
-}
-
-__global__ void sketch_f64_reduce(const double *__restrict__ part, int nblk, int d, int64_t r,
-                                  const int64_t *__restrict__ d_count, double scale, double *__restrict__ SA,
-                                  int64_t ldsa, double *__restrict__ Sb) {
-  int64_t rr = r;
-  if (d_count) rr = min(r, *d_count);
-  const int col = blockIdx.y;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < rr; k += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int g = 0; g < nblk; ++g) s += part[((int64_t)col * nblk + g) * r + k];
-    if (col < d)
-      SA[(int64_t)col * ldsa + k] = scale * s;
-    else
-      Sb[k] = scale * s;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// FP64, n > 2^13, r > kF64MaxRows: transform every chunk of 2^12 rows into a
-// workspace, then combine at the sampled rows.
+// FP64, n > 2^13: transform every chunk of 2^12 rows into a workspace, then
+// combine at the sampled rows.  (Correctness path; FP64 is slow on GB300.)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) chunk_transform_f64(const double *__restrict__ A, int64_t lda,
                                                            const double *__restrict__ b, int64_t n_raw, int d,
@@ -2212,21 +2129,6 @@ int sketch_f64(rnnls_ctx *ctx, const sketch_args_f64 &a) {
     sketch_small<double><<<(unsigned)(a.d + 1), 256, smem, s>>>(a.A, a.lda, a.b, a.n_raw, a.n_raw, a.d, a.L, a.seed,
                                                                 a.inst, a.idx, a.r, a.d_count, a.scale, a.SA, a.ldsa,
                                                                 a.Sb, a.r);
-    return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
-  }
-  if (a.r <= kF64MaxRows) {
-    const int nblk = (int)((n / kM + kF64Group - 1) / kF64Group);
-    const size_t pbytes = align_up((size_t)(a.d + 1) * nblk * a.r * sizeof(double), 256);
-    int st = ensure_workspace(ctx, pbytes);
-    if (st) return st;
-    double *part = (double *)ctx->ws;
-    const size_t smem = (size_t)kM * sizeof(double) + (size_t)a.r * (sizeof(double) + sizeof(uint32_t));
-    static smem_attr group_attr;
-    RNNLS_CUDA_TRY(group_attr.ensure((const void *)sketch_f64_group, smem));
-    sketch_f64_group<<<dim3((unsigned)nblk, (unsigned)(a.d + 1)), 256, smem, s>>>(
-        a.A, a.lda, a.b, a.n_raw, a.d, n, a.seed, a.inst, a.idx, a.r, a.d_count, part);
-    dim3 grid((unsigned)std::min<int64_t>((a.r + 255) / 256, 64), (unsigned)(a.d + 1));
-    sketch_f64_reduce<<<grid, 256, 0, s>>>(part, nblk, a.d, a.r, a.d_count, a.scale, a.SA, a.ldsa, a.Sb);
     return cudaGetLastError() == cudaSuccess ? RNNLS_OK : RNNLS_ECUDA;
   }
   const size_t zbytes = align_up((size_t)(a.d + 1) * n * sizeof(double), 256);
