@@ -30,7 +30,7 @@ CANDIDATES = {
     "gram_min_chunks": [0, 4, 16, 32],
     "gram_max_splits": [0, 8, 16, 64],
     "batch_gram_chunks": [0, 32, 64, 256],
-    "batch_step_cost": [0, 150, 400],
+    "batch_step_cost": [0, 60, 180, 300],
     "lh_warp_max_d": [0, 32, 64],
 }
 

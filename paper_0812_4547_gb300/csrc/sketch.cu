@@ -1956,24 +1956,19 @@ int sketch_batched_f32(rnnls_ctx *ctx, const rnnls_sketch_job *jobs, int64_t cou
   first_p[(size_t)nb] = plan_tot;
   const int sms = (ctx->sketch_sms > 0) ? std::min(ctx->sketch_sms, num_sms) : num_sms;
   const int64_t B = std::max<int64_t>(1, std::min<int64_t>(sms, Ttot));
-  // Block ranges of equal estimated cost (hundredths of a microsecond),
-  // fitted to per-block %globaltimer totals of workload 5 (152 blocks,
-  // 1 % rms): a step alone costs 244 + 3.85 slots (6.11 slots in the
-  // full-step mode), a step pair 714 + 2.28 slots, a unit's write-out
-  // 174 + 13 slots; spread evenly over the instance's steps.
+  // Block ranges of equal estimated cost, in units of about 22 ns: a step
+  // costs about 114 + slots (the transform, then the plan rows), plus the
+  // unit's write-out (about 6 slots) spread over its J steps.
   std::vector<int64_t> starts((size_t)B + 1);
   {
     std::vector<double> wt((size_t)nb), cum((size_t)nb + 1, 0.0);
-    const double step_cost = (double)tune_or(ctx->tune.batch_step_cost, 244);
+    const double step_cost = (double)tune_or(ctx->tune.batch_step_cost, 114);
     for (int t = 0; t < nb; ++t) {
       const srht_job &J = sj[(size_t)t];
-      const double sl = (double)J.slots;
-      const bool full = J.slots >= J.full_min;
-      const bool pairs = full && J.slots >= kPairMinSlots && J.J >= 2;
-      const double single = step_cost + (full ? 6.11 : 3.85) * sl;
-      const double unit = pairs ? (double)(J.J / 2) * (714.0 + 2.28 * sl) + (double)(J.J % 2) * single
-                                : (double)J.J * single;
-      wt[(size_t)t] = (unit + 174.0 + 13.0 * sl) / (double)J.J;
+      // steps combined in pairs (full-step mode) read each row once per two
+      // steps: about half the rows' cost, plus the pair's extra butterfly pass
+      const bool pairs = J.slots >= J.full_min && J.slots >= kPairMinSlots && J.J >= 2;
+      wt[(size_t)t] = step_cost + (pairs ? 16.0 + 0.55 * J.slots : (double)J.slots) + 6.0 * (double)J.slots / (double)J.J;
       cum[(size_t)t + 1] = cum[(size_t)t] + wt[(size_t)t] * (double)(J.U * J.J);
     }
     int t = 0;
