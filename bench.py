@@ -1387,8 +1387,9 @@ def e2e_batch(args, insts, bufs, dev, local: int, rank: int, ws: int, tuning=Non
                 for i in ids:
                     xs_host[i].copy_(bufs[i][3], non_blocking=True)
 
-    e2e_steps = args.e2e_steps if args.e2e_steps is not None else 3
-    e2e_step(0)
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else 4
+    for _ in range(2):  # warm-up: workspaces, pinned staging and the link's first transfers
+        e2e_step(0)
     torch.cuda.synchronize(dev)
     e0 = time.perf_counter()
     for k in range(e2e_steps):
