@@ -27,6 +27,20 @@ def test_coordinate_search_keeps_the_base_when_nothing_is_faster():
     assert best == {"a": 0} and t_best == t_base == 5.0
 
 
+def test_coordinate_search_skips_knobs_without_candidates():
+    """A caller's candidate table may cover only some of the kind's knobs:
+    the others keep their base value and are not timed."""
+    seen = []
+
+    def cost(t):
+        seen.append(dict(t))
+        return 1.0 + t.get("a", 0)
+
+    best, _, _, trials = T.coordinate_search(cost, ["a", "missing"], {"a": [0, 1]}, {"a": 1, "missing": 7})
+    assert best == {"a": 0, "missing": 7}
+    assert all(t["missing"] == 7 for t in seen) and len(trials) == 2
+
+
 def test_cache_round_trip_and_bad_files(tmp_path):
     p = str(tmp_path / "sub" / "tuning.json")
     assert T.load_cache(p) == {"version": T.CACHE_VERSION, "entries": {}}
