@@ -314,16 +314,18 @@ __device__ __forceinline__ void apply_B(const lh_vecs &V, int p, const float *g,
   for (int base = 0; base < p; base += NT / tpr) {
     const int s = base + threadIdx.x / tpr;
     const bool ok = s < p;
-    float a0 = 0.0f, a1 = 0.0f;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
     if (ok) {
       int q = part;
-      for (; q + tpr < p; q += 2 * tpr) {
+      for (; q + 3 * tpr < p; q += 4 * tpr) {
         a0 = fmaf(V.B[q * V.ldB + s], g[q], a0);
         a1 = fmaf(V.B[(q + tpr) * V.ldB + s], g[q + tpr], a1);
+        a2 = fmaf(V.B[(q + 2 * tpr) * V.ldB + s], g[q + 2 * tpr], a2);
+        a3 = fmaf(V.B[(q + 3 * tpr) * V.ldB + s], g[q + 3 * tpr], a3);
       }
-      if (q < p) a0 = fmaf(V.B[q * V.ldB + s], g[q], a0);
+      for (; q < p; q += tpr) a0 = fmaf(V.B[q * V.ldB + s], g[q], a0);
     }
-    float a = a0 + a1;
+    float a = (a0 + a1) + (a2 + a3);
     for (int o = 1; o < tpr; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (ok && part == 0) y[s] = a;
   }
@@ -365,16 +367,19 @@ __device__ __forceinline__ void dual_and_warp_best(const lh_vecs &V, int d, int 
   for (int base = 0; base < d; base += NT / tpj) {
     const int j = base + threadIdx.x / tpj;
     const bool ok = j < d;
-    float a0 = 0.0f, a1 = 0.0f;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
     if (ok) {
+      // four independent loads in flight (Q may sit in L1/L2 for large d)
       int s = part;
-      for (; s + tpj < p; s += 2 * tpj) {
+      for (; s + 3 * tpj < p; s += 4 * tpj) {
         a0 = fmaf(-V.Qh[V.slotvar[s] * V.ldQ + j], V.xs[s].hi, a0);
         a1 = fmaf(-V.Qh[V.slotvar[s + tpj] * V.ldQ + j], V.xs[s + tpj].hi, a1);
+        a2 = fmaf(-V.Qh[V.slotvar[s + 2 * tpj] * V.ldQ + j], V.xs[s + 2 * tpj].hi, a2);
+        a3 = fmaf(-V.Qh[V.slotvar[s + 3 * tpj] * V.ldQ + j], V.xs[s + 3 * tpj].hi, a3);
       }
-      if (s < p) a0 = fmaf(-V.Qh[V.slotvar[s] * V.ldQ + j], V.xs[s].hi, a0);
+      for (; s < p; s += tpj) a0 = fmaf(-V.Qh[V.slotvar[s] * V.ldQ + j], V.xs[s].hi, a0);
     }
-    float a = a0 + a1;
+    float a = (a0 + a1) + (a2 + a3);
     for (int o = 1; o < tpj; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (ok && part == 0) {
       const float wj = V.qv[j].hi + a;
@@ -424,20 +429,23 @@ __device__ __forceinline__ void bordered_v(const lh_vecs &V, int p, int t, float
   for (int base = 0; base < p; base += NT / tpr) {
     const int s = base + threadIdx.x / tpr;
     const bool ok = s < p;
-    float a0 = 0.0f, a1 = 0.0f;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
     if (ok) {
       int q = part;
-      for (; q + tpr < p; q += 2 * tpr) {
+      for (; q + 3 * tpr < p; q += 4 * tpr) {
         const int v0 = V.slotvar[q], v1 = V.slotvar[q + tpr];
+        const int v2 = V.slotvar[q + 2 * tpr], v3 = V.slotvar[q + 3 * tpr];
         a0 = fmaf(V.B[q * V.ldB + s], qt[v0] * V.Dsc[v0], a0);
         a1 = fmaf(V.B[(q + tpr) * V.ldB + s], qt[v1] * V.Dsc[v1], a1);
+        a2 = fmaf(V.B[(q + 2 * tpr) * V.ldB + s], qt[v2] * V.Dsc[v2], a2);
+        a3 = fmaf(V.B[(q + 3 * tpr) * V.ldB + s], qt[v3] * V.Dsc[v3], a3);
       }
-      if (q < p) {
+      for (; q < p; q += tpr) {
         const int v0 = V.slotvar[q];
         a0 = fmaf(V.B[q * V.ldB + s], qt[v0] * V.Dsc[v0], a0);
       }
     }
-    float a = (a0 + a1) * dt;
+    float a = ((a0 + a1) + (a2 + a3)) * dt;
     for (int o = 1; o < tpr; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (ok && part == 0) {
       V.f3[s] = a;
