@@ -339,15 +339,21 @@ __device__ __noinline__ void compute_w(const lh_vecs &V, int d, int p) {
   for (int base = 0; base < d; base += NT / tpj) {
     const int j = base + threadIdx.x / tpj;
     const bool ok = j < d;
-    dotff a0;
+    dotff a0, a1;
     if (ok) {
       if (part == 0) a0.init(V.qv[j]);
-      for (int s = part; s < p; s += tpj) {
-        const int e = V.slotvar[s] * V.ldQ + j;
-        a0.sub_prod(ff{V.Qh[e], V.Ql[e]}, V.xs[s]);
+      int s = part;
+      for (; s + tpj < p; s += 2 * tpj) {
+        const int e0 = V.slotvar[s] * V.ldQ + j, e1 = V.slotvar[s + tpj] * V.ldQ + j;
+        a0.sub_prod(ff{V.Qh[e0], V.Ql[e0]}, V.xs[s]);
+        a1.sub_prod(ff{V.Qh[e1], V.Ql[e1]}, V.xs[s + tpj]);
+      }
+      if (s < p) {
+        const int e0 = V.slotvar[s] * V.ldQ + j;
+        a0.sub_prod(ff{V.Qh[e0], V.Ql[e0]}, V.xs[s]);
       }
     }
-    ff a = a0.value();
+    ff a = ff_add(a0.value(), a1.value());
     for (int o = 1; o < tpj; o <<= 1) {
       const ff u{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
       a = ff_add(a, u);
@@ -367,22 +373,23 @@ __device__ __forceinline__ void dual_and_warp_best(const lh_vecs &V, int d, int 
   for (int base = 0; base < d; base += NT / tpj) {
     const int j = base + threadIdx.x / tpj;
     const bool ok = j < d;
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (ok) {
-      // four independent loads in flight (Q may sit in L1/L2 for large d)
+      // eight independent loads in flight (Q sits in L2 for large d)
       int s = part;
-      for (; s + 3 * tpj < p; s += 4 * tpj) {
-        a0 = fmaf(-V.Qh[V.slotvar[s] * V.ldQ + j], V.xs[s].hi, a0);
-        a1 = fmaf(-V.Qh[V.slotvar[s + tpj] * V.ldQ + j], V.xs[s + tpj].hi, a1);
-        a2 = fmaf(-V.Qh[V.slotvar[s + 2 * tpj] * V.ldQ + j], V.xs[s + 2 * tpj].hi, a2);
-        a3 = fmaf(-V.Qh[V.slotvar[s + 3 * tpj] * V.ldQ + j], V.xs[s + 3 * tpj].hi, a3);
+      for (; s + 7 * tpj < p; s += 8 * tpj) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int su = s + u * tpj;
+          a[u] = fmaf(-V.Qh[V.slotvar[su] * V.ldQ + j], V.xs[su].hi, a[u]);
+        }
       }
-      for (; s < p; s += tpj) a0 = fmaf(-V.Qh[V.slotvar[s] * V.ldQ + j], V.xs[s].hi, a0);
+      for (; s < p; s += tpj) a[0] = fmaf(-V.Qh[V.slotvar[s] * V.ldQ + j], V.xs[s].hi, a[0]);
     }
-    float a = (a0 + a1) + (a2 + a3);
-    for (int o = 1; o < tpj; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    float acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    for (int o = 1; o < tpj; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (ok && part == 0) {
-      const float wj = V.qv[j].hi + a;
+      const float wj = V.qv[j].hi + acc;
       V.w[j] = ff{wj, 0.0f};
       if (V.varslot[j] < 0) {
         const uint32_t k = fkey(wj);
@@ -515,26 +522,37 @@ __device__ __noinline__ int select_alpha(const lh_vecs &V, int p, lh_shared &sh,
   return sh.t;
 }
 
-// res_i = q_{v_i} - sum_q Q[v_i][v_q] z_q for slots i < np (float-float)
+// res_i = q_{v_i} - sum_q Q[v_i][v_q] z_q for slots i < np (float-float).
+// Q is stored bitwise symmetric, so slot i reads column v_i of the rows v_q:
+// the slots of one warp then read within the same rows.
 template <int NT>
 __device__ __noinline__ void residual_slots(const lh_vecs &V, int np) {
-  for (int i = threadIdx.x; i < np; i += NT) {
-    const int vi = V.slotvar[i];
-    const float *rh = V.Qh + vi * V.ldQ;
-    const float *rl = V.Ql + vi * V.ldQ;
+  const int tpr = lanes_per_row(np);
+  const int part = threadIdx.x & (tpr - 1);
+  for (int base = 0; base < np; base += NT / tpr) {
+    const int i = base + threadIdx.x / tpr;
+    const bool ok = i < np;
     dotff a0, a1;
-    a0.init(V.qv[vi]);
-    int q = 0;
-    for (; q + 1 < np; q += 2) {
-      const int v0 = V.slotvar[q], v1 = V.slotvar[q + 1];
-      a0.sub_prod(ff{rh[v0], rl[v0]}, V.zs[q]);
-      a1.sub_prod(ff{rh[v1], rl[v1]}, V.zs[q + 1]);
+    if (ok) {
+      const int vi = V.slotvar[i];
+      if (part == 0) a0.init(V.qv[vi]);
+      int q = part;
+      for (; q + tpr < np; q += 2 * tpr) {
+        const int e0 = V.slotvar[q] * V.ldQ + vi, e1 = V.slotvar[q + tpr] * V.ldQ + vi;
+        a0.sub_prod(ff{V.Qh[e0], V.Ql[e0]}, V.zs[q]);
+        a1.sub_prod(ff{V.Qh[e1], V.Ql[e1]}, V.zs[q + tpr]);
+      }
+      if (q < np) {
+        const int e0 = V.slotvar[q] * V.ldQ + vi;
+        a0.sub_prod(ff{V.Qh[e0], V.Ql[e0]}, V.zs[q]);
+      }
     }
-    if (q < np) {
-      const int v0 = V.slotvar[q];
-      a0.sub_prod(ff{rh[v0], rl[v0]}, V.zs[q]);
+    ff a = ff_add(a0.value(), a1.value());
+    for (int o = 1; o < tpr; o <<= 1) {
+      const ff u{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+      a = ff_add(a, u);
     }
-    V.res[i] = ff_add(a0.value(), a1.value());
+    if (ok && part == 0) V.res[i] = a;
   }
 }
 
