@@ -425,13 +425,21 @@ __device__ __forceinline__ int merge_warp_best(const lh_shared &sh) {
   return bi;
 }
 
-// Fast path, phase 2: v = B u with u_s = D_s Q[v_s][t] D_t made on the fly,
-// v into f3, per-warp partial sums of u'v into sh.wsum.
+// Fast path, phase 2: v = B u with u_s = D_s Q[v_s][t] D_t, v into f3,
+// per-warp partial sums of u'v into sh.wsum.  D_s Q[v_s][t] is formed once
+// per slot into f1 (row t of Q may sit in L2; f1 is free here), so the
+// product reads shared memory only.
 template <int NT>
 __device__ __forceinline__ void bordered_v(const lh_vecs &V, int p, int t, float dt, lh_shared &sh) {
   const int tpr = lanes_per_row(p);
   const int part = threadIdx.x & (tpr - 1);
   const float *qt = V.Qh + t * V.ldQ;
+  for (int q = threadIdx.x; q < p; q += NT) {
+    const int v = V.slotvar[q];
+    V.f1[q] = qt[v] * V.Dsc[v];
+  }
+  __syncthreads();
+  const float *u = V.f1;
   float uv = 0.0f;
   for (int base = 0; base < p; base += NT / tpr) {
     const int s = base + threadIdx.x / tpr;
@@ -440,24 +448,18 @@ __device__ __forceinline__ void bordered_v(const lh_vecs &V, int p, int t, float
     if (ok) {
       int q = part;
       for (; q + 3 * tpr < p; q += 4 * tpr) {
-        const int v0 = V.slotvar[q], v1 = V.slotvar[q + tpr];
-        const int v2 = V.slotvar[q + 2 * tpr], v3 = V.slotvar[q + 3 * tpr];
-        a0 = fmaf(V.B[q * V.ldB + s], qt[v0] * V.Dsc[v0], a0);
-        a1 = fmaf(V.B[(q + tpr) * V.ldB + s], qt[v1] * V.Dsc[v1], a1);
-        a2 = fmaf(V.B[(q + 2 * tpr) * V.ldB + s], qt[v2] * V.Dsc[v2], a2);
-        a3 = fmaf(V.B[(q + 3 * tpr) * V.ldB + s], qt[v3] * V.Dsc[v3], a3);
+        a0 = fmaf(V.B[q * V.ldB + s], u[q], a0);
+        a1 = fmaf(V.B[(q + tpr) * V.ldB + s], u[q + tpr], a1);
+        a2 = fmaf(V.B[(q + 2 * tpr) * V.ldB + s], u[q + 2 * tpr], a2);
+        a3 = fmaf(V.B[(q + 3 * tpr) * V.ldB + s], u[q + 3 * tpr], a3);
       }
-      for (; q < p; q += tpr) {
-        const int v0 = V.slotvar[q];
-        a0 = fmaf(V.B[q * V.ldB + s], qt[v0] * V.Dsc[v0], a0);
-      }
+      for (; q < p; q += tpr) a0 = fmaf(V.B[q * V.ldB + s], u[q], a0);
     }
     float a = ((a0 + a1) + (a2 + a3)) * dt;
     for (int o = 1; o < tpr; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (ok && part == 0) {
       V.f3[s] = a;
-      const int vs = V.slotvar[s];
-      uv = fmaf(qt[vs] * V.Dsc[vs] * dt, a, uv);
+      uv = fmaf(u[s] * dt, a, uv);
     }
   }
   for (int o = 16; o > 0; o >>= 1) uv += __shfl_xor_sync(0xffffffffu, uv, o);
