@@ -2,13 +2,14 @@
 active-set method, every step refined in float-float) made to happen.
 
 The problems have a near-tie: at the optimum over a support P, one inactive
-column j0 has a dual w_j0 = 30 tol -- clearly positive in FP64, yet far below
-the noise of an FP32 dual -- and every other inactive column a strongly
-negative one.  The exact method therefore adds j0 with a tiny positive value.
-The solver's FP32 iterations miss j0 about half the time; their end-point
-check in float-float then finds w_j0 > tol and continues in the accurate
-mode (info.accurate_mode = 2).  Either way the final active set must be the
-oracle's and x within 1e-6 of it."""
+column j0 has a dual w_j0 = 30 tol or 5 tol -- clearly positive in FP64, yet
+within the noise of an FP32 dual (about 10 to 20 tol on these sizes) -- and
+every other inactive column a strongly negative one.  The exact method
+therefore adds j0 with a tiny positive value.  The solver's FP32 iterations
+miss j0 in some of the problems (rarely at 30 tol, often at 5 tol); their
+end-point check in float-float then finds w_j0 > tol and continues in the
+accurate mode (info.accurate_mode = 2).  Either way the final active set must
+be the oracle's and x within 1e-6 of it."""
 import numpy as np
 import pytest
 
@@ -49,9 +50,9 @@ def near_tie_problem(orc, seed, r=2000, d=40, npass=15, delta_tols=30.0, depende
     return SA, Sb, j0
 
 
-@pytest.mark.parametrize("seed", [0, 3, 6])
-def test_construction_has_the_near_tie(orc, seed):
-    SA, Sb, j0 = near_tie_problem(orc, seed)
+@pytest.mark.parametrize("seed,delta_tols", [(0, 30.0), (3, 30.0), (6, 30.0), (200, 5.0), (207, 5.0), (211, 5.0)])
+def test_construction_has_the_near_tie(orc, seed, delta_tols):
+    SA, Sb, j0 = near_tie_problem(orc, seed, delta_tols=delta_tols)
     x, info = orc.nnls(SA, Sb)
     assert info["status"] == 0
     assert set(np.flatnonzero(x > 0)) == set(range(15)) | {j0}
@@ -65,7 +66,8 @@ def test_accurate_mode_is_entered_and_matches_the_oracle(orc):
     ctx = P.Context(0)
     modes = []
     try:
-        cases = [dict(seed=s) for s in range(12)] + [dict(seed=100 + s, dependent=1e-3) for s in range(4)]
+        cases = ([dict(seed=s) for s in range(12)] + [dict(seed=100 + s, dependent=1e-3) for s in range(4)] +
+                 [dict(seed=200 + s, delta_tols=5.0) for s in range(12)])
         for kw in cases:
             SA, Sb, j0 = near_tie_problem(orc, **kw)
             x_ref, info_ref = orc.nnls(SA, Sb)
@@ -79,7 +81,7 @@ def test_accurate_mode_is_entered_and_matches_the_oracle(orc):
             modes.append(got["accurate_mode"])
     finally:
         ctx.close()
-    # the FP32 iterations miss the near-tie about half the time
+    # the FP32 iterations miss the near-tie in some of the problems
     assert sum(m > 0 for m in modes) >= 1, modes
 
 
@@ -92,6 +94,7 @@ def test_accurate_mode_in_batched_solves(orc):
     import paper_0812_4547_gb300 as P
 
     probs = [near_tie_problem(orc, seed) for seed in range(8)]
+    probs += [near_tie_problem(orc, 200 + s, delta_tols=5.0) for s in range(8)]
     ctx = P.Context(0)
     try:
         tens = []
